@@ -1,0 +1,273 @@
+"""Serial FINOM recurrences in float64 (test infrastructure).
+
+This module is test infrastructure, not product code.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline and reference
+legs) may import it.  It shares no code with the CUDA library.
+
+It follows the paper's construction step by step, with 0-based arrays:
+
+* ``dividing_index``      -- Definition (dividing index), Sec. 2.2:
+  zeta(i) = number of y_j with y_j <= x_i (so zeta(i) = 0 when x_i < y_1 and
+  zeta(i) = M when x_i >= y_M).
+* ``lower_representation`` -- Theorem (vector representation of K_L), eqs.
+  ``ratio`` and ``eta``: r_i = k~_{i+1,1} / k~_{i,1} (1 when the denominator is
+  a structural zero, i.e. zeta(i) = 0) and the block-edge vectors
+  eta_i = [k~_{i, zeta(i-1)+1} ... k~_{i, zeta(i)}].
+* ``upper_representation`` -- Theorem (vector representation of K_U):
+  r'_i = k^_{i,M} / k^_{i+1,M} (1 when zeta(i+1) = M) and
+  eta'_i = [k^_{i, zeta(i)+1} ... k^_{i, zeta(i+1)}], zeta(N+1) := M.
+* ``matvec_linear`` -- eqs. ``decompose to p+q``, ``p by dynamic programming``
+  and ``q by dynamic programming``: p_1 = eta_1 . psi_1,
+  p_{i+1} = r_i p_i + eta_{i+1} . psi_{i+1}; q_N = eta'_N . psi'_N,
+  q_i = r'_i q_{i+1} + eta'_i . psi'_i; K psi = p + q.
+* ``matvec_log`` -- the same recurrences for the stabilised kernel of Remark
+  ``log-domain-stabilization`` (r_i <- e^{(a_{i+1}-a_i)/eps} r_i,
+  k~_ij <- e^{(a_i+b_j)/eps} k~_ij), evaluated in log arithmetic.
+* ``sinkhorn_log`` -- Algorithm 1 with that stabilisation applied after every
+  half step, in log arithmetic.
+* ``apply2d_log`` / ``sinkhorn2d_log`` -- Algorithm 2 with the stabilisation
+  of Appendix A (eq. ``K'bpsi``): a column pass with a_x = 0, b_x = B(:, j)
+  and a row pass with a_y = A(k, :), b_y = 0.
+
+Ratios are taken in closed form, ``e^{-(x_{i+1}-x_i)/eps}``: in exact
+arithmetic that is what the quotient of two kernel entries equals, and it
+avoids the 0/0 that the quotient of two float64 underflows would give.
+Pure-Python loops: for small inputs only (N, M up to a few thousand).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "dividing_index", "lower_representation", "upper_representation",
+    "matvec_linear", "matvec_log", "sinkhorn_log", "apply2d_log",
+    "sinkhorn2d_log", "logaddexp", "lse",
+]
+
+NEG_INF = -math.inf
+
+
+def logaddexp(a, b):
+    """log(e^a + e^b) with -inf handled."""
+    if a == NEG_INF:
+        return b
+    if b == NEG_INF:
+        return a
+    m = max(a, b)
+    return m + math.log1p(math.exp(-abs(a - b)))
+
+
+def lse(vals):
+    """log sum exp of a list (empty -> -inf)."""
+    if len(vals) == 0:
+        return NEG_INF
+    m = max(vals)
+    if m == NEG_INF:
+        return NEG_INF
+    return m + math.log(math.fsum(math.exp(t - m) for t in vals))
+
+
+def dividing_index(x, y):
+    """zeta(i) = #{j : y_j <= x_i} for sorted x, y (Definition, Sec. 2.2)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N, M = len(x), len(y)
+    zeta = np.zeros(N, dtype=np.int64)
+    j = 0
+    for i in range(N):
+        while j < M and y[j] <= x[i]:
+            j += 1
+        zeta[i] = j
+    return zeta
+
+
+def _kcheck(x, y, zeta, i, j, eps):
+    """Entry of K_L: e^{-(x_i - y_j)/eps} for j < zeta(i) (0-based j), else 0."""
+    return math.exp(-(x[i] - y[j]) / eps) if j < zeta[i] else 0.0
+
+
+def _khat(x, y, zeta, i, j, eps):
+    """Entry of K_U: e^{-(y_j - x_i)/eps} for j >= zeta(i) (0-based j), else 0."""
+    return math.exp(-(y[j] - x[i]) / eps) if j >= zeta[i] else 0.0
+
+
+def lower_representation(x, y, eps, zeta=None):
+    """(r, eta) of Theorem (vector representation of K_L)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if zeta is None:
+        zeta = dividing_index(x, y)
+    N = len(x)
+    r = []
+    for i in range(N - 1):
+        # denominator k~_{i,1} is a structural zero when row i of K_L is empty
+        r.append(math.exp(-(x[i + 1] - x[i]) / eps) if zeta[i] >= 1 else 1.0)
+    eta = []
+    for i in range(N):
+        lo = zeta[i - 1] if i >= 1 else 0
+        eta.append([_kcheck(x, y, zeta, i, j, eps) for j in range(lo, zeta[i])])
+    return r, eta
+
+
+def upper_representation(x, y, eps, zeta=None):
+    """(r', eta') of Theorem (vector representation of K_U)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if zeta is None:
+        zeta = dividing_index(x, y)
+    N, M = len(x), len(y)
+    rp = []
+    for i in range(N - 1):
+        # denominator k^_{i+1,M} is a structural zero when row i+1 of K_U is empty
+        rp.append(math.exp(-(x[i + 1] - x[i]) / eps) if zeta[i + 1] < M else 1.0)
+    etap = []
+    for i in range(N):
+        hi = zeta[i + 1] if i + 1 < N else M
+        etap.append([_khat(x, y, zeta, i, j, eps) for j in range(zeta[i], hi)])
+    return rp, etap
+
+
+def matvec_linear(x, y, eps, psi):
+    """K psi by the two recurrences (eqs. p/q by dynamic programming)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    psi = np.asarray(psi, dtype=np.float64)
+    N = len(x)
+    zeta = dividing_index(x, y)
+    r, eta = lower_representation(x, y, eps, zeta)
+    rp, etap = upper_representation(x, y, eps, zeta)
+    M = len(y)
+    p = np.zeros(N)
+    q = np.zeros(N)
+    # p_1 = eta_1 . psi_1 ; p_{i+1} = r_i p_i + eta_{i+1} . psi_{i+1}
+    seg = psi[0:zeta[0]]
+    p[0] = math.fsum(a * b for a, b in zip(eta[0], seg))
+    for i in range(N - 1):
+        seg = psi[zeta[i]:zeta[i + 1]]
+        p[i + 1] = r[i] * p[i] + math.fsum(a * b for a, b in zip(eta[i + 1], seg))
+    # q_N = eta'_N . psi'_N ; q_i = r'_i q_{i+1} + eta'_i . psi'_i
+    seg = psi[zeta[N - 1]:M]
+    q[N - 1] = math.fsum(a * b for a, b in zip(etap[N - 1], seg))
+    for i in range(N - 2, -1, -1):
+        seg = psi[zeta[i]:zeta[i + 1]]
+        q[i] = rp[i] * q[i + 1] + math.fsum(a * b for a, b in zip(etap[i], seg))
+    return p + q, p, q
+
+
+def matvec_log(x, y, eps, a, b):
+    """log(K' 1) for K' = diag(e^{a/eps}) K diag(e^{b/eps}) (Remark
+    log-domain-stabilization), by the p/q recurrences in log arithmetic.
+
+    Modified ratios: log r_i = (a_{i+1} - a_i)/eps + log r_i, and modified
+    entries log k~'_ij = (a_i + b_j)/eps + log k~_ij (likewise for K_U).
+    Returns (log(p+q), log p, log q)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    N, M = len(x), len(y)
+    zeta = dividing_index(x, y)
+
+    def log_kcheck(i, j):   # log of the absorbed lower-block entry
+        return (a[i] + b[j] - (x[i] - y[j])) / eps
+
+    def log_khat(i, j):     # log of the absorbed upper-block entry
+        return (a[i] + b[j] - (y[j] - x[i])) / eps
+
+    lp = np.full(N, NEG_INF)
+    lq = np.full(N, NEG_INF)
+    lp[0] = lse([log_kcheck(0, j) for j in range(0, zeta[0])])
+    for i in range(N - 1):
+        # closed-form lower ratio (1 where the denominator is a structural zero)
+        lr = -(x[i + 1] - x[i]) / eps if zeta[i] >= 1 else 0.0
+        lr += (a[i + 1] - a[i]) / eps
+        edge = lse([log_kcheck(i + 1, j) for j in range(zeta[i], zeta[i + 1])])
+        lp[i + 1] = logaddexp(lr + lp[i] if lp[i] != NEG_INF else NEG_INF, edge)
+    lq[N - 1] = lse([log_khat(N - 1, j) for j in range(zeta[N - 1], M)])
+    for i in range(N - 2, -1, -1):
+        lr = -(x[i + 1] - x[i]) / eps if zeta[i + 1] < M else 0.0
+        lr += (a[i] - a[i + 1]) / eps
+        edge = lse([log_khat(i, j) for j in range(zeta[i], zeta[i + 1])])
+        lq[i] = logaddexp(lr + lq[i + 1] if lq[i + 1] != NEG_INF else NEG_INF, edge)
+    tot = np.array([logaddexp(lp[i], lq[i]) for i in range(N)])
+    return tot, lp, lq
+
+
+def _log(a):
+    a = np.asarray(a, dtype=np.float64)
+    out = np.full(a.shape, -np.inf)
+    out[a > 0] = np.log(a[a > 0])
+    return out
+
+
+def sinkhorn_log(x, y, u, v, eps, tol, maxit):
+    """Algorithm 1 with log-domain stabilisation absorbed after every half step.
+
+    Absorption vectors a (x side) and b (y side) carry eps*log(phi) and
+    eps*log(psi); after each absorption phi = psi = 1, so each half step is
+    one stabilised product K'^T 1 or K' 1.  Start: phi = 1/N, psi = 1/M.
+    Loop head: marginal error || diag(psi) K^T phi - v ||_1 <= tol or l = maxit.
+    Returns (a, b, iters, err)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N, M = len(x), len(y)
+    logu, logv = _log(u), _log(v)
+    a = np.full(N, eps * math.log(1.0 / N))
+    b = np.full(M, eps * math.log(1.0 / M))
+    it = 0
+    while True:
+        # K'^T 1 with rows = y (transposed case): roles of (x, a) and (y, b) swap
+        lt, _, _ = matvec_log(y, x, eps, b, a)
+        err = math.fsum(abs(math.exp(t) - vj) for t, vj in zip(lt, v))
+        if it >= maxit or err <= tol:
+            break
+        b = b + eps * (logv - lt)          # absorb eps*log(psi), psi = v / (K'^T 1)
+        lk, _, _ = matvec_log(x, y, eps, a, b)
+        a = a + eps * (logu - lk)          # absorb eps*log(phi), phi = u / (K' 1)
+        it += 1
+    return a, b, it, err
+
+
+def apply2d_log(x1, y1, x2, y2, eps, A, B):
+    """log(K' 1) on the first grid for K' = diag(e^{a/eps}) (K_y (x) K_x)
+    diag(e^{b/eps}) (Appendix A, eq. K'bpsi), with a = vec(A), b = vec(B)
+    (A, B of shape N x M, column-major grids).
+
+    Column pass: log Q(:, j) = log(K_x e^{B(:, j)/eps}) -- the 1D stabilised
+    product with a_x = 0, b_x = B(:, j).  Row pass: log P(k, :) =
+    log(diag(e^{A(k,:)/eps}) K_y Q(k,:)^T) -- the 1D stabilised product with
+    a_y = A(k, :), b_y = eps * log Q(k, :)."""
+    N, M = len(x1), len(y1)
+    logQ = np.empty((N, M))
+    zeros_n = np.zeros(N)
+    for j in range(M):
+        logQ[:, j], _, _ = matvec_log(x1, x2, eps, zeros_n, B[:, j])
+    logP = np.empty((N, M))
+    for k in range(N):
+        logP[k, :], _, _ = matvec_log(y1, y2, eps, A[k, :], eps * logQ[k, :])
+    return logP
+
+
+def sinkhorn2d_log(x1, y1, x2, y2, U, V, eps, tol, maxit):
+    """Algorithm 2 with the Appendix A stabilisation (absorb every half step).
+
+    U, V: N x M masses (column-major grids).  Start Phi = Psi = 1/(NM).
+    Returns (A, B, iters, err) with A = eps log Phi, B = eps log Psi."""
+    N, M = len(x1), len(y1)
+    logU, logV = _log(U), _log(V)
+    A = np.full((N, M), eps * math.log(1.0 / (N * M)))
+    B = np.full((N, M), eps * math.log(1.0 / (N * M)))
+    it = 0
+    while True:
+        # transposed product: grids swap roles
+        lt = apply2d_log(x2, y2, x1, y1, eps, B, A)
+        err = math.fsum(np.abs(np.exp(lt) - V).ravel().tolist())
+        if it >= maxit or err <= tol:
+            break
+        B = B + eps * (logV - lt)
+        lk = apply2d_log(x1, y1, x2, y2, eps, A, B)
+        A = A + eps * (logU - lk)
+        it += 1
+    return A, B, it, err
