@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the FINOM hot path: Sinkhorn iterations on the 1D large graded mesh.
+
+Workload: N = M = 2^20 graded meshes (x_i = ((i+1/2)/N)^2, tanh-stretched y,
+stretch 3), three-component Gaussian mixtures, eps = 1e-3, FP32 log-domain
+scans.  One step = one Sinkhorn iteration (K^T phi half step with the fused
+divide and marginal-error check, then the K psi half step): 2^21
+point-iterations.  L2 is flushed (256 MB write) before every timed step, and
+each step is timed with CUDA events on the launching stream.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(serial float64 FINOM recurrences in plain C) on the same workload instead.
+Under torchrun every rank runs its own replica of the workload (weak
+scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point-iters/s (K·v) vs HBM roofline; served solves/s, p99 at W1 relerr≤1e-4"
+UNIT = "point-iters/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_apply_graded_1d_2e20.md")
+KERNEL_SOURCES = ["paper_2605_26659_gb300/csrc/apply.cuh", "paper_2605_26659_gb300/csrc/dev_common.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
+    ap.add_argument("--n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        txt = open(PROFILE_MD).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*;\s*kernel_sha:\s*([0-9a-f]+)", txt)
+    if not m or m.group(2) != kernel_sha():
+        return None
+    return float(m.group(1))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(pr, budget_s=12.0):
+    """The CPU oracle (serial C FINOM, float64) on a bounded sample: whole
+    Sinkhorn iterations on the full-size meshes, one core."""
+    from oracle import serial_c
+    serial_c.lib()
+    t0 = time.perf_counter()
+    serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1)
+    t1 = time.perf_counter() - t0
+    iters = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, iters)
+    dt = time.perf_counter() - t0
+    # the oracle computes the loop-head check once per completed iteration + once at exit
+    return {"value": (len(pr.x) + len(pr.y)) * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} Sinkhorn iterations of the serial C float64 FINOM oracle on the full "
+                      f"N=M={len(pr.x)} graded meshes ({dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.config2(args.n)
+    from oracle import serial_c
+    serial_c.lib()
+    # each step: one Sinkhorn iteration of the oracle at full size
+    f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 0)
+    for _ in range(args.warmup):
+        f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1, f0=f, g0=g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1, f0=f, g0=g)
+    dt = time.perf_counter() - t0
+    val = (len(pr.x) + len(pr.y)) * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "gpu_launches": 0,
+            "config": {"workload": f"1D graded meshes N=M={args.n}, eps=1e-3, one Sinkhorn iteration per step",
+                       "N": args.n, "M": args.n, "eps": pr.eps},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} Sinkhorn iterations of the serial C float64 oracle"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_finom(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2605_26659_gb300 import api, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    pr = inputs.config2(args.n)
+    N, M = len(pr.x), len(pr.y)
+    L = N + M
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    x, y, u, v = T(pr.x), T(pr.y), T(pr.u), T(pr.v)
+    stream = torch.cuda.current_stream(dev)
+    plan = api.finom_plan(x, y, pr.eps, "f32_log", stream=stream)
+    api.finom_solve_begin(plan, u, v, 0.0, 1 << 40, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        api.finom_solve_step(plan, 1, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s_ev, e_ev in evs:
+        flush.zero_()
+        s_ev.record(stream)
+        api.finom_solve_step(plan, 1, stream=stream)
+        e_ev.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    times = [s.elapsed_time(e) for s, e in evs]
+    total_ms = float(sum(times))
+    done, iters = api.finom_solve_poll(plan, stream=stream)
+    assert not done and iters == args.warmup + args.steps + 1, (done, iters)
+    total_ms = max_over_ranks(total_ms, ws)
+    step_s = total_ms / 1e3 / args.steps
+    value = ws * L * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the fused half step; two launches per step)
+    bytes_per_launch = 0.5 * (8.25 * L + 32.0 * (N + M))
+    peak, peak_kind = peaks()
+    achieved = bytes_per_launch / (step_s / 2) / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the public API with host buffers: copy the inputs in,
+    # plan, solve to the workload's tolerance, read the potentials back
+    e2e = None
+    if args.e2e_steps > 0:
+        hx, hy, hu, hv = (torch.tensor(a, dtype=torch.float64).pin_memory() for a in (pr.x, pr.y, pr.u, pr.v))
+        hf = torch.empty(N, dtype=torch.float64).pin_memory()
+        hg = torch.empty(M, dtype=torch.float64).pin_memory()
+        pts, secs = 0, 0.0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dx, dy, du, dv = (t.to(dev, non_blocking=True) for t in (hx, hy, hu, hv))
+            p2 = api.finom_plan(dx, dy, pr.eps, "f32_log", stream=stream)
+            f, g, res = api.finom_solve(p2, du, dv, pr.tol, 60000, stream=stream)
+            hf.copy_(f, non_blocking=True)
+            hg.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            api.finom_plan_destroy(p2)
+            if k > 0:   # the first call is a warm-up
+                pts += L * res["iters"]
+                secs += dt
+        e2e = {"value": ws * pts / secs, "unit": UNIT, "h2d_bytes_per_step": 8 * (2 * N + 2 * M),
+               "d2h_bytes_per_step": 8 * (N + M), "solve_iters": res["iters"], "converged": res["converged"],
+               "marginal_err": res["marginal_err"], "w1": res["w1"], "seconds_per_solve": secs / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pr)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"1D graded meshes N=M={N} (x=((i+1/2)/N)^2, tanh-stretched y, stretch 3), "
+                                   f"3-Gaussian mixtures, eps=1e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
+                       "N": N, "M": M, "eps": pr.eps, "point_iters_per_step": L,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "finom::k_apply<float,false> (fused half step)",
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    api.finom_plan_destroy(plan)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_finom(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * finom.h -- C ABI of libfinom, a GB300 (sm_103a) implementation of FINOM,
+ * the fast Sinkhorn algorithm for the entropic Wasserstein-1 distance on
+ * non-uniform meshes (Cheng, Liao, Wu, Yang).
+ *
+ * Problem (Sec. 1, eq. w1Definition; Sec. 2.1, eq. regularized problem):
+ * mu = sum_i u_i delta_{x_i} and nu = sum_j v_j delta_{y_j} on sorted meshes,
+ * cost c_ij = |x_i - y_j|, kernel K = exp(-C / eps).  The Sinkhorn iteration
+ * (eq. iteration) needs K psi and K^T phi; FINOM evaluates them in O(N + M)
+ * through the dividing index (Definition, Sec. 2.2) and two first-order
+ * recurrences (eqs. p/q by dynamic programming, Sec. 2.3).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers (cudaMalloc / torch CUDA tensors) on
+ *     the device that was current when the plan was made, unless the name
+ *     says "_host".  The caller owns every array it passes; the library never
+ *     keeps a caller pointer after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it unless stated otherwise.
+ *   - Every call returns a finom_status.  On failure nothing is written to the
+ *     outputs, and finom_last_error() gives a one-line message (per thread).
+ *   - A plan may be used by one host thread / one stream at a time.
+ *   - Coordinates: float64, sorted non-decreasing, finite.  Duplicates and
+ *     ties between x and y are allowed: a tie x_i = y_j belongs to the lower
+ *     block of K (Definition, first bullet: y_zeta <= x_i).
+ *   - Potentials are in cost units: f = eps * log(phi), g = eps * log(psi)
+ *     (-inf where the mass is zero).
+ */
+#ifndef FINOM_H
+#define FINOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FINOM_OK = 0,
+  FINOM_EINVAL = 1,           /* invalid argument: sizes, eps, unsorted or non-finite meshes, bad masses */
+  FINOM_ENOMEM = 2,           /* a device allocation failed */
+  FINOM_ECUDA = 3,            /* a CUDA runtime call failed (message in finom_last_error) */
+  FINOM_EDEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+  FINOM_ENOTSUP = 5           /* the plan's precision or kind does not support the call */
+} finom_status;
+
+typedef enum {
+  FINOM_F64 = 0,      /* float64 throughout (the plain form) */
+  FINOM_F32_LOG = 1   /* float32 log-domain scans with absorbed potentials (Remark
+                         log-domain-stabilization); float64 for the cost <C,Gamma>
+                         and the final marginal-error check */
+} finom_precision;
+
+typedef struct finom_plan_s* finom_plan_t;
+
+typedef struct {
+  double w1;              /* <C, Gamma> of the returned plan, float64 (objective of eq. w1Definition) */
+  double marginal_err;    /* || diag(psi) K^T phi - v ||_1 of the returned potentials, float64 */
+  double marginal_err_loop; /* the same quantity as computed by the loop's own check (plan precision) */
+  double dual;            /* <f, u> + <g, v> */
+  int64_t iters;          /* completed Sinkhorn iterations (the paper's l at loop exit) */
+  int32_t converged;      /* 1 if the loop stopped because its check was <= tol */
+  int32_t status;         /* finom_status of the solve */
+} finom_result;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int finom_version(void);
+
+/* Last error message of the calling host thread ("" if none). */
+const char* finom_last_error(void);
+
+/*
+ * finom_plan -- build the plan for the mesh pair (x, y): the merged order of
+ * the two meshes (ties: y before x), the dividing index zeta of K and zeta^T
+ * of K^T (Definition, Sec. 2.2; Algorithm 1 first step), and the decay
+ * factors between consecutive merged points (the ratio vectors r, r' of the
+ * Theorems on the vector representation of K_L and K_U, eq. ratio, split at
+ * every merged point).
+ *   x: N doubles, y: M doubles (device), sorted non-decreasing and finite.
+ *   N, M >= 1.  eps > 0 and finite.
+ *   prec: FINOM_F64 or FINOM_F32_LOG.
+ *   out: receives the plan handle (owned by the library until finom_plan_destroy).
+ * Synchronous: returns after the plan is built.  Errors: FINOM_EINVAL for
+ * bad sizes/eps or unsorted/non-finite coordinates, FINOM_ENOMEM, FINOM_ECUDA.
+ */
+finom_status finom_plan(const double* x, int64_t N, const double* y, int64_t M, double eps,
+                        finom_precision prec, void* stream, finom_plan_t* out);
+
+/* Release the plan and all device memory it owns.  NULL is accepted. */
+finom_status finom_plan_destroy(finom_plan_t plan);
+
+/* Sizes of a plan (any pointer may be NULL). */
+finom_status finom_plan_info(finom_plan_t plan, int64_t* N, int64_t* M, double* eps,
+                             int32_t* precision);
+
+/*
+ * finom_dividing_index -- copy the dividing indices out (Definition, Sec. 2.2).
+ *   zeta:  N int32 (device), zeta[i] = #{j : y_j <= x_i} in 0..M (the paper's
+ *          zeta(i) for row i of K).  May be NULL.
+ *   zetaT: M int32 (device), zetaT[j] = #{i : x_i <= y_j} in 0..N (the same
+ *          definition applied to K^T).  May be NULL.
+ */
+finom_status finom_dividing_index(finom_plan_t plan, int32_t* zeta, int32_t* zetaT, void* stream);
+
+/*
+ * finom_kv -- out = K v (eq. decompose to p+q: p + q from the forward and the
+ * backward recurrence).  v: M doubles, out: N doubles (device), v >= 0 and
+ * finite (the recurrences run on log-weights in both precisions).
+ * Relative error vs the dense product: <= 1e-12 (F64), <= 1e-5 (F32_LOG) on
+ * entries above 1e-30 of the largest.
+ */
+finom_status finom_kv(finom_plan_t plan, const double* v, double* out, void* stream);
+
+/* finom_ktu -- out = K^T u.  u: N doubles, out: M doubles (device). */
+finom_status finom_ktu(finom_plan_t plan, const double* u, double* out, void* stream);
+
+/*
+ * finom_kv_log -- the stabilised product of Remark log-domain-stabilization:
+ *   out_i = log( sum_j exp((a_i + b_j - |x_i - y_j|) / eps) ),
+ * i.e. log( diag(e^{a/eps}) K diag(e^{b/eps}) 1 ).  a: N doubles, b: M
+ * doubles (absorption vectors, cost units, finite or -inf in b), out: N
+ * doubles (natural log).  For both precisions.
+ */
+finom_status finom_kv_log(finom_plan_t plan, const double* a, const double* b, double* out,
+                          void* stream);
+
+/* finom_ktu_log -- out_j = log( sum_i exp((a_i + b_j - |x_i - y_j|)/eps) ); out: M doubles. */
+finom_status finom_ktu_log(finom_plan_t plan, const double* a, const double* b, double* out,
+                           void* stream);
+
+/*
+ * finom_solve -- Sinkhorn loop of Algorithm 1 (psi first, then phi), started
+ * from phi = 1/N, psi = 1/M, or from warm-start potentials.  Stops at the loop
+ * head when the marginal error || diag(psi) K^T phi - v ||_1 <= tol or after
+ * maxit iterations.
+ *   u: N doubles, v: M doubles (device), >= 0, finite, positive sums; they are
+ *      normalised to sum 1 internally.
+ *   tol >= 0, maxit >= 0.
+ *   f: N doubles, g: M doubles (device, outputs; f, g in cost units).  If
+ *      warm != 0 they are also inputs (warm-start potentials).
+ *   res: host struct, filled on return.
+ * Synchronous (returns when the solve is done).  Non-convergence is not an
+ * error: res->converged = 0, res->iters = maxit.
+ */
+finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, double tol,
+                         int64_t maxit, double* f, double* g, int32_t warm, finom_result* res,
+                         void* stream);
+
+/*
+ * Stepwise form of finom_solve (same loop, driven by the caller):
+ *   finom_solve_begin  normalises u, v, sets phi = 1/N, psi = 1/M (or the
+ *                      warm start f0, g0 when both are non-NULL) and launches
+ *                      iteration 0 on `stream`.  Asynchronous except for the
+ *                      mass validation (one small device->host read).
+ *   finom_solve_step   launches `iterations` more Sinkhorn iterations (two
+ *                      kernels each) on `stream`; asynchronous.  Iterations
+ *                      after the loop has stopped return at once.
+ *   finom_solve_poll   *done = 1 once the loop stopped (check <= tol or maxit);
+ *                      *iters = completed iterations.  Synchronises `stream`.
+ *   finom_solve_end    writes f, g (device, cost units) and res (host) for the
+ *                      state at the loop exit, or after the last completed
+ *                      iteration if the loop is still running.  Synchronous.
+ * Any kernel product or finom_cost on the same plan in between ends the solve.
+ */
+finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double* v, double tol,
+                               int64_t maxit, const double* f0, const double* g0, void* stream);
+finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* stream);
+finom_status finom_solve_poll(finom_plan_t plan, int32_t* done, int64_t* iters, void* stream);
+finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_result* res,
+                             void* stream);
+
+/*
+ * finom_cost -- W1 and marginal error of given potentials, float64:
+ *   w1  = <C, Gamma>, Gamma_ij = exp((f_i + g_j - |x_i - y_j|)/eps)
+ *   err = sum_j | sum_i Gamma_ij - v_j |
+ * u, f: N doubles; v, g: M doubles (device); w1, err: host doubles.
+ * Synchronous.
+ */
+finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, const double* f,
+                        const double* g, double* w1, double* err, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FINOM_H */

@@ -207,7 +207,10 @@ def sinkhorn_log(x, y, u, v, eps, tol, maxit):
 
     Absorption vectors a (x side) and b (y side) carry eps*log(phi) and
     eps*log(psi); after each absorption phi = psi = 1, so each half step is
-    one stabilised product K'^T 1 or K' 1.  Start: phi = 1/N, psi = 1/M.
+    one stabilised product.  The product is evaluated with the column
+    absorption only (row absorption zero) and the row factor e^{b/eps} is
+    applied after, which is the same product and keeps zero masses (-inf
+    potentials) out of the recurrence ratios.  Start: phi = 1/N, psi = 1/M.
     Loop head: marginal error || diag(psi) K^T phi - v ||_1 <= tol or l = maxit.
     Returns (a, b, iters, err)."""
     x = np.asarray(x, dtype=np.float64)
@@ -216,16 +219,17 @@ def sinkhorn_log(x, y, u, v, eps, tol, maxit):
     logu, logv = _log(u), _log(v)
     a = np.full(N, eps * math.log(1.0 / N))
     b = np.full(M, eps * math.log(1.0 / M))
+    zx, zy = np.zeros(N), np.zeros(M)
     it = 0
     while True:
-        # K'^T 1 with rows = y (transposed case): roles of (x, a) and (y, b) swap
-        lt, _, _ = matvec_log(y, x, eps, b, a)
-        err = math.fsum(abs(math.exp(t) - vj) for t, vj in zip(lt, v))
+        # log (K^T phi)_j: rows = y (transposed case), columns absorbed by a
+        q, _, _ = matvec_log(y, x, eps, zy, a)
+        err = math.fsum(abs(math.exp(bj / eps + t) - vj) for bj, t, vj in zip(b, q, v))
         if it >= maxit or err <= tol:
             break
-        b = b + eps * (logv - lt)          # absorb eps*log(psi), psi = v / (K'^T 1)
-        lk, _, _ = matvec_log(x, y, eps, a, b)
-        a = a + eps * (logu - lk)          # absorb eps*log(phi), phi = u / (K' 1)
+        b = eps * (logv - q)               # psi = v / (K^T phi), absorbed
+        qk, _, _ = matvec_log(x, y, eps, zx, b)
+        a = eps * (logu - qk)              # phi = u / (K psi), absorbed
         it += 1
     return a, b, it, err
 

@@ -1,0 +1,100 @@
+"""ctypes loader of the plain-C serial FINOM oracle (test infrastructure).
+
+Compiles ``oracle/finom_serial.c`` with gcc (``-O2 -fPIC -shared``, IEEE
+semantics kept) into ``oracle/_build/libfinomref.so`` on first use.  Only
+``tests/``, ``__graft_entry__`` and ``bench.py`` may import this module.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "finom_serial.c")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libfinomref.so")
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler for the serial oracle")
+    tmp = LIB + f".{os.getpid()}.tmp"
+    subprocess.run([cc, "-O2", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"], check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        I64, D = ctypes.c_int64, ctypes.c_double
+        L.finom_ref_dividing_index.argtypes = [_dp, I64, _dp, I64, _ip]
+        L.finom_ref_dividing_index.restype = None
+        L.finom_ref_log_apply.argtypes = [_dp, I64, _dp, I64, D, _dp, _dp, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+        L.finom_ref_log_apply.restype = None
+        L.finom_ref_marginal_error.argtypes = [_dp, I64, _dp, I64, D, _dp, _dp, _dp]
+        L.finom_ref_marginal_error.restype = D
+        L.finom_ref_cost.argtypes = [_dp, I64, _dp, I64, D, _dp, _dp]
+        L.finom_ref_cost.restype = D
+        L.finom_ref_sinkhorn.argtypes = [_dp, I64, _dp, I64, _dp, _dp, D, D, I64, ctypes.c_int,
+                                         _dp, _dp, ctypes.POINTER(D)]
+        L.finom_ref_sinkhorn.restype = I64
+        _lib = L
+    return _lib
+
+
+def _a(v):
+    return np.ascontiguousarray(v, dtype=np.float64)
+
+
+def dividing_index(x, y):
+    x, y = _a(x), _a(y)
+    z = np.zeros(len(x), dtype=np.int64)
+    lib().finom_ref_dividing_index(x, len(x), y, len(y), z)
+    return z
+
+
+def log_apply(x, y, eps, b, with_cost=False):
+    """log sum_j exp((b_j - |x_i - y_j|)/eps) per row i (and the cost-weighted version)."""
+    x, y, b = _a(x), _a(y), _a(b)
+    out = np.empty(len(x))
+    cost = np.empty(len(x)) if with_cost else None
+    lib().finom_ref_log_apply(x, len(x), y, len(y), float(eps), b, out, None, None,
+                              cost.ctypes.data if with_cost else None)
+    return (out, cost) if with_cost else out
+
+
+def marginal_error(x, y, eps, f, g, v):
+    x, y = _a(x), _a(y)
+    return lib().finom_ref_marginal_error(x, len(x), y, len(y), float(eps), _a(f), _a(g), _a(v))
+
+
+def cost(x, y, eps, f, g):
+    x, y = _a(x), _a(y)
+    return lib().finom_ref_cost(x, len(x), y, len(y), float(eps), _a(f), _a(g))
+
+
+def sinkhorn(x, y, u, v, eps, tol, maxit, f0=None, g0=None):
+    """Algorithm 1 (absorbed log arithmetic); returns (f, g, iters, err)."""
+    x, y, u, v = _a(x), _a(y), _a(u), _a(v)
+    warm = f0 is not None and g0 is not None
+    f = _a(f0).copy() if warm else np.empty(len(x))
+    g = _a(g0).copy() if warm else np.empty(len(y))
+    err = ctypes.c_double()
+    it = lib().finom_ref_sinkhorn(x, len(x), y, len(y), u, v, float(eps), float(tol), int(maxit),
+                                  1 if warm else 0, f, g, ctypes.byref(err))
+    return f, g, int(it), err.value

@@ -1,0 +1,256 @@
+"""Thin Python binding of libfinom (include/finom.h), same names as the C ABI.
+
+Argument marshalling only: device arrays are torch CUDA tensors (float64,
+contiguous) passed as raw pointers; every computation runs in the CUDA
+library.  There is no CPU fallback: if libfinom.so cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfinom.so")
+
+FINOM_OK, FINOM_EINVAL, FINOM_ENOMEM, FINOM_ECUDA, FINOM_EDEVICE_TIMEOUT, FINOM_ENOTSUP = range(6)
+F64, F32_LOG = 0, 1
+_PREC = {"f64": F64, "fp64": F64, "float64": F64, F64: F64,
+         "f32_log": F32_LOG, "fp32_log": F32_LOG, "f32": F32_LOG, F32_LOG: F32_LOG}
+
+
+class FinomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"finom status {status}: {msg}")
+        self.status = status
+
+
+class FinomResult(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_double), ("marginal_err", ctypes.c_double),
+                ("marginal_err_loop", ctypes.c_double), ("dual", ctypes.c_double),
+                ("iters", ctypes.c_int64), ("converged", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+
+_SIGS = {
+    "finom_version": ([], ctypes.c_int),
+    "finom_last_error": ([], ctypes.c_char_p),
+    "finom_plan": ([_P, _I64, _P, _I64, _D, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "finom_plan_destroy": ([_P], ctypes.c_int),
+    "finom_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_D),
+                         ctypes.POINTER(_I32)], ctypes.c_int),
+    "finom_dividing_index": ([_P, _P, _P, _P], ctypes.c_int),
+    "finom_kv": ([_P, _P, _P, _P], ctypes.c_int),
+    "finom_ktu": ([_P, _P, _P, _P], ctypes.c_int),
+    "finom_kv_log": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_ktu_log": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_solve": ([_P, _P, _P, _D, _I64, _P, _P, _I32, ctypes.POINTER(FinomResult), _P], ctypes.c_int),
+    "finom_solve_begin": ([_P, _P, _P, _D, _I64, _P, _P, _P], ctypes.c_int),
+    "finom_solve_step": ([_P, _I64, _P], ctypes.c_int),
+    "finom_solve_poll": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), _P], ctypes.c_int),
+    "finom_solve_end": ([_P, _P, _P, ctypes.POINTER(FinomResult), _P], ctypes.c_int),
+    "finom_cost": ([_P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], ctypes.c_int),
+}
+
+
+def load(path: str | None = None):
+    """Load libfinom.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    p = path or LIB_PATH
+    if path is None and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(p):
+        raise FinomError(-1, f"libfinom.so not found at {p}; run paper_2605_26659_gb300/build.py")
+    lib = ctypes.CDLL(p)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != FINOM_OK:
+        raise FinomError(rc, _lib.finom_last_error().decode())
+
+
+def _dev(t, n=None, dtype=None, name="array"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Plan:
+    handle: ctypes.c_void_p
+    N: int
+    M: int
+    eps: float
+    precision: int
+    device: int
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.finom_plan_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def finom_version():
+    return load().finom_version()
+
+
+def finom_plan(x, y, eps, precision="f32_log", stream=None) -> Plan:
+    import torch
+    load()
+    N, M = x.numel(), y.numel()
+    h = ctypes.c_void_p()
+    _check(_lib.finom_plan(_dev(x, N, torch.float64, "x"), N, _dev(y, M, torch.float64, "y"), M,
+                           float(eps), _PREC[precision], _stream(stream), ctypes.byref(h)))
+    return Plan(h, N, M, float(eps), _PREC[precision], x.device.index or 0)
+
+
+def finom_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(_lib.finom_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def finom_plan_info(plan: Plan):
+    n, m, e, p = _I64(), _I64(), _D(), _I32()
+    _check(_lib.finom_plan_info(plan.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), ctypes.byref(p)))
+    return n.value, m.value, e.value, p.value
+
+
+def finom_dividing_index(plan: Plan, stream=None):
+    import torch
+    dev = torch.device("cuda", plan.device)
+    z = torch.empty(plan.N, dtype=torch.int32, device=dev)
+    zt = torch.empty(plan.M, dtype=torch.int32, device=dev)
+    _check(_lib.finom_dividing_index(plan.handle, _dev(z), _dev(zt), _stream(stream)))
+    return z, zt
+
+
+def _out(n, plan, out):
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", plan.device))
+    return out
+
+
+def finom_kv(plan: Plan, v, out=None, stream=None):
+    import torch
+    out = _out(plan.N, plan, out)
+    _check(_lib.finom_kv(plan.handle, _dev(v, plan.M, torch.float64, "v"), _dev(out, plan.N), _stream(stream)))
+    return out
+
+
+def finom_ktu(plan: Plan, u, out=None, stream=None):
+    import torch
+    out = _out(plan.M, plan, out)
+    _check(_lib.finom_ktu(plan.handle, _dev(u, plan.N, torch.float64, "u"), _dev(out, plan.M), _stream(stream)))
+    return out
+
+
+def finom_kv_log(plan: Plan, a, b, out=None, stream=None):
+    import torch
+    out = _out(plan.N, plan, out)
+    _check(_lib.finom_kv_log(plan.handle, _dev(a, plan.N, torch.float64, "a"),
+                             _dev(b, plan.M, torch.float64, "b"), _dev(out, plan.N), _stream(stream)))
+    return out
+
+
+def finom_ktu_log(plan: Plan, a, b, out=None, stream=None):
+    import torch
+    out = _out(plan.M, plan, out)
+    _check(_lib.finom_ktu_log(plan.handle, _dev(a, plan.N, torch.float64, "a"),
+                              _dev(b, plan.M, torch.float64, "b"), _dev(out, plan.M), _stream(stream)))
+    return out
+
+
+def finom_solve(plan: Plan, u, v, tol, maxit, f=None, g=None, warm=False, stream=None):
+    """Run the Sinkhorn loop; returns (f, g, result dict)."""
+    import torch
+    dev = torch.device("cuda", plan.device)
+    if f is None:
+        f = torch.empty(plan.N, dtype=torch.float64, device=dev)
+    if g is None:
+        g = torch.empty(plan.M, dtype=torch.float64, device=dev)
+    res = FinomResult()
+    _check(_lib.finom_solve(plan.handle, _dev(u, plan.N, torch.float64, "u"), _dev(v, plan.M, torch.float64, "v"),
+                            float(tol), int(maxit), _dev(f, plan.N, torch.float64, "f"),
+                            _dev(g, plan.M, torch.float64, "g"), 1 if warm else 0, ctypes.byref(res),
+                            _stream(stream)))
+    return f, g, res.as_dict()
+
+
+def finom_solve_begin(plan: Plan, u, v, tol, maxit, f0=None, g0=None, stream=None):
+    import torch
+    fp = _dev(f0, plan.N, torch.float64, "f0") if f0 is not None else None
+    gp = _dev(g0, plan.M, torch.float64, "g0") if g0 is not None else None
+    _check(_lib.finom_solve_begin(plan.handle, _dev(u, plan.N, torch.float64, "u"),
+                                  _dev(v, plan.M, torch.float64, "v"), float(tol), int(maxit), fp, gp,
+                                  _stream(stream)))
+
+
+def finom_solve_step(plan: Plan, iterations, stream=None):
+    _check(_lib.finom_solve_step(plan.handle, int(iterations), _stream(stream)))
+
+
+def finom_solve_poll(plan: Plan, stream=None):
+    d, it = _I32(), _I64()
+    _check(_lib.finom_solve_poll(plan.handle, ctypes.byref(d), ctypes.byref(it), _stream(stream)))
+    return bool(d.value), it.value
+
+
+def finom_solve_end(plan: Plan, f=None, g=None, stream=None):
+    import torch
+    dev = torch.device("cuda", plan.device)
+    if f is None:
+        f = torch.empty(plan.N, dtype=torch.float64, device=dev)
+    if g is None:
+        g = torch.empty(plan.M, dtype=torch.float64, device=dev)
+    res = FinomResult()
+    _check(_lib.finom_solve_end(plan.handle, _dev(f, plan.N), _dev(g, plan.M), ctypes.byref(res), _stream(stream)))
+    return f, g, res.as_dict()
+
+
+def finom_cost(plan: Plan, u, v, f, g, stream=None):
+    import torch
+    w1, err = _D(), _D()
+    _check(_lib.finom_cost(plan.handle, _dev(u, plan.N, torch.float64, "u"), _dev(v, plan.M, torch.float64, "v"),
+                           _dev(f, plan.N, torch.float64, "f"), _dev(g, plan.M, torch.float64, "g"),
+                           ctypes.byref(w1), ctypes.byref(err), _stream(stream)))
+    return w1.value, err.value

@@ -1,0 +1,596 @@
+// C ABI of libfinom: argument checking, plan lifetime, kernel products and
+// the Sinkhorn loop (Algorithm 1) driven from the host with CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "apply.cuh"
+#include "finom_internal.h"
+
+namespace finom {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& m) { g_err = m; }
+
+finom_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FINOM_ENOMEM : FINOM_ECUDA;
+}
+
+template <class R>
+finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s);
+template <class R>
+void conv_weights_log(const double*, int64_t, double, void*, void*, cudaStream_t);
+template <class R>
+void conv_weights_lin(const double*, int64_t, void*, void*, cudaStream_t);
+template <class R>
+void conv_pot_scale(const double*, int64_t, double, void*, cudaStream_t);
+template <class R>
+void fill_pot(void*, int64_t, double, cudaStream_t);
+template <class R>
+void fill_mass(void*, int64_t, double, cudaStream_t);
+template <class R>
+void conv_pot_from_f(const double*, const double*, int64_t, double, void*, cudaStream_t);
+template <class R>
+void conv_f_from_pot(const void*, const double*, int64_t, double, double*, double*, cudaStream_t);
+template <class R>
+finom_status normalise_masses(const double*, int64_t, void*, double*, double*, int*, double*,
+                              cudaStream_t);
+void fill_d(double*, int64_t, double, cudaStream_t);
+void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
+
+namespace {
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class R>
+constexpr size_t pot_size() { return sizeof(typename Tr<R>::Pot); }
+template <class R>
+constexpr size_t mass_size() { return sizeof(typename Tr<R>::Mass); }
+
+template <class R>
+finom_status ensure_state(finom_plan_s* p) {
+  SolveState& st = p->st;
+  if (st.ready) return FINOM_OK;
+  const int64_t N = p->N, M = p->M, C = p->C, NM = std::max(N, M);
+  for (int q = 0; q < 2; ++q) {
+    FINOM_CUDA(cudaMalloc(&st.px[q], pot_size<R>() * N));
+    FINOM_CUDA(cudaMalloc(&st.py[q], pot_size<R>() * M));
+  }
+  FINOM_CUDA(cudaMalloc(&st.mu, mass_size<R>() * N));
+  FINOM_CUDA(cudaMalloc(&st.nu, mass_size<R>() * M));
+  FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * N));
+  FINOM_CUDA(cudaMalloc(&st.nu64, sizeof(double) * M));
+  FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * N));
+  FINOM_CUDA(cudaMalloc(&st.ty, sizeof(double) * M));
+  FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * 6 * C));
+  FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * 4 * C));
+  FINOM_CUDA(cudaMalloc(&st.part, sizeof(double) * C));
+  FINOM_CUDA(cudaMalloc(&st.scal, sizeof(double) * 520));
+  FINOM_CUDA(cudaMalloc(&st.ctrl, sizeof(int32_t) * 8));
+  FINOM_CUDA(cudaMalloc(&st.bad, sizeof(int)));
+  FINOM_CUDA(cudaMalloc(&st.qo, pot_size<R>() * NM));
+  FINOM_CUDA(cudaMalloc(&st.qom, mass_size<R>() * NM));
+  FINOM_CUDA(cudaMalloc(&st.qw, pot_size<R>() * NM));
+  FINOM_CUDA(cudaMalloc(&st.qwm, mass_size<R>() * NM));
+  FINOM_CUDA(cudaMemset(st.ctrl, 0, sizeof(int32_t) * 8));
+  FINOM_CUDA(cudaMemset(st.scal, 0, sizeof(double) * 520));
+  FINOM_CUDA(cudaMemset(st.carries, 0, sizeof(R) * 4 * C));
+  FINOM_CUDA(cudaMemset(st.qom, 0, mass_size<R>() * NM));
+  FINOM_CUDA(cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking));
+  st.ready = true;
+  return FINOM_OK;
+}
+
+void free_state(finom_plan_s* p) {
+  SolveState& st = p->st;
+  if (st.body) cudaGraphExecDestroy(st.body);
+  for (int q = 0; q < 2; ++q) {
+    cudaFree(st.px[q]);
+    cudaFree(st.py[q]);
+  }
+  void* bufs[] = {st.mu, st.nu, st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part,
+                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm};
+  for (void* b : bufs) cudaFree(b);
+  if (st.stream) cudaStreamDestroy(st.stream);
+  st = SolveState();
+}
+
+template <class R>
+ApplyArgs<R> base_args(finom_plan_s* p) {
+  ApplyArgs<R> a{};
+  a.tbits = p->tbits;
+  a.gap = (const R*)p->gap;
+  a.tile_x0 = p->tile_x0;
+  a.L = p->L;
+  a.C = (int)p->C;
+  a.agg_out = (R*)p->st.aggs;
+  a.carry_in = (const R*)p->st.carries;
+  a.carry_out = (R*)p->st.carries;
+  a.part = p->st.part;
+  a.scal = p->st.scal;
+  a.ctrl = p->st.ctrl;
+  return a;
+}
+
+// One kernel product: frames qo on the O side, weights (qw, qwm) on the W side.
+template <class R>
+finom_status product(finom_plan_s* p, int o_is_x, double* out, int outflag, cudaStream_t s) {
+  using Pot = typename Tr<R>::Pot;
+  using Mass = typename Tr<R>::Mass;
+  SolveState& st = p->st;
+  st.active = false;   // a product overwrites the loop's scan scratch
+  ApplyArgs<R> a = base_args<R>(p);
+  a.o_is_x = o_is_x;
+  a.pO = (const Pot*)st.qo;
+  a.mO = (const Mass*)st.qom;
+  a.pW = (const Pot*)st.qw;
+  a.mW = (const Mass*)st.qwm;
+  a.out = out;
+  a.flags = 0;
+  finom_status rc = launch_apply<R>(a, true, s);
+  if (rc != FINOM_OK) return rc;
+  a.flags = outflag;
+  return launch_apply<R>(a, false, s);
+}
+
+template <class R>
+ApplyArgs<R> half_args(finom_plan_s* p, bool o_is_x, int q) {
+  using Pot = typename Tr<R>::Pot;
+  using Mass = typename Tr<R>::Mass;
+  SolveState& st = p->st;
+  ApplyArgs<R> a = base_args<R>(p);
+  a.tol = st.tol;
+  a.maxit = st.maxit;
+  if (!o_is_x) {   // psi <- v / (K^T phi): outputs on y, weights on x
+    a.o_is_x = 0;
+    a.pO = (const Pot*)st.py[q];
+    a.mO = (const Mass*)st.nu;
+    a.pO_out = (Pot*)st.py[1 - q];
+    a.pW = (const Pot*)st.px[q];
+    a.mW = (const Mass*)st.mu;
+    a.flags = F_OUT_POT | F_ERR | F_NEXT | F_CHECK_DONE;
+  } else {         // phi <- u / (K psi): outputs on x, weights on y
+    a.o_is_x = 1;
+    a.pO = (const Pot*)st.px[q];
+    a.mO = (const Mass*)st.mu;
+    a.pO_out = (Pot*)st.px[1 - q];
+    a.pW = (const Pot*)st.py[1 - q];
+    a.mW = (const Mass*)st.nu;
+    a.flags = F_OUT_POT | F_NEXT | F_ITER_END | F_CHECK_DONE;
+  }
+  return a;
+}
+
+// one Sinkhorn iteration with parity q (iteration l has q = l % 2)
+template <class R>
+finom_status launch_iteration(finom_plan_s* p, int q, cudaStream_t s) {
+  finom_status rc = launch_apply<R>(half_args<R>(p, false, q), false, s);
+  if (rc != FINOM_OK) return rc;
+  return launch_apply<R>(half_args<R>(p, true, q), false, s);
+}
+
+template <class R>
+finom_status build_body(finom_plan_s* p) {
+  SolveState& st = p->st;
+  if (st.body) {
+    cudaGraphExecDestroy(st.body);
+    st.body = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  FINOM_CUDA(cudaStreamBeginCapture(st.stream, cudaStreamCaptureModeThreadLocal));
+  finom_status rc = launch_iteration<R>(p, 1, st.stream);
+  if (rc == FINOM_OK) rc = launch_iteration<R>(p, 0, st.stream);
+  cudaError_t e = cudaStreamEndCapture(st.stream, &g);
+  if (rc != FINOM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&st.body, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return FINOM_OK;
+}
+
+template <class R>
+finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                         const double* f0, const double* g0, cudaStream_t s) {
+  finom_status rc = ensure_state<R>(p);
+  if (rc != FINOM_OK) return rc;
+  SolveState& st = p->st;
+  const int64_t N = p->N, M = p->M;
+  rc = normalise_masses<R>(u, N, st.mu, st.mu64, st.tx, st.bad, nullptr, s);
+  if (rc != FINOM_OK) return rc;
+  rc = normalise_masses<R>(v, M, st.nu, st.nu64, st.ty, st.bad, nullptr, s);
+  if (rc != FINOM_OK) return rc;
+  const double scale = 1.0 / (p->eps * kLn2);
+  st.warm = (f0 != nullptr && g0 != nullptr);
+  if (st.warm) {
+    conv_pot_from_f<R>(f0, st.mu64, N, scale, st.px[0], s);
+    conv_pot_from_f<R>(g0, st.nu64, M, scale, st.py[0], s);
+  } else {
+    fill_pot<R>(st.px[0], N, 0.0, s);
+    fill_pot<R>(st.py[0], M, 0.0, s);
+  }
+  FINOM_CUDA(cudaMemsetAsync(st.ctrl, 0, sizeof(int32_t) * 8, s));
+  FINOM_CUDA(cudaMemsetAsync(st.scal, 0, sizeof(double) * 8, s));
+  st.tol = tol;
+  st.maxit = maxit;
+  st.launched = 0;
+  st.active = true;
+  // iteration 0: the first K^T phi uses phi = 1/N and checks against psi = 1/M
+  ApplyArgs<R> a0 = half_args<R>(p, false, 0);
+  if (!st.warm) {
+    a0.w_uniform = (R)(1.0 / (double)N);
+    a0.o_scale = (R)(1.0 / (double)M);
+  }
+  ApplyArgs<R> agg = a0;
+  agg.flags = 0;
+  rc = launch_apply<R>(agg, true, s);
+  if (rc != FINOM_OK) return rc;
+  if (maxit == 0) {   // only the loop-head check of l = 0
+    a0.flags = F_ERR;
+    return launch_apply<R>(a0, false, s);
+  }
+  rc = launch_apply<R>(a0, false, s);
+  if (rc != FINOM_OK) return rc;
+  rc = launch_apply<R>(half_args<R>(p, true, 0), false, s);
+  if (rc != FINOM_OK) return rc;
+  st.launched = 1;
+  return FINOM_OK;
+}
+
+template <class R>
+finom_status solve_step(finom_plan_s* p, int64_t iters, cudaStream_t s) {
+  SolveState& st = p->st;
+  for (int64_t k = 0; k < iters; ++k) {
+    finom_status rc = launch_iteration<R>(p, (int)(st.launched & 1), s);
+    if (rc != FINOM_OK) return rc;
+    ++st.launched;
+  }
+  return FINOM_OK;
+}
+
+finom_status solve_poll(finom_plan_s* p, cudaStream_t s, int32_t* done, int64_t* iters) {
+  int32_t h[8];
+  FINOM_CUDA(cudaMemcpyAsync(h, p->st.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FINOM_CUDA(cudaStreamSynchronize(s));
+  if (done) *done = h[1];
+  if (iters) *iters = h[1] ? h[3] : h[2];
+  return FINOM_OK;
+}
+
+template <class R>
+finom_status solve_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s) {
+  SolveState& st = p->st;
+  const int64_t N = p->N, M = p->M;
+  int32_t h[8];
+  double loop_err = 0.0;
+  FINOM_CUDA(cudaMemcpyAsync(h, st.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+  FINOM_CUDA(cudaMemcpyAsync(&loop_err, st.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FINOM_CUDA(cudaStreamSynchronize(s));
+  const bool done = h[1] != 0;
+  int64_t iters = done ? h[3] : h[2];
+  int32_t converged = h[4];
+  if (st.maxit == 0) iters = 0;
+  const double eps_ln2 = p->eps * kLn2;
+  double err64 = 0.0, w1 = 0.0;
+  if (iters == 0 && !st.warm) {
+    // the paper's start phi = 1/N, psi = 1/M; its marginal error is the one
+    // the loop measured at the first loop head (plan precision)
+    fill_d(f, N, p->eps * std::log(1.0 / (double)N), s);
+    fill_d(g, M, p->eps * std::log(1.0 / (double)M), s);
+    fill_d(st.tx, N, 0.0, s);
+    fill_d(st.ty, M, 0.0, s);
+    double* uu = nullptr;
+    FINOM_CUDA(cudaMallocAsync(&uu, sizeof(double) * (N + M), s));
+    fill_d(uu, N, 1.0 / (double)N, s);
+    fill_d(uu + N, M, 1.0 / (double)M, s);
+    finom_status rc = cost64(p, st.tx, st.ty, uu, uu + N, &err64, &w1, s);
+    cudaFreeAsync(uu, s);
+    if (rc != FINOM_OK) return rc;
+    err64 = loop_err;
+  } else {
+    const int q = (int)(iters & 1);
+    conv_f_from_pot<R>(st.px[q], st.mu64, N, eps_ln2, f, st.tx, s);
+    conv_f_from_pot<R>(st.py[q], st.nu64, M, eps_ln2, g, st.ty, s);
+    finom_status rc = cost64(p, st.tx, st.ty, st.mu64, st.nu64, &err64, &w1, s);
+    if (rc != FINOM_OK) return rc;
+  }
+  double* d2 = st.scal + 16;
+  dot_pos(st.mu64, f, N, d2, s);
+  dot_pos(st.nu64, g, M, d2 + 1, s);
+  double hd[2];
+  FINOM_CUDA(cudaMemcpyAsync(hd, d2, sizeof(hd), cudaMemcpyDeviceToHost, s));
+  FINOM_CUDA(cudaStreamSynchronize(s));
+  if (res) {
+    res->w1 = w1;
+    res->marginal_err = err64;
+    res->marginal_err_loop = loop_err;
+    res->dual = hd[0] + hd[1];
+    res->iters = iters;
+    res->converged = (converged || err64 <= st.tol) ? 1 : 0;
+    res->status = FINOM_OK;
+  }
+  st.active = false;
+  return FINOM_OK;
+}
+
+template <class R>
+finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, double tol,
+                            int64_t maxit, double* f, double* g, int32_t warm, finom_result* res,
+                            cudaStream_t us) {
+  FINOM_CUDA(cudaStreamSynchronize(us));   // inputs are produced on the caller's stream
+  finom_status rc = ensure_state<R>(p);
+  if (rc != FINOM_OK) return rc;
+  SolveState& st = p->st;
+  cudaStream_t s = st.stream;
+  rc = solve_begin<R>(p, u, v, tol, maxit, warm ? f : nullptr, warm ? g : nullptr, s);
+  if (rc != FINOM_OK) return rc;
+  if (maxit > 0) {
+    rc = build_body<R>(p);
+    if (rc != FINOM_OK) return rc;
+    int64_t bodies = 1;
+    for (;;) {
+      int32_t done = 0;
+      rc = solve_poll(p, s, &done, nullptr);
+      if (rc != FINOM_OK) return rc;
+      if (done) break;
+      if (st.launched & 1) {
+        for (int64_t b = 0; b < bodies; ++b) FINOM_CUDA(cudaGraphLaunch(st.body, s));
+        st.launched += 2 * bodies;
+      } else {
+        rc = solve_step<R>(p, 1, s);
+        if (rc != FINOM_OK) return rc;
+      }
+      bodies = std::min<int64_t>(bodies * 2, 64);
+    }
+  }
+  rc = solve_end<R>(p, f, g, res, s);
+  if (rc != FINOM_OK) return rc;
+  return FINOM_OK;
+}
+
+bool bad_plan(finom_plan_t p) {
+  if (!p) {
+    set_error("null plan");
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+}  // namespace finom
+
+using namespace finom;
+
+namespace {
+
+template <class R>
+finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double* a, const double* b,
+                     double* out, cudaStream_t s) {
+  finom_status rc = ensure_state<R>(p);
+  if (rc != FINOM_OK) return rc;
+  SolveState& st = p->st;
+  const int64_t N = p->N, M = p->M;
+  const int64_t nO = transpose ? M : N, nW = transpose ? N : M;
+  const double scale = 1.0 / (p->eps * kLn2);
+  if (logmode) {
+    // frames: the O side's absorption vector; weights: the W side's
+    const double* ao = transpose ? b : a;
+    const double* bw = transpose ? a : b;
+    conv_pot_scale<R>(ao, nO, scale, st.qo, s);
+    conv_weights_log<R>(bw, nW, scale, st.qw, st.qwm, s);
+  } else {
+    fill_pot<R>(st.qo, nO, 0.0, s);
+    conv_weights_lin<R>(b, nW, st.qw, st.qwm, s);
+  }
+  return product<R>(p, transpose ? 0 : 1, out, logmode ? F_OUT_LOG : F_OUT_LIN, s);
+}
+
+finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const double* a,
+                         const double* b, double* out, void* stream) {
+  if (bad_plan(p)) return FINOM_EINVAL;
+  if (!out || (!logmode && !b) || (logmode && (!a || !b))) {
+    set_error("kernel product: null argument");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return p->prec == FINOM_F32_LOG ? kv_impl<float>(p, transpose, logmode, a, b, out, s)
+                                  : kv_impl<double>(p, transpose, logmode, a, b, out, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int finom_version(void) { return 100; }
+
+const char* finom_last_error(void) { return g_err.c_str(); }
+
+finom_status finom_plan(const double* x, int64_t N, const double* y, int64_t M, double eps,
+                        finom_precision prec, void* stream, finom_plan_t* out) {
+  if (!out) {
+    set_error("finom_plan: out is NULL");
+    return FINOM_EINVAL;
+  }
+  *out = nullptr;
+  if (!x || !y || N < 1 || M < 1 || !(eps > 0.0) || !std::isfinite(eps) ||
+      (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
+    set_error("finom_plan: need x, y non-null, N, M >= 1, eps > 0 finite, known precision");
+    return FINOM_EINVAL;
+  }
+  if (N + M > (int64_t)INT32_MAX - 2 * kTile) {
+    set_error("finom_plan: N + M too large");
+    return FINOM_EINVAL;
+  }
+  finom_plan_s* p = new (std::nothrow) finom_plan_s();
+  if (!p) return FINOM_ENOMEM;
+  p->N = N;
+  p->M = M;
+  p->eps = eps;
+  p->prec = prec;
+  cudaGetDevice(&p->device);
+  finom_status rc = build_plan(p, x, y, (cudaStream_t)stream);
+  if (rc != FINOM_OK) {
+    free_plan(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_destroy(finom_plan_t plan) {
+  if (!plan) return FINOM_OK;
+  DeviceGuard dg(plan->device);
+  cudaDeviceSynchronize();
+  free_state(plan);
+  free_plan(plan);
+  delete plan;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_info(finom_plan_t plan, int64_t* N, int64_t* M, double* eps,
+                             int32_t* precision) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (N) *N = plan->N;
+  if (M) *M = plan->M;
+  if (eps) *eps = plan->eps;
+  if (precision) *precision = (int32_t)plan->prec;
+  return FINOM_OK;
+}
+
+finom_status finom_dividing_index(finom_plan_t plan, int32_t* zeta, int32_t* zetaT, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (zeta) FINOM_CUDA(cudaMemcpyAsync(zeta, plan->zeta, sizeof(int32_t) * plan->N, cudaMemcpyDeviceToDevice, s));
+  if (zetaT) FINOM_CUDA(cudaMemcpyAsync(zetaT, plan->zetaT, sizeof(int32_t) * plan->M, cudaMemcpyDeviceToDevice, s));
+  return FINOM_OK;
+}
+
+
+finom_status finom_kv(finom_plan_t plan, const double* v, double* out, void* stream) {
+  return kv_dispatch(plan, false, false, nullptr, v, out, stream);
+}
+
+finom_status finom_ktu(finom_plan_t plan, const double* u, double* out, void* stream) {
+  return kv_dispatch(plan, true, false, nullptr, u, out, stream);
+}
+
+finom_status finom_kv_log(finom_plan_t plan, const double* a, const double* b, double* out,
+                          void* stream) {
+  return kv_dispatch(plan, false, true, a, b, out, stream);
+}
+
+finom_status finom_ktu_log(finom_plan_t plan, const double* a, const double* b, double* out,
+                           void* stream) {
+  return kv_dispatch(plan, true, true, a, b, out, stream);
+}
+
+finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, double tol,
+                         int64_t maxit, double* f, double* g, int32_t warm, finom_result* res,
+                         void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!u || !v || !f || !g || !(tol >= 0.0) || maxit < 0) {
+    set_error("finom_solve: need u, v, f, g non-null, tol >= 0, maxit >= 0");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  finom_status rc = plan->prec == FINOM_F32_LOG
+                        ? solve_blocking<float>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream)
+                        : solve_blocking<double>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
+  if (res && rc != FINOM_OK) res->status = rc;
+  return rc;
+}
+
+finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double* v, double tol,
+                               int64_t maxit, const double* f0, const double* g0, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!u || !v || !(tol >= 0.0) || maxit < 0) {
+    set_error("finom_solve_begin: need u, v non-null, tol >= 0, maxit >= 0");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return plan->prec == FINOM_F32_LOG ? solve_begin<float>(plan, u, v, tol, maxit, f0, g0, s)
+                                     : solve_begin<double>(plan, u, v, tol, maxit, f0, g0, s);
+}
+
+finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!plan->st.active || iterations < 0) {
+    set_error("finom_solve_step: no solve in progress (finom_solve_begin first) or negative count");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return plan->prec == FINOM_F32_LOG ? solve_step<float>(plan, iterations, s)
+                                     : solve_step<double>(plan, iterations, s);
+}
+
+finom_status finom_solve_poll(finom_plan_t plan, int32_t* done, int64_t* iters, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!plan->st.ready) {
+    set_error("finom_solve_poll: no solve state");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  return solve_poll(plan, (cudaStream_t)stream, done, iters);
+}
+
+finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_result* res,
+                             void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!plan->st.active || !f || !g) {
+    set_error("finom_solve_end: no solve in progress or null output");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  return plan->prec == FINOM_F32_LOG ? solve_end<float>(plan, f, g, res, s)
+                                     : solve_end<double>(plan, f, g, res, s);
+}
+
+finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, const double* f,
+                        const double* g, double* w1, double* err, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!u || !v || !f || !g || !w1 || !err) {
+    set_error("finom_cost: null argument");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  finom_status rc = plan->prec == FINOM_F32_LOG ? ensure_state<float>(plan) : ensure_state<double>(plan);
+  if (rc != FINOM_OK) return rc;
+  SolveState& st = plan->st;
+  const double scale = 1.0 / (plan->eps * kLn2);
+  // masses as given (not renormalised) and smooth potentials P = f/(eps ln2) - log2 u
+  FINOM_CUDA(cudaMemcpyAsync(st.mu64, u, sizeof(double) * plan->N, cudaMemcpyDeviceToDevice, s));
+  FINOM_CUDA(cudaMemcpyAsync(st.nu64, v, sizeof(double) * plan->M, cudaMemcpyDeviceToDevice, s));
+  conv_pot_from_f<double>(f, st.mu64, plan->N, scale, st.tx, s);
+  conv_pot_from_f<double>(g, st.nu64, plan->M, scale, st.ty, s);
+  st.active = false;
+  return cost64(plan, st.tx, st.ty, st.mu64, st.nu64, err, w1, s);
+}
+
+}  // extern "C"

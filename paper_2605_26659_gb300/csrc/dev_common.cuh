@@ -1,0 +1,217 @@
+// Device-side building blocks of the FINOM scans.
+//
+// Representation.  A Sinkhorn half step needs, at every output point k of one
+// mesh (the "O" side), the stabilised sum
+//     S_k = sum_m  2^{ c_k + P_m + log2 w_m - G(k, m) }
+// over the points m of the other mesh (the "W" side), where c is a reference
+// ("frame") potential, P the absorbed potential of Remark
+// log-domain-stabilization, w the mass and G = |z_k - z_m| / (eps ln 2) the
+// cost in bits.  In the merged order of both meshes the lower and upper block
+// sums (eqs. p/q by dynamic programming) become a forward and a backward
+// first-order recurrence
+//     fwd:  L_k = (L_{k-1} + A_k) (+) B_k          A_k  =  (c_k - c_{k-1}) - g_k
+//     bwd:  R_{k-1} = (R_k (+) B_k) + A'_k          A'_k = -(c_k - c_{k-1}) - g_k
+// with g_k the gap to the previous merged point in bits, B_k the log2 weight
+// of a W point and (+) the log-sum.  Log-sums are carried as LS {m, s}
+// (value s * 2^m, s in [1, 2)) so that adding one term costs one ex2.
+// The recurrence maps compose associatively: Agg {D, m, s} is the map
+// L -> (L + D) (+) (m, s).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace finom {
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <class R>
+struct Tr;
+
+// float path: potentials as unevaluated sums hi + lo of two floats
+template <>
+struct Tr<float> {
+  using Pot = float2;
+  using Mass = float;
+  static constexpr float kNegBig = -1.0e30f;
+  __device__ __forceinline__ static float ex2(float x) { return ex2_approx(x); }
+  __device__ __forceinline__ static float lg2(float x) { return lg2_approx(x); }
+  // a - b rounded to float (hi parts subtract exactly when close)
+  __device__ __forceinline__ static float diff(Pot a, Pot b) { return (a.x - b.x) + (a.y - b.y); }
+  // a + b + e rounded to float; e is an integer exponent, added to the hi
+  // sum first (exact when a.x + b.x cancels, as it does for matched frames)
+  __device__ __forceinline__ static float sum(Pot a, Pot b, float e) {
+    return ((a.x + b.x) + e) + (a.y + b.y);
+  }
+  // a - t as a renormalised pair (two-sum of the hi part, Knuth)
+  __device__ __forceinline__ static Pot sub(Pot a, float t) {
+    float s = a.x - t;
+    float bb = s - a.x;
+    float err = (a.x - (s - bb)) + (-t - bb);
+    float lo = err + a.y;
+    float hi = s + lo;
+    lo = lo - (hi - s);
+    return make_float2(hi, lo);
+  }
+  __device__ __forceinline__ static Pot zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static double to_double(Pot a) { return (double)a.x + (double)a.y; }
+  // mass = mant * 2^e, mant in [1, 2); zero (or subnormal) -> (kNegBig, 0)
+  __device__ __forceinline__ static void split(float w, float& e, float& mant) {
+    uint32_t b = __float_as_uint(w);
+    uint32_t ex = (b >> 23) & 0xffu;
+    bool z = (ex == 0u);
+    e = z ? kNegBig : (float)((int)ex - 127);
+    mant = z ? 0.f : __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+  }
+};
+
+// double path: plain float64
+template <>
+struct Tr<double> {
+  using Pot = double;
+  using Mass = double;
+  static constexpr double kNegBig = -1.0e300;
+  __device__ __forceinline__ static double ex2(double x) { return exp2(x); }
+  __device__ __forceinline__ static double lg2(double x) { return log2(x); }
+  __device__ __forceinline__ static double diff(Pot a, Pot b) { return a - b; }
+  __device__ __forceinline__ static double sum(Pot a, Pot b, double e) { return (a + b) + e; }
+  __device__ __forceinline__ static Pot sub(Pot a, double t) { return a - t; }
+  __device__ __forceinline__ static Pot zero() { return 0.0; }
+  __device__ __forceinline__ static double to_double(Pot a) { return a; }
+  __device__ __forceinline__ static void split(double w, double& e, double& mant) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(w);
+    int ex = (int)((b >> 52) & 0x7ffull);
+    bool z = (ex == 0);
+    e = z ? kNegBig : (double)(ex - 1023);
+    mant = z ? 0.0 : __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+  }
+};
+
+template <class R>
+struct LS {
+  R m, s;
+};
+
+template <class R>
+struct Agg {
+  R D, m, s;
+};
+
+template <class R>
+__device__ __forceinline__ LS<R> ls_empty() {
+  return {Tr<R>::kNegBig, R(0)};
+}
+
+// (ma, sa) (+) (mb, sb): log-sum of two LS values, result renormalised.
+template <class R>
+__device__ __forceinline__ LS<R> ls_add(R ma, R sa, R mb, R sb) {
+  R d = mb - ma;
+  bool bmax = d > R(0);
+  R mx = bmax ? mb : ma;
+  R e = Tr<R>::ex2(-fabs(d));
+  R s = bmax ? fma(sa, e, sb) : fma(sb, e, sa);
+  if (s >= R(2)) {
+    s *= R(0.5);
+    mx += R(1);
+  }
+  return {mx, s};
+}
+
+template <class R>
+__device__ __forceinline__ Agg<R> agg_identity() {
+  return {R(0), Tr<R>::kNegBig, R(0)};
+}
+
+// map a applied first, then map b
+template <class R>
+__device__ __forceinline__ Agg<R> agg_then(const Agg<R>& a, const Agg<R>& b) {
+  LS<R> t = ls_add(a.m + b.D, a.s, b.m, b.s);
+  return {a.D + b.D, t.m, t.s};
+}
+
+// state st pushed through map a
+template <class R>
+__device__ __forceinline__ LS<R> agg_apply(const Agg<R>& a, LS<R> st) {
+  return ls_add(st.m + a.D, st.s, a.m, a.s);
+}
+
+template <class R>
+__device__ __forceinline__ Agg<R> shfl_up_agg(const Agg<R>& a, int o) {
+  return {__shfl_up_sync(0xffffffffu, a.D, o), __shfl_up_sync(0xffffffffu, a.m, o),
+          __shfl_up_sync(0xffffffffu, a.s, o)};
+}
+template <class R>
+__device__ __forceinline__ Agg<R> shfl_down_agg(const Agg<R>& a, int o) {
+  return {__shfl_down_sync(0xffffffffu, a.D, o), __shfl_down_sync(0xffffffffu, a.m, o),
+          __shfl_down_sync(0xffffffffu, a.s, o)};
+}
+
+// Block-wide exclusive scan of per-thread maps.  Forward: thread t receives
+// the composition of threads 0..t-1 (0 first).  Reverse: thread t receives
+// the composition of threads NT-1..t+1 (NT-1 first).  `total` receives the
+// composition of all threads in the same order.  `sh` holds NT/32 entries.
+template <class R, int NT, bool kReverse>
+__device__ __forceinline__ Agg<R> block_exclusive_scan(Agg<R> x, Agg<R>* sh, Agg<R>& total) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Agg<R> inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    if (!kReverse) {
+      Agg<R> t = shfl_up_agg(inc, o);
+      if (lane >= o) inc = agg_then(t, inc);
+    } else {
+      Agg<R> t = shfl_down_agg(inc, o);
+      if (lane + o < 32) inc = agg_then(t, inc);
+    }
+  }
+  Agg<R> exc = kReverse ? shfl_down_agg(inc, 1) : shfl_up_agg(inc, 1);
+  if (kReverse ? (lane == 31) : (lane == 0)) exc = agg_identity<R>();
+  if (kReverse ? (lane == 0) : (lane == 31)) sh[warp] = inc;
+  __syncthreads();
+  Agg<R> wp = agg_identity<R>();
+  Agg<R> tot = agg_identity<R>();
+  if (!kReverse) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      if (w < warp) wp = agg_then(wp, sh[w]);
+      tot = agg_then(tot, sh[w]);
+    }
+  } else {
+#pragma unroll
+    for (int w = NW - 1; w >= 0; --w) {
+      if (w > warp) wp = agg_then(wp, sh[w]);
+      tot = agg_then(tot, sh[w]);
+    }
+  }
+  __syncthreads();
+  total = tot;
+  return agg_then(wp, exc);
+}
+
+// Block-wide ordered composition (no per-thread result).
+template <class R, int NT, bool kReverse>
+__device__ __forceinline__ Agg<R> block_reduce(Agg<R> x, Agg<R>* sh) {
+  Agg<R> total;
+  (void)block_exclusive_scan<R, NT, kReverse>(x, sh, total);
+  return total;
+}
+
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace finom
