@@ -41,6 +41,9 @@ template <class R>
 finom_status normalise_masses(const double*, int64_t, void*, double*, double*, int*, double*,
                               cudaStream_t);
 void fill_d(double*, int64_t, double, cudaStream_t);
+template <class R>
+void frame_from_log(const double*, int64_t, void*, cudaStream_t);
+void combine_passes(const double*, const double*, double, int64_t, int, double*, cudaStream_t);
 void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
 
 namespace {
@@ -383,6 +386,10 @@ using namespace finom;
 
 namespace {
 
+// Standalone products run two passes: the first with frame 0 gives ln S0;
+// the second uses the frame -ln S0 so that its sums are near 1, where the
+// float32 log-sum keeps full relative precision; the results are combined in
+// float64.  The O side's own absorption (log products) enters only there.
 template <class R>
 finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double* a, const double* b,
                      double* out, cudaStream_t s) {
@@ -392,17 +399,23 @@ finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double*
   const int64_t N = p->N, M = p->M;
   const int64_t nO = transpose ? M : N, nW = transpose ? N : M;
   const double scale = 1.0 / (p->eps * kLn2);
-  if (logmode) {
-    // frames: the O side's absorption vector; weights: the W side's
-    const double* ao = transpose ? b : a;
-    const double* bw = transpose ? a : b;
-    conv_pot_scale<R>(ao, nO, scale, st.qo, s);
-    conv_weights_log<R>(bw, nW, scale, st.qw, st.qwm, s);
-  } else {
-    fill_pot<R>(st.qo, nO, 0.0, s);
-    conv_weights_lin<R>(b, nW, st.qw, st.qwm, s);
-  }
-  return product<R>(p, transpose ? 0 : 1, out, logmode ? F_OUT_LOG : F_OUT_LIN, s);
+  // log products: the O side's absorption (frames) and the W side's absorption;
+  // linear products: no O-side absorption, the weights are the input vector b
+  const double* ao = logmode ? (transpose ? b : a) : nullptr;
+  const double* bw = logmode ? (transpose ? a : b) : b;
+  double* t0 = transpose ? st.ty : st.tx;
+  if (logmode) conv_weights_log<R>(bw, nW, scale, st.qw, st.qwm, s);
+  else conv_weights_lin<R>(bw, nW, st.qw, st.qwm, s);
+  fill_pot<R>(st.qo, nO, 0.0, s);
+  const int o_is_x = transpose ? 0 : 1;
+  rc = product<R>(p, o_is_x, t0, F_OUT_LOG, s);
+  if (rc != FINOM_OK) return rc;
+  frame_from_log<R>(t0, nO, st.qo, s);
+  rc = product<R>(p, o_is_x, out, logmode ? F_OUT_LOG : F_OUT_LIN, s);
+  if (rc != FINOM_OK) return rc;
+  combine_passes(t0, ao, 1.0 / p->eps, nO, logmode ? 0 : 1, out, s);
+  FINOM_CUDA(cudaGetLastError());
+  return FINOM_OK;
 }
 
 finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const double* a,

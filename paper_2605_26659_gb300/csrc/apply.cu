@@ -11,8 +11,18 @@ namespace finom {
 template <class R>
 finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) {
   const size_t smem = sizeof(TileSmem<R>);
-  if (agg_only) k_apply<R, true><<<a.C, kThreads, smem, s>>>(a);
-  else k_apply<R, false><<<a.C, kThreads, smem, s>>>(a);
+  const int mode = agg_only ? kModeAgg : a.flags;
+  switch (mode) {
+    case kModeAgg: k_apply<R, kModeAgg><<<a.C, kThreads, smem, s>>>(a); break;
+    case kModeHalfY: k_apply<R, kModeHalfY><<<a.C, kThreads, smem, s>>>(a); break;
+    case kModeHalfX: k_apply<R, kModeHalfX><<<a.C, kThreads, smem, s>>>(a); break;
+    case kModeCheck: k_apply<R, kModeCheck><<<a.C, kThreads, smem, s>>>(a); break;
+    case kModeLin: k_apply<R, kModeLin><<<a.C, kThreads, smem, s>>>(a); break;
+    case kModeLog: k_apply<R, kModeLog><<<a.C, kThreads, smem, s>>>(a); break;
+    default:
+      set_error("k_apply: unsupported launch mode");
+      return FINOM_EINVAL;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
   return FINOM_OK;
@@ -143,6 +153,25 @@ __global__ void k_f_from_pot(const Pot* pot, const double* m64, int64_t n, doubl
   f[i] = (w > 0.0) ? eps_ln2 * (P + log2(w)) : -INFINITY;
 }
 
+// frame for the second pass of a standalone product: c = -ln S0 / ln 2 (0 where S0 = 0)
+template <class Pot>
+__global__ void k_frame_from_log(const double* t0, int64_t n, Pot* pot) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = t0[i];
+  store_pot(pot, i, (v > -INFINITY && v < INFINITY) ? -v * 1.4426950408889634074 : 0.0);
+}
+
+// combine the two passes: linear S = e^{t0} S2, log: a/eps + t0 + ln S2
+__global__ void k_combine(const double* t0, const double* a, double inv_eps, int64_t n, int lin, double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = t0[i];
+  double l2 = out[i];
+  if (lin) out[i] = (t > -INFINITY) ? exp(t) * l2 : 0.0;
+  else out[i] = (t > -INFINITY) ? a[i] * inv_eps + t + l2 : -INFINITY;
+}
+
 __global__ void k_fill_d(double* f, int64_t n, double v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) f[i] = v;
@@ -167,6 +196,14 @@ inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 
+template <class R>
+void frame_from_log(const double* t0, int64_t n, void* pot, cudaStream_t s) {
+  k_frame_from_log<<<nb(n), 256, 0, s>>>(t0, n, (typename Tr<R>::Pot*)pot);
+}
+void combine_passes(const double* t0, const double* a, double inv_eps, int64_t n, int lin, double* out,
+                    cudaStream_t s) {
+  k_combine<<<nb(n), 256, 0, s>>>(t0, a, inv_eps, n, lin, out);
+}
 template <class R>
 void conv_weights_log(const double* b, int64_t n, double scale, void* pot, void* mass, cudaStream_t s) {
   k_weights_log<<<nb(n), 256, 0, s>>>(b, n, scale, (typename Tr<R>::Pot*)pot,
@@ -200,6 +237,7 @@ void conv_f_from_pot(const void* pot, const double* m64, int64_t n, double eps_l
 }
 
 #define FINOM_INST(R)                                                                        \
+  template void frame_from_log<R>(const double*, int64_t, void*, cudaStream_t);                  \
   template void conv_weights_log<R>(const double*, int64_t, double, void*, void*, cudaStream_t); \
   template void conv_weights_lin<R>(const double*, int64_t, void*, void*, cudaStream_t);         \
   template void conv_pot_scale<R>(const double*, int64_t, double, void*, cudaStream_t);          \

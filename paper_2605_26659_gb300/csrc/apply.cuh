@@ -2,22 +2,25 @@
 //
 // One CTA owns one tile of kTile merged points; thread t walks kElems
 // consecutive points.  For the application with output side O and weight
-// side W (O = x: K psi; O = y: K^T phi) a thread
-//   1. forms, for each of its points, the forward and backward exponents
-//      A_k, A'_k and the log2 weight B_k of W points (frame: the absorbed
-//      potential of the O side, carried across W points -- Remark
-//      log-domain-stabilization);
-//   2. runs the forward recurrence (eq. p by dynamic programming) and the
-//      backward recurrence (eq. q by dynamic programming) over its points,
-//      each as: local map -> block scan of maps -> carry from the tile carry
-//      -> second local pass that emits the state at O points;
-//   3. at O points adds p and q (eq. decompose to p+q) and performs the
+// side W (O = x: K psi; O = y: K^T phi) the stabilised sums (Remark
+// log-domain-stabilization) are carried in log2 form relative to a frame:
+// at an O point its own absorbed potential, at a W point the frame of the O
+// point before it.  Between consecutive points the lower-block recurrence
+// (eq. p by dynamic programming) moves by A_k = (c_k - c_{k-1}) - g_k and the
+// upper-block one (eq. q) by A'_k = -(c_k - c_{k-1}) - g_k (g = gap in bits);
+// both are small once the frame tracks the potential, so their prefix sums
+// D, PB over a thread's points stay precise in float32.  A thread
+//   1. forms its prefix sums D, PB, its weight levels B (frame + potential +
+//      log2 mass) and the maps of both recurrences over its points (each a
+//      log-sum of its weights against their maximum);
+//   2. gets its entry states from a scan of the 256 maps of the tile (two
+//      warps, one per direction) seeded with the tile's carries;
+//   3. at each O point adds p and q (eq. decompose to p+q) and performs the
 //      Sinkhorn division of eq. iteration in the log domain: the absorbed
 //      potential drops by log2 of the stabilised sum;
-//   4. on request adds v_j |S_j - 1| to the marginal error (Algorithm 1
-//      loop head; Sec. 4), and computes the tile's forward and backward maps
-//      for the NEXT application (roles swapped, new potentials), so that the
-//      next launch finds its tile carries ready;
+//   4. on request adds v_j |S_j - 1| to the marginal error (Algorithm 1 loop
+//      head; Sec. 4) and forms the tile maps of the NEXT application (roles
+//      swapped, new potentials), so the next launch finds its carries ready;
 //   5. the last CTA to finish (ticket) scans the tile maps into per-tile
 //      carries, reduces the error in float64 and updates the loop control.
 #pragma once
@@ -30,12 +33,21 @@ namespace finom {
 enum : int {
   F_OUT_POT = 1,     // write new O potentials
   F_OUT_LIN = 2,     // write S (linear, float64) per O point
-  F_OUT_LOG = 4,     // write log S (natural log, float64) per O point
+  F_OUT_LOG = 4,     // write ln S (float64) per O point
   F_ERR = 8,         // marginal error + convergence flag
-  F_NEXT = 16,       // aggregates of the next application (roles swapped)
+  F_NEXT = 16,       // maps of the next application (roles swapped)
   F_ITER_END = 32,   // this launch ends a Sinkhorn iteration
   F_CHECK_DONE = 64, // exit at once when the loop is done
+  F_AGG_ONLY = 128,  // only the tile maps of this application (no outputs)
 };
+
+// the launch kinds (compile-time flag sets)
+constexpr int kModeHalfY = F_OUT_POT | F_ERR | F_NEXT | F_CHECK_DONE;      // psi <- v / K^T phi
+constexpr int kModeHalfX = F_OUT_POT | F_NEXT | F_ITER_END | F_CHECK_DONE; // phi <- u / K psi
+constexpr int kModeCheck = F_ERR;                                           // loop-head check only
+constexpr int kModeLin = F_OUT_LIN;
+constexpr int kModeLog = F_OUT_LOG;
+constexpr int kModeAgg = F_AGG_ONLY;
 
 template <class R>
 struct ApplyArgs {
@@ -66,13 +78,20 @@ struct ApplyArgs {
   int flags;
 };
 
+// padded index of a per-thread slot: conflict-free both for the threads that
+// fill the slots and for the raking warp that reads 8 consecutive slots per lane
+__device__ __forceinline__ int slot(int t) { return t + (t >> 5); }
+constexpr int kSlots = kThreads + kThreads / 32;
+constexpr int kPer = kThreads / 32;   // slots raked per lane
+
 template <class R>
 struct TileSmem {
   using Pot = typename Tr<R>::Pot;
   using Mass = typename Tr<R>::Mass;
   Pot pot[kTile + 2];
   Mass mass[kTile + 2];
-  Agg<R> scan[kThreads / 32];
+  R tf[3][kSlots];   // per-thread forward maps (D, m, s); after the rake: carries (m, s)
+  R tb[3][kSlots];   // per-thread backward maps; after the rake: carries
   double red[kThreads / 32];
   int iscan[kThreads / 32];
   int last;
@@ -98,162 +117,237 @@ __device__ __forceinline__ int block_exclusive_sum(int v, int* sh) {
   return wp + inc - v;
 }
 
-// Per-point exponents of one application.  omask/wmask: which of the thread's
-// points are O / W points.  Frames come from po[] (po[o0] = the O point before
-// the thread's first point, then one entry per O point); weights from pw[],
-// mw[] starting at index w0.
 template <class R>
-__device__ __forceinline__ void point_terms(uint32_t omask, uint32_t wmask, const R (&g)[kElems],
-                                            const typename Tr<R>::Pot* po, int o0,
-                                            const typename Tr<R>::Pot* pw,
-                                            const typename Tr<R>::Mass* mw, int w0, R w_uniform,
-                                            R (&Af)[kElems], R (&Ab)[kElems], R (&Bl)[kElems],
-                                            R (&Bs)[kElems]) {
+__device__ __forceinline__ void put_map(R (*arr)[kSlots], int t, const Agg<R>& a) {
+  const int i = slot(t);
+  arr[0][i] = a.D;
+  arr[1][i] = a.m;
+  arr[2][i] = a.s;
+}
+template <class R>
+__device__ __forceinline__ Agg<R> get_map(R (*arr)[kSlots], int t) {
+  const int i = slot(t);
+  return {arr[0][i], arr[1][i], arr[2][i]};
+}
+
+// Warps 0 and 1: turn the 256 per-thread maps into per-thread entry states.
+// Warp 0, forward: state entering thread t = threads 0..t-1 applied to cf.
+// Warp 1, backward: state entering thread t from its right = threads
+// 255..t+1 applied to cb.  Slots are overwritten with (m, s) of those states.
+template <class R>
+__device__ __forceinline__ void rake_scan(TileSmem<R>& sm, LS<R> cf, LS<R> cb) {
+  const int lane = threadIdx.x & 31;
+  const bool fwd = threadIdx.x < 32;
+  R (*arr)[kSlots] = fwd ? sm.tf : sm.tb;
+  Agg<R> f = agg_identity<R>();
+  if (fwd) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) f = agg_then(f, get_map(arr, lane * kPer + k));
+  } else {
+#pragma unroll
+    for (int k = kPer - 1; k >= 0; --k) f = agg_then(f, get_map(arr, lane * kPer + k));
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    if (fwd) {
+      Agg<R> t = shfl_up_agg(f, o);
+      if (lane >= o) f = agg_then(t, f);
+    } else {
+      Agg<R> t = shfl_down_agg(f, o);
+      if (lane + o < 32) f = agg_then(t, f);
+    }
+  }
+  Agg<R> ex = fwd ? shfl_up_agg(f, 1) : shfl_down_agg(f, 1);
+  if (fwd ? lane == 0 : lane == 31) ex = agg_identity<R>();
+  LS<R> st = agg_apply(ex, fwd ? cf : cb);
+#pragma unroll
+  for (int kk = 0; kk < kPer; ++kk) {
+    const int k = fwd ? kk : kPer - 1 - kk;
+    const int t = lane * kPer + k;
+    Agg<R> a = get_map(arr, t);
+    arr[1][slot(t)] = st.m;
+    arr[2][slot(t)] = st.s;
+    st = agg_apply(a, st);
+  }
+}
+
+// Warps 0 and 1: ordered composition of the 256 per-thread maps (warp 0
+// forward, warp 1 backward); lane 0 of each writes its half of the tile map.
+template <class R>
+__device__ __forceinline__ void rake_reduce(TileSmem<R>& sm, R* out) {
+  const int lane = threadIdx.x & 31;
+  const bool fwd = threadIdx.x < 32;
+  R (*arr)[kSlots] = fwd ? sm.tf : sm.tb;
+  Agg<R> f = agg_identity<R>();
+  if (fwd) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) f = agg_then(f, get_map(arr, lane * kPer + k));
+  } else {
+#pragma unroll
+    for (int k = kPer - 1; k >= 0; --k) f = agg_then(f, get_map(arr, lane * kPer + k));
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Agg<R> t = shfl_down_agg(f, o);
+    // forward: lane l gathers lanes l..l+2o-1 in order; backward: lanes l+2o-1..l
+    if (lane + o < 32) f = fwd ? agg_then(f, t) : agg_then(t, f);
+  }
+  if (lane == 0) {
+    R* o = out + (fwd ? 0 : 3);
+    o[0] = f.D; o[1] = f.m; o[2] = f.s;
+  }
+}
+
+
+#ifndef FINOM_CPASYNC
+#define FINOM_CPASYNC 1
+#endif
+
+// asynchronous global -> shared copies (LDGSTS): every load of the tile is in
+// flight at once and nothing passes through registers
+template <class T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async size");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+  else if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Terms of one application over the thread's points.  Frames come from po[]
+// (po[o0] = the O point before the thread's first point, then one entry per
+// O point); weights from pw[], mw[] starting at w0.  Outputs per point e:
+//   D[e]  = A_0 + ... + A_e     (forward, frame-compensated log decays)
+//   PB[e] = A'_0 + ... + A'_e   (backward)
+//   L1[e] = B_e - D[e], L2[e] = B_e + PB[e]   (weight levels carried to the
+//           segment start; kNegBig for points without weight)
+//   mt[e] = mass mantissa in [1, 2) (0 for points without weight)
+template <class R>
+__device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const R (&g)[kElems],
+                                          const typename Tr<R>::Pot* po, int o0,
+                                          const typename Tr<R>::Pot* pw,
+                                          const typename Tr<R>::Mass* mw, int w0, R w_uniform,
+                                          R (&D)[kElems], R (&PB)[kElems], R (&L1)[kElems],
+                                          R (&L2)[kElems], R (&mt)[kElems]) {
   using T = Tr<R>;
   typename T::Pot cprev = po[o0];
   int oi = o0 + 1, wi = w0;
+  R d = R(0), pb = R(0);
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
     R dc = R(0);
     if ((omask >> e) & 1u) {
-      typename T::Pot c = po[oi++];
+      const typename T::Pot c = po[oi++];
       dc = T::diff(c, cprev);
       cprev = c;
     }
-    Af[e] = dc - g[e];
-    Ab[e] = -dc - g[e];
-    Bl[e] = T::kNegBig;
-    Bs[e] = R(0);
+    d += dc - g[e];
+    pb -= dc + g[e];
+    D[e] = d;
+    PB[e] = pb;
+    L1[e] = T::kNegBig;
+    L2[e] = T::kNegBig;
+    mt[e] = R(0);
     if ((wmask >> e) & 1u) {
-      typename T::Pot pwv = (w_uniform > R(0)) ? T::zero() : pw[wi];
-      typename T::Mass wv = (w_uniform > R(0)) ? (typename T::Mass)w_uniform : mw[wi];
+      const typename T::Pot pv = (w_uniform > R(0)) ? T::zero() : pw[wi];
+      const typename T::Mass mv = (w_uniform > R(0)) ? (typename T::Mass)w_uniform : mw[wi];
       ++wi;
-      R ex, mt;
-      T::split(wv, ex, mt);
-      if (mt > R(0)) {
-        Bl[e] = T::sum(cprev, pwv, ex);
-        Bs[e] = mt;
+      R ex, mn;
+      T::split(mv, ex, mn);
+      if (mn > R(0)) {
+        const R B = T::sum(cprev, pv, ex);
+        L1[e] = B - d;
+        L2[e] = B + pb;
+        mt[e] = mn;
       }
     }
   }
 }
 
+// Maxima and spread of the levels; when the spread allows (fast path) the
+// levels are replaced in place by the scaled terms mt 2^{L - M}.  Returns the
+// maps of both recurrences over the thread's points:
+//   forward  (D_last,  MF + D_last, sum tF),  backward (PB_last, MB, sum tB).
 template <class R>
-__device__ __forceinline__ Agg<R> fwd_map(const R (&Af)[kElems], const R (&Bl)[kElems],
-                                          const R (&Bs)[kElems], uint32_t wmask) {
-  Agg<R> a = agg_identity<R>();
+__device__ __forceinline__ bool seg_maps(const R (&D)[kElems], const R (&PB)[kElems],
+                                         R (&L1)[kElems], R (&L2)[kElems], const R (&mt)[kElems],
+                                         Agg<R>& mapF, Agg<R>& mapB, R& MF, R& MB) {
+  using T = Tr<R>;
+  MF = T::kNegBig;
+  MB = T::kNegBig;
+  R mnF = R(1e30), mnB = R(1e30);
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
-    a.D += Af[e];
-    a.m += Af[e];
-    if ((wmask >> e) & 1u) {
-      LS<R> t = ls_add(a.m, a.s, Bl[e], Bs[e]);
-      a.m = t.m;
-      a.s = t.s;
+    MF = fmax(MF, L1[e]);
+    MB = fmax(MB, L2[e]);
+    if (mt[e] > R(0)) {
+      mnF = fmin(mnF, L1[e]);
+      mnB = fmin(mnB, L2[e]);
     }
   }
-  return a;
-}
-
-template <class R>
-__device__ __forceinline__ Agg<R> bwd_map(const R (&Ab)[kElems], const R (&Bl)[kElems],
-                                          const R (&Bs)[kElems], uint32_t wmask) {
-  Agg<R> a = agg_identity<R>();
+  // the fast path sums scaled terms; a term more than 60 bits below the
+  // maximum would underflow while it may still matter at an earlier point
+  const bool fast = fmax(MF - mnF, MB - mnB) <= R(60);
+  R sF = R(0), sB = R(0);
+  if (fast) {
 #pragma unroll
-  for (int e = kElems - 1; e >= 0; --e) {
-    if ((wmask >> e) & 1u) {
-      LS<R> t = ls_add(a.m, a.s, Bl[e], Bs[e]);
-      a.m = t.m;
-      a.s = t.s;
+    for (int e = 0; e < kElems; ++e) {
+      L1[e] = mt[e] * T::ex2(L1[e] - MF);
+      L2[e] = mt[e] * T::ex2(L2[e] - MB);
+      sF += L1[e];
+      sB += L2[e];
     }
-    a.m += Ab[e];
-    a.D += Ab[e];
+    R m1 = MF + D[kElems - 1];
+    renorm(m1, sF);
+    R m2 = MB;
+    renorm(m2, sB);
+    mapF = {D[kElems - 1], m1, sF};
+    mapB = {PB[kElems - 1], m2, sB};
+  } else {
+    R m1 = T::kNegBig, m2 = T::kNegBig;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      if (mt[e] > R(0)) {
+        ls_add_fast(m1, sF, L1[e], mt[e]);
+        ls_add_fast(m2, sB, L2[e], mt[e]);
+      }
+    }
+    m1 += D[kElems - 1];
+    renorm(m1, sF);
+    renorm(m2, sB);
+    mapF = {D[kElems - 1], m1, sF};
+    mapB = {PB[kElems - 1], m2, sB};
   }
-  return a;
-}
-
-// Last CTA: scan the tile maps agg[6*C] into carries[4*C].
-template <class R>
-__device__ void carry_scan(const R* agg, R* carry, int C, TileSmem<R>& sm) {
-  const int tid = threadIdx.x;
-  const int per = (C + kThreads - 1) / kThreads;
-  const int t0 = min(C, tid * per), t1 = min(C, t0 + per);
-  // forward
-  Agg<R> loc = agg_identity<R>();
-  for (int t = t0; t < t1; ++t) {
-    Agg<R> a = {__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)};
-    loc = agg_then(loc, a);
-  }
-  Agg<R> tot;
-  Agg<R> pre = block_exclusive_scan<R, kThreads, false>(loc, sm.scan, tot);
-  LS<R> st = agg_apply(pre, ls_empty<R>());
-  for (int t = t0; t < t1; ++t) {
-    carry[4 * t + 0] = st.m;
-    carry[4 * t + 1] = st.s;
-    Agg<R> a = {__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)};
-    st = agg_apply(a, st);
-  }
-  // backward: tiles right to left
-  loc = agg_identity<R>();
-  for (int t = t1 - 1; t >= t0; --t) {
-    Agg<R> a = {__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)};
-    loc = agg_then(loc, a);
-  }
-  pre = block_exclusive_scan<R, kThreads, true>(loc, sm.scan, tot);
-  st = agg_apply(pre, ls_empty<R>());
-  for (int t = t1 - 1; t >= t0; --t) {
-    carry[4 * t + 2] = st.m;
-    carry[4 * t + 3] = st.s;
-    Agg<R> a = {__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)};
-    st = agg_apply(a, st);
-  }
+  return fast;
 }
 
 template <class R>
-__device__ __forceinline__ void load_gaps(const R* gap, int64_t seg, int64_t L, R (&g)[kElems]);
+__device__ __forceinline__ void load_gaps(const R* gap, int64_t seg, R (&g)[kElems]);
 
 template <>
-__device__ __forceinline__ void load_gaps<float>(const float* gap, int64_t seg, int64_t L,
-                                                 float (&g)[kElems]) {
-  // gap arrays are padded to whole tiles, so the two vector loads stay in bounds
+__device__ __forceinline__ void load_gaps<float>(const float* gap, int64_t seg, float (&g)[kElems]) {
+  // gap arrays are padded to whole tiles, so the vector loads stay in bounds
+  static_assert(kElems % 4 == 0 && kElems <= 16, "kElems");
   const float4* p = reinterpret_cast<const float4*>(gap + seg);
-  float4 a = __ldg(p), b = __ldg(p + 1);
-  g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
-  g[4] = b.x; g[5] = b.y; g[6] = b.z; g[7] = b.w;
-  (void)L;
+#pragma unroll
+  for (int q = 0; q < kElems / 4; ++q) {
+    float4 v = __ldg(p + q);
+    g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+  }
 }
 
 template <>
-__device__ __forceinline__ void load_gaps<double>(const double* gap, int64_t seg, int64_t L,
-                                                  double (&g)[kElems]) {
+__device__ __forceinline__ void load_gaps<double>(const double* gap, int64_t seg, double (&g)[kElems]) {
   const double2* p = reinterpret_cast<const double2*>(gap + seg);
 #pragma unroll
   for (int q = 0; q < kElems / 2; ++q) {
     double2 a = __ldg(p + q);
     g[2 * q] = a.x;
     g[2 * q + 1] = a.y;
-  }
-  (void)L;
-}
-
-// Tile maps of one application (used by the aggregate-only launch and by the
-// F_NEXT epilogue).  Thread 0 writes the tile's forward/backward maps.
-template <class R>
-__device__ __forceinline__ void tile_maps(uint32_t omask, uint32_t wmask, const R (&g)[kElems],
-                                          const typename Tr<R>::Pot* po, int o0,
-                                          const typename Tr<R>::Pot* pw,
-                                          const typename Tr<R>::Mass* mw, int w0, R w_uniform,
-                                          R* agg_out, int tile, TileSmem<R>& sm) {
-  R Af[kElems], Ab[kElems], Bl[kElems], Bs[kElems];
-  point_terms<R>(omask, wmask, g, po, o0, pw, mw, w0, w_uniform, Af, Ab, Bl, Bs);
-  Agg<R> f = fwd_map<R>(Af, Bl, Bs, wmask);
-  Agg<R> b = bwd_map<R>(Ab, Bl, Bs, wmask);
-  Agg<R> tf = block_reduce<R, kThreads, false>(f, sm.scan);
-  Agg<R> tb = block_reduce<R, kThreads, true>(b, sm.scan);
-  if (threadIdx.x == 0) {
-    R* a = agg_out + 6 * tile;
-    a[0] = tf.D; a[1] = tf.m; a[2] = tf.s;
-    a[3] = tb.D; a[4] = tb.m; a[5] = tb.s;
   }
 }
 
@@ -271,15 +365,63 @@ __device__ __forceinline__ bool last_cta(int32_t* ticket, int C, TileSmem<R>& sm
   return sm.last != 0;
 }
 
-template <class R, bool kAggOnly>
-__global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs<R> a) {
+// Last CTA: scan the tile maps agg[6*C] into carries[4*C] (all threads).
+template <class R>
+__device__ void carry_scan(const R* agg, R* carry, int C, TileSmem<R>& sm) {
+  const int tid = threadIdx.x;
+  const int per = (C + kThreads - 1) / kThreads;
+  const int t0 = min(C, tid * per), t1 = min(C, t0 + per);
+  Agg<R> f = agg_identity<R>(), b = agg_identity<R>();
+  for (int t = t0; t < t1; ++t)
+    f = agg_then(f, Agg<R>{__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)});
+  for (int t = t1 - 1; t >= t0; --t)
+    b = agg_then(b, Agg<R>{__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)});
+  put_map(sm.tf, tid, f);
+  put_map(sm.tb, tid, b);
+  __syncthreads();
+  if (tid < 64) rake_scan<R>(sm, ls_empty<R>(), ls_empty<R>());
+  __syncthreads();
+  LS<R> st = {sm.tf[1][slot(tid)], sm.tf[2][slot(tid)]};
+  for (int t = t0; t < t1; ++t) {
+    carry[4 * t + 0] = st.m;
+    carry[4 * t + 1] = st.s;
+    st = agg_apply(Agg<R>{__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)}, st);
+  }
+  st = {sm.tb[1][slot(tid)], sm.tb[2][slot(tid)]};
+  for (int t = t1 - 1; t >= t0; --t) {
+    carry[4 * t + 2] = st.m;
+    carry[4 * t + 3] = st.s;
+    st = agg_apply(Agg<R>{__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)}, st);
+  }
+}
+
+// Last CTA: float64 sum of the C per-tile partial sums (all threads).
+template <class R>
+__device__ double sum_parts(const double* part, int C, TileSmem<R>& sm) {
+  double s = 0.0;
+  for (int t = threadIdx.x; t < C; t += kThreads) s += __ldcg(part + t);
+  s = warp_sum(s);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
+  return tot;
+}
+
+template <class R, int kFlags>
+#ifndef FINOM_MINB
+#define FINOM_MINB 4
+#endif
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_apply(ApplyArgs<R> a) {
+  constexpr bool kAggOnly = (kFlags & F_AGG_ONLY) != 0;
   using T = Tr<R>;
   using Pot = typename T::Pot;
-  using Mass = typename T::Mass;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<R>& sm = *reinterpret_cast<TileSmem<R>*>(smem_raw);
 
-  if ((a.flags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return;
+  if ((kFlags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return;
 
   const int tid = threadIdx.x;
   const int tile = blockIdx.x;
@@ -305,30 +447,51 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs<R> a) {
   const uint32_t omask = a.o_is_x ? xmask : ymask;
   const uint32_t wmask = a.o_is_x ? ymask : xmask;
   R g[kElems];
-  load_gaps<R>(a.gap, seg, a.L, g);
-
-  const int o_before = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
-  // threads past the end of the sequence own no points; keep their index in range
-  const int w_before = min((int)(seg - k0) - o_before, n_w);   // valid for threads with seg < L
+  load_gaps<R>(a.gap, seg, g);
 
   // stage the tile's O and W data (plus the point before the tile) in shared memory
   for (int i = tid; i < n_o + 1; i += kThreads) {
-    int gi = max(o_start - 1 + i, 0);
+    const int gi = max(o_start - 1 + i, 0);
+#if FINOM_CPASYNC
+    cp_async(&sm.pot[i], &a.pO[gi]);
+    cp_async(&sm.mass[i], &a.mO[gi]);
+#else
     sm.pot[i] = a.pO[gi];
     sm.mass[i] = a.mO[gi];
+#endif
   }
-  if (a.w_uniform <= R(0) || (a.flags & F_NEXT)) {
+  if (a.w_uniform <= R(0) || (kFlags & F_NEXT)) {
     for (int i = tid; i < n_w + 1; i += kThreads) {
-      int gi = max(w_start - 1 + i, 0);
+      const int gi = max(w_start - 1 + i, 0);
+#if FINOM_CPASYNC
+      cp_async(&sm.pot[wofs + i], &a.pW[gi]);
+      cp_async(&sm.mass[wofs + i], &a.mW[gi]);
+#else
       sm.pot[wofs + i] = a.pW[gi];
       sm.mass[wofs + i] = a.mW[gi];
+#endif
     }
   }
+  const int o_before = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
+  // threads past the end of the sequence own no points; keep their index in range
+  const int w_before = min((int)(seg - k0) - o_before, n_w);
+#if FINOM_CPASYNC
+  cp_async_commit_wait();
   __syncthreads();
+#endif
 
-  if (kAggOnly) {
-    tile_maps<R>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
-                 a.w_uniform, a.agg_out, tile, sm);
+  using Pot = typename T::Pot;
+  R D[kElems], PB[kElems], L1[kElems], L2[kElems], mt[kElems], MF, MB;
+  Agg<R> mapF, mapB;
+  seg_terms<R>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
+               a.w_uniform, D, PB, L1, L2, mt);
+  const bool fast = seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
+
+  if constexpr (kAggOnly) {
+    put_map(sm.tf, tid, mapF);
+    put_map(sm.tb, tid, mapB);
+    __syncthreads();
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * tile);
     if (last_cta<R>(a.ctrl, a.C, sm)) {
       carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
       if (tid == 0) a.ctrl[0] = 0;
@@ -336,93 +499,144 @@ __global__ void __launch_bounds__(kThreads) k_apply(ApplyArgs<R> a) {
     return;
   }
 
-  R Af[kElems], Ab[kElems], Bl[kElems], Bs[kElems];
-  point_terms<R>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
-                 a.w_uniform, Af, Ab, Bl, Bs);
-
-  // forward recurrence: local map, block scan, carried second pass
-  Agg<R> tot;
-  Agg<R> pre = block_exclusive_scan<R, kThreads, false>(fwd_map<R>(Af, Bl, Bs, wmask), sm.scan, tot);
-  LS<R> st = agg_apply(pre, LS<R>{__ldg(a.carry_in + 4 * tile + 0), __ldg(a.carry_in + 4 * tile + 1)});
-  R fm[kElems], fs[kElems];
-#pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    st.m += Af[e];
-    if ((wmask >> e) & 1u) st = ls_add(st.m, st.s, Bl[e], Bs[e]);
-    fm[e] = st.m;
-    fs[e] = st.s;
+  // entry states of the thread's points: forward (from the left) and
+  // backward (from the right, in the frame of the thread's last point)
+  LS<R> ef, eb;
+  {
+    const R* c = a.carry_in + 4 * tile;
+    const LS<R> cf = {__ldg(c + 0), __ldg(c + 1)}, cb = {__ldg(c + 2), __ldg(c + 3)};
+    put_map(sm.tf, tid, mapF);
+    put_map(sm.tb, tid, mapB);
+    __syncthreads();
+    if (tid < 64) rake_scan<R>(sm, cf, cb);
+    __syncthreads();
+    ef = {sm.tf[1][slot(tid)], sm.tf[2][slot(tid)]};
+    eb = {sm.tb[1][slot(tid)], sm.tb[2][slot(tid)]};
   }
-  // backward recurrence
-  pre = block_exclusive_scan<R, kThreads, true>(bwd_map<R>(Ab, Bl, Bs, wmask), sm.scan, tot);
-  st = agg_apply(pre, LS<R>{__ldg(a.carry_in + 4 * tile + 2), __ldg(a.carry_in + 4 * tile + 3)});
-  int oi = o_before + __popc(omask);   // smem index of this thread's last O point
+
+  // lam_e = log2 S_e in the point's own frame (S = p + q, eq. decompose to p+q):
+  //   p_e = D_e + log2(entry_f (+) weights t <= e),  q_e = -PB_e + log2(entry_b' (+) weights t > e)
+  // with entry_b' = the backward entry state carried to the segment start.
+  R lam[kElems];
+  const R ebm = eb.m + PB[kElems - 1];
+  if (fast) {
+    R qsuf[kElems];
+    R acc = R(0);
+#pragma unroll
+    for (int e = kElems - 1; e >= 0; --e) {
+      qsuf[e] = acc;         // backward terms strictly after e
+      acc += L2[e];
+    }
+    // fold each entry state into its local sum once per thread; a part with
+    // no weight must not set the level
+    const R lf1 = (ef.s > R(0)) ? ef.m : T::kNegBig;
+    const R LF = fmax(lf1, MF);
+    const R cF0 = ef.s * T::ex2(lf1 - LF), cF1 = T::ex2(MF - LF);
+    const R lb1 = (eb.s > R(0)) ? ebm : T::kNegBig;
+    const R LB = fmax(lb1, MB);
+    const R cB0 = eb.s * T::ex2(lb1 - LB), cB1 = T::ex2(MB - LB);
+    R pf = R(0);
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      pf += L1[e];           // forward terms up to e
+      const R sf = fma(cF1, pf, cF0), sb = fma(cB1, qsuf[e], cB0);
+      const R a1 = (sf > R(0)) ? LF + D[e] : T::kNegBig;
+      const R a2 = (sb > R(0)) ? LB - PB[e] : T::kNegBig;
+      const R M = fmax(a1, a2);
+      lam[e] = M + T::lg2(fma(sf, T::ex2(a1 - M), sb * T::ex2(a2 - M)));
+    }
+  } else {
+    // levels spread over more than 60 bits: running-max log-sums
+    R fm[kElems], fs[kElems];
+    R m = ef.m, sv = ef.s;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      if (mt[e] > R(0)) ls_add_fast(m, sv, L1[e], mt[e]);
+      fm[e] = m;
+      fs[e] = sv;
+    }
+    m = ebm;
+    sv = eb.s;
+#pragma unroll
+    for (int e = kElems - 1; e >= 0; --e) {
+      LS<R> s2 = ls_add(fm[e] + D[e], fs[e], m - PB[e], sv);
+      lam[e] = s2.m + T::lg2(s2.s);
+      if (mt[e] > R(0)) ls_add_fast(m, sv, L2[e], mt[e]);
+    }
+  }
+
+  // outputs at the O points: the division of eq. iteration in the log domain
+  int oi = o_before;   // smem index of the O point before the current one
   R err = R(0);
 #pragma unroll
-  for (int e = kElems - 1; e >= 0; --e) {
+  for (int e = 0; e < kElems; ++e) {
     if ((omask >> e) & 1u) {
-      LS<R> s2 = ls_add(fm[e], fs[e], st.m, st.s);   // p + q (eq. decompose to p+q)
-      R l2 = s2.m + T::lg2(s2.s);                      // log2 of the stabilised sum
-      Pot c = sm.pot[oi];
-      if (a.flags & F_OUT_POT) sm.pot[oi] = T::sub(c, l2);
-      if (a.flags & (F_OUT_LIN | F_OUT_LOG)) {
+      ++oi;
+      const R l2 = lam[e];
+      if constexpr ((kFlags & F_OUT_POT) != 0) sm.pot[oi] = T::sub(sm.pot[oi], l2);
+      if constexpr ((kFlags & (F_OUT_LIN | F_OUT_LOG)) != 0) {
         double v;
-        if (a.flags & F_OUT_LIN) v = (double)s2.s * exp2((double)s2.m);
-        else v = 0.69314718055994530942 * ((double)s2.m + log2((double)s2.s));
+        if constexpr ((kFlags & F_OUT_LIN) != 0) v = exp2((double)l2);
+        else v = 0.69314718055994530942 * (double)l2;
         a.out[o_start + oi - 1] = v;
       }
-      if (a.flags & F_ERR) {
-        R mo = (R)sm.mass[oi];
+      if constexpr ((kFlags & F_ERR) != 0) {
+        const R mo = (R)sm.mass[oi];
         if (a.o_scale > R(0)) {
           err += fabs(a.o_scale * T::ex2(l2) - mo);
         } else {
           // S - 1 without the cancellation of ex2(l2) - 1 near l2 = 0
-          R x = l2 * R(0.69314718055994530942);
-          R sm1 = (fabs(x) < R(0.03)) ? x * (R(1) + x * (R(0.5) + x * (R(1.0 / 6) + x * R(1.0 / 24))))
-                                      : T::ex2(l2) - R(1);
+          const R x = l2 * R(0.69314718055994530942);
+          const R sm1 = (fabs(x) < R(0.03))
+                            ? x * (R(1) + x * (R(0.5) + x * (R(1.0 / 6) + x * R(1.0 / 24))))
+                            : T::ex2(l2) - R(1);
           err += mo * fabs(sm1);
         }
       }
-      --oi;
     }
-    if ((wmask >> e) & 1u) st = ls_add(st.m, st.s, Bl[e], Bs[e]);
-    st.m += Ab[e];
   }
 
-  if (a.flags & F_ERR) {
+  if (kFlags & F_ERR) {
     double e64 = warp_sum((double)err);
     if ((tid & 31) == 0) sm.red[tid >> 5] = e64;
   }
   __syncthreads();
-  if ((a.flags & F_ERR) && tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += sm.red[w];
-    a.part[tile] = s;
+  if ((kFlags & F_ERR) && tid == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
+    a.part[tile] = tot;
   }
-  if (a.flags & F_OUT_POT) {
+  if (kFlags & F_OUT_POT) {
     for (int i = tid; i < n_o; i += kThreads) a.pO_out[o_start + i] = sm.pot[1 + i];
   }
-  if (a.flags & F_NEXT) {
+  if (kFlags & F_NEXT) {
     // next application: O' = current W (frames = current W potentials),
-    // W' = current O (new potentials, same masses)
-    tile_maps<R>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0),
-                 a.agg_out, tile, sm);
+    // W' = current O (new potentials, same masses); same gaps
+    seg_terms<R>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0), D,
+                 PB, L1, L2, mt);
+    (void)seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
+    put_map(sm.tf, tid, mapF);
+    put_map(sm.tb, tid, mapB);
+    __syncthreads();
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * tile);
   }
 
   if (last_cta<R>(a.ctrl, a.C, sm)) {
-    if (a.flags & F_NEXT) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+    if (kFlags & F_NEXT) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+    double errsum = 0.0;
+    if (kFlags & F_ERR) errsum = sum_parts<R>(a.part, a.C, sm);
     if (tid == 0) {
       int32_t* c = a.ctrl;
-      if (a.flags & F_ERR) {
-        double s = 0.0;
-        for (int t = 0; t < a.C; ++t) s += __ldcg(a.part + t);
-        a.scal[0] = s;
-        if (s <= a.tol) {
+      if (kFlags & F_ERR) {
+        a.scal[0] = errsum;
+        if (errsum <= a.tol) {
           c[1] = 1;
           c[3] = c[2];
           c[4] = 1;
         }
       }
-      if ((a.flags & F_ITER_END) && !c[1]) {
+      if ((kFlags & F_ITER_END) && !c[1]) {
         c[2] += 1;
         if ((int64_t)c[2] >= a.maxit) {
           c[1] = 1;

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
   uint32_t bits = (seg < a.L) ? ((a.tbits[seg >> 5] >> (seg & 31)) & ((1u << kElems) - 1u)) : 0u;
   const uint32_t wmask = bits & vmask, omask = (~bits) & vmask;
   double g[kElems];
-  load_gaps<double>(a.gap, seg, a.L, g);
+  load_gaps<double>(a.gap, seg, g);
   const int o_before = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
   // threads past the end of the sequence own no points; keep their index in range
   const int w_before = min((int)(seg - k0) - o_before, n_w);

@@ -111,19 +111,43 @@ __device__ __forceinline__ LS<R> ls_empty() {
   return {Tr<R>::kNegBig, R(0)};
 }
 
-// (ma, sa) (+) (mb, sb): log-sum of two LS values, result renormalised.
+// Move the binary exponent of s into m so that s lands in [1, 2) (exact).
+__device__ __forceinline__ void renorm(float& m, float& s) {
+  int b = __float_as_int(s);
+  int ex = ((b >> 23) & 0xff) - 127;
+  if (ex > -127) {   // s > 0 and normal
+    s = __int_as_float(b - ex * (1 << 23));
+    m += (float)ex;
+  }
+}
+__device__ __forceinline__ void renorm(double& m, double& s) {
+  long long b = __double_as_longlong(s);
+  long long ex = ((b >> 52) & 0x7ffll) - 1023;
+  if (ex > -1023) {
+    s = __longlong_as_double(b - ex * (1ll << 52));
+    m += (double)ex;
+  }
+}
+
+// (ma, sa) (+) (mb, sb) without renormalisation (one ex2); used inside the
+// per-thread chains, where s grows by at most 2 per added point.
+template <class R>
+__device__ __forceinline__ void ls_add_fast(R& m, R& s, R mb, R sb) {
+  R d = mb - m;
+  R e = Tr<R>::ex2(-fabs(d));
+  bool gt = d > R(0);
+  R s1 = fma(sb, e, s);
+  R s2 = fma(s, e, sb);
+  s = gt ? s2 : s1;
+  m = gt ? mb : m;
+}
+
+// (ma, sa) (+) (mb, sb), renormalised.
 template <class R>
 __device__ __forceinline__ LS<R> ls_add(R ma, R sa, R mb, R sb) {
-  R d = mb - ma;
-  bool bmax = d > R(0);
-  R mx = bmax ? mb : ma;
-  R e = Tr<R>::ex2(-fabs(d));
-  R s = bmax ? fma(sa, e, sb) : fma(sb, e, sa);
-  if (s >= R(2)) {
-    s *= R(0.5);
-    mx += R(1);
-  }
-  return {mx, s};
+  ls_add_fast(ma, sa, mb, sb);
+  renorm(ma, sa);
+  return {ma, sa};
 }
 
 template <class R>
@@ -153,58 +177,6 @@ template <class R>
 __device__ __forceinline__ Agg<R> shfl_down_agg(const Agg<R>& a, int o) {
   return {__shfl_down_sync(0xffffffffu, a.D, o), __shfl_down_sync(0xffffffffu, a.m, o),
           __shfl_down_sync(0xffffffffu, a.s, o)};
-}
-
-// Block-wide exclusive scan of per-thread maps.  Forward: thread t receives
-// the composition of threads 0..t-1 (0 first).  Reverse: thread t receives
-// the composition of threads NT-1..t+1 (NT-1 first).  `total` receives the
-// composition of all threads in the same order.  `sh` holds NT/32 entries.
-template <class R, int NT, bool kReverse>
-__device__ __forceinline__ Agg<R> block_exclusive_scan(Agg<R> x, Agg<R>* sh, Agg<R>& total) {
-  constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  Agg<R> inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    if (!kReverse) {
-      Agg<R> t = shfl_up_agg(inc, o);
-      if (lane >= o) inc = agg_then(t, inc);
-    } else {
-      Agg<R> t = shfl_down_agg(inc, o);
-      if (lane + o < 32) inc = agg_then(t, inc);
-    }
-  }
-  Agg<R> exc = kReverse ? shfl_down_agg(inc, 1) : shfl_up_agg(inc, 1);
-  if (kReverse ? (lane == 31) : (lane == 0)) exc = agg_identity<R>();
-  if (kReverse ? (lane == 0) : (lane == 31)) sh[warp] = inc;
-  __syncthreads();
-  Agg<R> wp = agg_identity<R>();
-  Agg<R> tot = agg_identity<R>();
-  if (!kReverse) {
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      if (w < warp) wp = agg_then(wp, sh[w]);
-      tot = agg_then(tot, sh[w]);
-    }
-  } else {
-#pragma unroll
-    for (int w = NW - 1; w >= 0; --w) {
-      if (w > warp) wp = agg_then(wp, sh[w]);
-      tot = agg_then(tot, sh[w]);
-    }
-  }
-  __syncthreads();
-  total = tot;
-  return agg_then(wp, exc);
-}
-
-// Block-wide ordered composition (no per-thread result).
-template <class R, int NT, bool kReverse>
-__device__ __forceinline__ Agg<R> block_reduce(Agg<R> x, Agg<R>* sh) {
-  Agg<R> total;
-  (void)block_exclusive_scan<R, NT, kReverse>(x, sh, total);
-  return total;
 }
 
 template <class R>

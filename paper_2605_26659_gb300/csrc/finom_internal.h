@@ -13,9 +13,15 @@ namespace finom {
 // Scan geometry: one CTA handles a tile of kThreads * kElems merged points;
 // each thread walks kElems consecutive points.  The tile size is fixed for
 // both precisions so a plan's tile table serves every kernel.
-constexpr int kThreads = 256;
-constexpr int kElems = 8;
-constexpr int kTile = kThreads * kElems;   // 2048 merged points per tile
+#ifndef FINOM_THREADS
+#define FINOM_THREADS 256
+#endif
+#ifndef FINOM_ELEMS
+#define FINOM_ELEMS 8
+#endif
+constexpr int kThreads = FINOM_THREADS;
+constexpr int kElems = FINOM_ELEMS;
+constexpr int kTile = kThreads * kElems;   // merged points per tile (2048 by default)
 
 void set_error(const std::string& msg);
 finom_status cuda_fail(cudaError_t e, const char* what);
