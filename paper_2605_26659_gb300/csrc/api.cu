@@ -329,7 +329,7 @@ finom_status solve_end(finom_plan_s* p, double* f, double* g, finom_result* res,
     res->marginal_err_loop = loop_err;
     res->dual = hd[0] + hd[1];
     res->iters = iters;
-    res->converged = (converged || err64 <= st.tol) ? 1 : 0;
+    res->converged = (err64 <= st.tol || (converged && sizeof(R) == sizeof(double))) ? 1 : 0;
     res->status = FINOM_OK;
   }
   st.active = false;
@@ -348,23 +348,57 @@ finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, d
   rc = solve_begin<R>(p, u, v, tol, maxit, warm ? f : nullptr, warm ? g : nullptr, s);
   if (rc != FINOM_OK) return rc;
   if (maxit > 0) {
-    rc = build_body<R>(p);
-    if (rc != FINOM_OK) return rc;
-    int64_t bodies = 1;
-    for (;;) {
-      int32_t done = 0;
-      rc = solve_poll(p, s, &done, nullptr);
+    // Loop until the device-side check stops it.  When the check passed in
+    // the plan's precision, verify the marginal error in float64; if that is
+    // still above tol, tighten the loop tolerance and resume from the exact
+    // state at the stop (the skipped phi half step of iteration l).
+    for (int attempt = 0;; ++attempt) {
+      rc = build_body<R>(p);
       if (rc != FINOM_OK) return rc;
-      if (done) break;
-      if (st.launched & 1) {
-        for (int64_t b = 0; b < bodies; ++b) FINOM_CUDA(cudaGraphLaunch(st.body, s));
-        st.launched += 2 * bodies;
-      } else {
-        rc = solve_step<R>(p, 1, s);
+      int64_t bodies = 1;
+      for (;;) {
+        int32_t done = 0;
+        rc = solve_poll(p, s, &done, nullptr);
         if (rc != FINOM_OK) return rc;
+        if (done) break;
+        if (st.launched & 1) {
+          for (int64_t b = 0; b < bodies; ++b) FINOM_CUDA(cudaGraphLaunch(st.body, s));
+          st.launched += 2 * bodies;
+        } else {
+          rc = solve_step<R>(p, 1, s);
+          if (rc != FINOM_OK) return rc;
+        }
+        bodies = std::min<int64_t>(bodies * 2, 64);
       }
-      bodies = std::min<int64_t>(bodies * 2, 64);
+      if (sizeof(R) == sizeof(double) || attempt >= 6) break;
+      int32_t h[8];
+      double loop_err = 0.0;
+      FINOM_CUDA(cudaMemcpyAsync(h, st.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+      FINOM_CUDA(cudaMemcpyAsync(&loop_err, st.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      FINOM_CUDA(cudaStreamSynchronize(s));
+      if (!h[4]) break;                      // stopped at maxit
+      const int64_t l = h[3];
+      if (l == 0 && !st.warm) break;         // the start already met tol
+      double err64 = 0.0, w1 = 0.0;
+      const int q = (int)(l & 1);
+      const double eps_ln2 = p->eps * kLn2;
+      // float64 smooth potentials into tx, ty (f, g receive the full ones)
+      conv_f_from_pot<R>(st.px[q], st.mu64, p->N, eps_ln2, f, st.tx, s);
+      conv_f_from_pot<R>(st.py[q], st.nu64, p->M, eps_ln2, g, st.ty, s);
+      rc = cost64(p, st.tx, st.ty, st.mu64, st.nu64, &err64, &w1, s);
+      if (rc != FINOM_OK) return rc;
+      if (err64 <= tol) break;
+      // resume: clear the stop, continue with the phi half step of iteration l
+      const double f = std::max(0.1, std::min(0.8, 0.8 * tol / err64));
+      st.tol = std::max(loop_err * f, 0.0);
+      int32_t zero[2] = {0, 0};
+      FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 1, &zero[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 4, &zero[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      rc = launch_apply<R>(half_args<R>(p, true, q), false, s);
+      if (rc != FINOM_OK) return rc;
+      st.launched = l + 1;
     }
+    st.tol = tol;
   }
   rc = solve_end<R>(p, f, g, res, s);
   if (rc != FINOM_OK) return rc;
