@@ -179,6 +179,32 @@ finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_resu
 finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, const double* f,
                         const double* g, double* w1, double* err, void* stream);
 
+/*
+ * finom_kv_log_noalloc -- the same product as finom_kv_log, for callers that
+ * must not allocate device memory (their memory is owned by a fixed pool or
+ * another allocator, they run under a hard memory budget, or they cannot
+ * afford the allocator's locks and implicit synchronisation).  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
+ *     call.  The working memory of the scan (tile maps, tile carries, the
+ *     last-block ticket) is one static device array of 327,936 bytes that
+ *     every GPU loading the library keeps until the process exits.
+ *   - Limit: N + M <= 8,388,608 merged points (4096 tiles); larger plans
+ *     return FINOM_EINVAL with a message, and nothing is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; the ticket
+ *     is reset at the start of each call.  Calls that overlap on the GPU (on
+ *     different streams, or from different host threads) race and must not
+ *     be issued.
+ *   - One pass with a as the frame: results agree with finom_kv_log to the
+ *     plan's precision when a varies smoothly between neighbouring points.
+ * Arguments as finom_kv_log (device pointers; out: N doubles, natural log).
+ */
+finom_status finom_kv_log_noalloc(finom_plan_t plan, const double* a, const double* b, double* out,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

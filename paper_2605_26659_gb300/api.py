@@ -60,6 +60,7 @@ _SIGS = {
     "finom_solve_poll": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), _P], ctypes.c_int),
     "finom_solve_end": ([_P, _P, _P, ctypes.POINTER(FinomResult), _P], ctypes.c_int),
     "finom_cost": ([_P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], ctypes.c_int),
+    "finom_kv_log_noalloc": ([_P, _P, _P, _P, _P], ctypes.c_int),
 }
 
 
@@ -254,3 +255,12 @@ def finom_cost(plan: Plan, u, v, f, g, stream=None):
                            _dev(f, plan.N, torch.float64, "f"), _dev(g, plan.M, torch.float64, "g"),
                            ctypes.byref(w1), ctypes.byref(err), _stream(stream)))
     return w1.value, err.value
+
+
+def finom_kv_log_noalloc(plan: Plan, a, b, out=None, stream=None):
+    """finom_kv_log without device allocation inside the library (static scratch)."""
+    import torch
+    out = _out(plan.N, plan, out)
+    _check(_lib.finom_kv_log_noalloc(plan.handle, _dev(a, plan.N, torch.float64, "a"),
+                                     _dev(b, plan.M, torch.float64, "b"), _dev(out, plan.N), _stream(stream)))
+    return out
