@@ -8,6 +8,11 @@ divide and marginal-error check, then the K psi half step): 2^21
 point-iterations.  L2 is flushed (256 MB write) before every timed step, and
 each step is timed with CUDA events on the launching stream.
 
+`--workload 2d` times the 2D path instead (Algorithm 2 with the Appendix A
+stabilisation): 1024 x 1024 grids, tanh-clustered axes, four anisotropic
+Gaussians, eps = 2e-3; one step = one iteration = four line-batch launches,
+2 * 1024^2 point-iterations.
+
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 (serial float64 FINOM recurrences in plain C) on the same workload instead.
 Under torchrun every rank runs its own replica of the workload (weak
@@ -45,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
     ap.add_argument("--n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", choices=["1d", "2d"], default="1d")
+    ap.add_argument("--side", type=int, default=1024, help="2D grid side (default 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -174,9 +181,29 @@ def cpu_baseline(pr, budget_s=12.0):
                       f"N=M={len(pr.x)} graded meshes ({dt:.1f} s)"}
 
 
+def cpu_baseline_2d(pr, budget_s=12.0):
+    """The CPU oracle on the 2D workload: whole Sinkhorn iterations (line-by-line
+    float64 FINOM in plain C), one core."""
+    from oracle import serial_c
+    serial_c.lib()
+    t0 = time.perf_counter()
+    serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1)
+    t1 = time.perf_counter() - t0
+    iters = max(1, min(50, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, iters)
+    dt = time.perf_counter() - t0
+    n = pr.U.size + pr.V.size
+    return {"value": n * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} Sinkhorn iterations of the serial C float64 2D oracle on the full "
+                      f"{pr.U.shape[0]}x{pr.U.shape[1]} grids ({dt:.1f} s)"}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
+    if args.workload == "2d":
+        return run_reference_2d(args)
     from paper_2605_26659_gb300 import inputs
     pr = inputs.config2(args.n)
     from oracle import serial_c
@@ -202,22 +229,36 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_finom(args, ws, rank, local):
-    import numpy as np
-    import torch
+def run_reference_2d(args):
+    from paper_2605_26659_gb300 import inputs
+    from oracle import serial_c
+    pr = inputs.config3(args.side)
+    serial_c.lib()
+    A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 0)
+    for _ in range(args.warmup):
+        A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1, A, B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1, A, B)
+    dt = time.perf_counter() - t0
+    n = pr.U.size + pr.V.size
+    val = n * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "gpu_launches": 0,
+            "config": {"workload": f"2D grids {args.side}x{args.side}, eps=2e-3, one Sinkhorn iteration per step",
+                       "side": args.side, "eps": pr.eps},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} Sinkhorn iterations of the serial C float64 2D oracle"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
-    from paper_2605_26659_gb300 import api, inputs
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    api.load()
-    pr = inputs.config2(args.n)
-    N, M = len(pr.x), len(pr.y)
-    L = N + M
-    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
-    x, y, u, v = T(pr.x), T(pr.y), T(pr.u), T(pr.v)
-    stream = torch.cuda.current_stream(dev)
-    plan = api.finom_plan(x, y, pr.eps, "f32_log", stream=stream)
-    api.finom_solve_begin(plan, u, v, 0.0, 1 << 40, stream=stream)
+
+def timed_steps(api, plan, args, stream, dev, ws):
+    """W untimed steps, then K steps each after a 256 MB L2 flush, each timed
+    with CUDA events on the launching stream; clocks sampled meanwhile."""
+    import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         flush.zero_()
@@ -243,7 +284,103 @@ def run_finom(args, ws, rank, local):
     barrier(ws)
     clocks = sampler.stop()
     times = [s.elapsed_time(e) for s, e in evs]
-    total_ms = float(sum(times))
+    return float(sum(times)), clocks
+
+
+def run_finom_2d(args, ws, rank, local):
+    import torch
+
+    from paper_2605_26659_gb300 import api, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    pr = inputs.config3(args.side)
+    N, M = pr.U.shape
+    NM = N * M
+    flat = lambda G: G.ravel(order="F")
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = api.finom_plan_2d(T(pr.x1), T(pr.x2), T(pr.y1), T(pr.y2), pr.eps, "f32_log", stream=stream)
+    api.finom_solve_begin(plan, T(flat(pr.U)), T(flat(pr.V)), 0.0, 1 << 40, stream=stream)
+    total_ms, clocks = timed_steps(api, plan, args, stream, dev, ws)
+    done, iters = api.finom_solve_poll(plan, stream=stream)
+    assert not done and iters == args.warmup + args.steps + 1, (done, iters)
+    total_ms = max_over_ranks(total_ms, ws)
+    step_s = total_ms / 1e3 / args.steps
+    pts = 2 * NM
+    value = ws * pts * args.steps / (total_ms / 1e3)
+    # per application: first pass reads W potentials + masses (12 B) and writes
+    # log2 Q (8 B); second pass reads O potentials + masses (12 B) and Q (8 B)
+    # and writes O potentials (8 B): 48 B per grid point, two applications
+    bytes_per_step = 2 * 48.0 * NM
+    peak, peak_kind = peaks()
+    achieved = bytes_per_step / step_s / 1e9
+
+    e2e = None
+    if args.e2e_steps > 0:
+        hs = [torch.tensor(a, dtype=torch.float64).pin_memory()
+              for a in (pr.x1, pr.x2, pr.y1, pr.y2, flat(pr.U), flat(pr.V))]
+        hf = torch.empty(NM, dtype=torch.float64).pin_memory()
+        hg = torch.empty(NM, dtype=torch.float64).pin_memory()
+        done_pts, secs = 0, 0.0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dx1, dx2, dy1, dy2, du, dv = (t.to(dev, non_blocking=True) for t in hs)
+            p2 = api.finom_plan_2d(dx1, dx2, dy1, dy2, pr.eps, "f32_log", stream=stream)
+            f, g, res = api.finom_solve(p2, du, dv, pr.tol, 200000, stream=stream)
+            hf.copy_(f, non_blocking=True)
+            hg.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            api.finom_plan_destroy(p2)
+            if k > 0:
+                done_pts += pts * res["iters"]
+                secs += dt
+        e2e = {"value": ws * done_pts / secs, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (2 * N + 2 * M + 2 * NM), "d2h_bytes_per_step": 8 * 2 * NM,
+               "solve_iters": res["iters"], "converged": res["converged"],
+               "marginal_err": res["marginal_err"], "w1": res["w1"], "seconds_per_solve": secs / args.e2e_steps}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_2d(pr)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"2D grids {N}x{M} (tanh-clustered axes, stretch 2.5), 4 anisotropic "
+                                   f"Gaussians, eps=2e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
+                       "N": N, "M": M, "eps": pr.eps, "point_iters_per_step": pts,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "gpu_launches": 4 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "finom::k_apply line batches (2D passes, 4 launches per step)",
+                         "algorithmic_bytes_per_step": bytes_per_step},
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    api.finom_plan_destroy(plan)
+
+
+def run_finom(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2605_26659_gb300 import api, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    pr = inputs.config2(args.n)
+    N, M = len(pr.x), len(pr.y)
+    L = N + M
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    x, y, u, v = T(pr.x), T(pr.y), T(pr.u), T(pr.v)
+    stream = torch.cuda.current_stream(dev)
+    plan = api.finom_plan(x, y, pr.eps, "f32_log", stream=stream)
+    api.finom_solve_begin(plan, u, v, 0.0, 1 << 40, stream=stream)
+    total_ms, clocks = timed_steps(api, plan, args, stream, dev, ws)
     done, iters = api.finom_solve_poll(plan, stream=stream)
     assert not done and iters == args.warmup + args.steps + 1, (done, iters)
     total_ms = max_over_ranks(total_ms, ws)
@@ -298,7 +435,7 @@ def run_finom(args, ws, rank, local):
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "finom::k_apply<float,false> (fused half step)",
+                         "kernel": "finom::k_apply<float, 113|89> (fused half steps)",
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "clocks": clocks,
             "e2e": e2e,
@@ -313,6 +450,8 @@ def main():
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "2d":
+        run_finom_2d(args, ws, rank, local)
     else:
         run_finom(args, ws, rank, local)
     if ws > 1:

@@ -86,6 +86,36 @@ const char* finom_last_error(void);
 finom_status finom_plan(const double* x, int64_t N, const double* y, int64_t M, double eps,
                         finom_precision prec, void* stream, finom_plan_t* out);
 
+/*
+ * finom_plan_2d -- plan for two tensor-product grids (Sec. 3, Algorithm 2):
+ *   grid 1 = { (x1_k, y1_i) }, grid 2 = { (x2_l, y2_j) },  k, l < N;  i, j < M,
+ * with cost |x1_k - x2_l| + |y1_i - y2_j|, so that K = K_y (x) K_x
+ * (eq. 2d-kron) with K_x the 1D kernel of (x1, x2) and K_y that of (y1, y2).
+ * The plan holds the two axis plans (merged order, dividing indices, decay
+ * factors of each axis).
+ *   x1, x2: N doubles; y1, y2: M doubles (device), each sorted non-decreasing
+ *   and finite.  N, M >= 1, N * M <= 2^31.  eps > 0 and finite.
+ * Grid arrays passed to the other entry points hold N * M values in the
+ * paper's column-major order: point (k, i) of grid 1 at k + N i, point (l, j)
+ * of grid 2 at l + N j (vec() of Sec. 3.2).  On a 2D plan finom_kv is
+ * K v (v on grid 2, out on grid 1), finom_ktu is K^T u, finom_kv_log /
+ * finom_ktu_log the stabilised products of Appendix A (eq. K'bpsi), and
+ * finom_solve / finom_solve_* / finom_cost run Algorithm 2 with that
+ * stabilisation (Phi = Psi = 1/(NM) at the start).  finom_dividing_index and
+ * finom_kv_log_noalloc return FINOM_ENOTSUP.  finom_plan_info reports N*M for
+ * both sizes.  Synchronous.  Errors as finom_plan.
+ */
+finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const double* y1,
+                           const double* y2, int64_t M, double eps, finom_precision prec,
+                           void* stream, finom_plan_t* out);
+
+/*
+ * finom_plan_shape -- dimension of a plan and its sizes: dim = 1 with the
+ * mesh sizes (N, M), or dim = 2 with the grid sides (N points along x, M
+ * along y).  Any pointer may be NULL.
+ */
+finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64_t* M);
+
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 finom_status finom_plan_destroy(finom_plan_t plan);
 

@@ -20,7 +20,11 @@
  *       (x_{i+1} - y_j) k_{i+1,j} = r_i (x_i - y_j) k_ij + (x_{i+1} - x_i) r_i k_ij,
  *     the cost-weighted sums obey c_{i+1} = r_i (c_i + (x_{i+1} - x_i) p_i)
  *     + block-edge terms, next to the p recurrence (and the mirror image for
- *     the upper block).
+ *     the upper block);
+ *   - the 2D products of Appendix A (eq. K'bpsi): the 1D stabilised product
+ *     applied to every column along x, then to every row along y; Algorithm 2
+ *     with absorption after every half step; the 2D <C, Gamma> from the
+ *     separable cost, C_x o K_x (x) K_y + K_x (x) C_y o K_y.
  * Build: gcc -O2 -fPIC -shared (no fast-math: IEEE semantics are kept).
  */
 #include <math.h>
@@ -170,6 +174,99 @@ int64_t finom_ref_sinkhorn(const double* x, int64_t N, const double* y, int64_t 
     ++it;
   }
   free(q);
+  *err = e;
+  return it;
+}
+
+/* ------------------------------------------------------------------ 2D --- */
+/*
+ * Grids: grid 1 = (x1_k, y1_i), grid 2 = (x2_l, y2_j), k, l < N, i, j < M,
+ * arrays column-major (k + N i).  out(k, i) = log sum_{l, j} exp((B(l, j) -
+ * |x1_k - x2_l| - |y1_i - y2_j|) / eps): the column pass logQ(:, j) =
+ * log K_x e^{B(:, j)/eps}, then the row pass log (K_y e^{logQ(k, :)}) (the
+ * absorption of the output grid is left to the caller).  With cost_axis = 1
+ * (2) the x (y) pass returns the cost-weighted sums instead, so that the
+ * result is log sum |x1_k - x2_l| (|y1_i - y2_j|) exp(...).
+ */
+static void log_apply2d_impl(const double* x1, const double* y1, const double* x2, const double* y2,
+                             int64_t N, int64_t M, double eps, const double* B, double* out,
+                             int cost_axis) {
+  double* Q = (double*)malloc(sizeof(double) * (size_t)(N * M));
+  double* col = (double*)malloc(sizeof(double) * (size_t)N);
+  double* cst = (double*)malloc(sizeof(double) * (size_t)(N > M ? N : M));
+  double* row = (double*)malloc(sizeof(double) * (size_t)M);
+  double* rout = (double*)malloc(sizeof(double) * (size_t)M);
+  for (int64_t j = 0; j < M; ++j) {
+    finom_ref_log_apply(x1, N, x2, N, eps, B + N * j, col, NULL, NULL, cost_axis == 1 ? cst : NULL);
+    for (int64_t k = 0; k < N; ++k) Q[k + N * j] = (cost_axis == 1) ? cst[k] : col[k];
+  }
+  for (int64_t k = 0; k < N; ++k) {
+    for (int64_t j = 0; j < M; ++j) row[j] = eps * Q[k + N * j];
+    finom_ref_log_apply(y1, M, y2, M, eps, row, rout, NULL, NULL, cost_axis == 2 ? cst : NULL);
+    for (int64_t i = 0; i < M; ++i) out[k + N * i] = (cost_axis == 2) ? cst[i] : rout[i];
+  }
+  free(Q); free(col); free(cst); free(row); free(rout);
+}
+
+void finom_ref_log_apply2d(const double* x1, const double* y1, const double* x2, const double* y2,
+                           int64_t N, int64_t M, double eps, const double* B, double* out) {
+  log_apply2d_impl(x1, y1, x2, y2, N, M, eps, B, out, 0);
+}
+
+/* sum | exp(B/eps + log K^T e^{A/eps}) - V | over grid 2 */
+double finom_ref_marginal_error2d(const double* x1, const double* y1, const double* x2,
+                                  const double* y2, int64_t N, int64_t M, double eps,
+                                  const double* A, const double* B, const double* V) {
+  double* lt = (double*)malloc(sizeof(double) * (size_t)(N * M));
+  log_apply2d_impl(x2, y2, x1, y1, N, M, eps, A, lt, 0);
+  nsum acc = {0.0, 0.0};
+  for (int64_t t = 0; t < N * M; ++t) nadd(&acc, fabs(exp(B[t] / eps + lt[t]) - V[t]));
+  free(lt);
+  return acc.s + acc.c;
+}
+
+/* <C, Gamma>, Gamma = exp((A(k,i) + B(l,j) - C)/eps), C = |dx| + |dy| */
+double finom_ref_cost2d(const double* x1, const double* y1, const double* x2, const double* y2,
+                        int64_t N, int64_t M, double eps, const double* A, const double* B) {
+  double* r = (double*)malloc(sizeof(double) * (size_t)(N * M));
+  nsum acc = {0.0, 0.0};
+  for (int axis = 1; axis <= 2; ++axis) {
+    log_apply2d_impl(x1, y1, x2, y2, N, M, eps, B, r, axis);
+    for (int64_t t = 0; t < N * M; ++t)
+      if (A[t] != -INFINITY && r[t] != -INFINITY) nadd(&acc, exp(A[t] / eps + r[t]));
+  }
+  free(r);
+  return acc.s + acc.c;
+}
+
+/*
+ * Algorithm 2 with absorption after every half step (Appendix A).  A, B
+ * (cost units, grid 1 / grid 2, column-major) are outputs; if warm != 0 they
+ * are also the start, else Phi = Psi = 1/(NM).  The loop head checks
+ * || diag(psi) K^T phi - v ||_1 as Algorithm 2 does.  U, V sum to 1.
+ */
+int64_t finom_ref_sinkhorn2d(const double* x1, const double* y1, const double* x2, const double* y2,
+                             int64_t N, int64_t M, const double* U, const double* V, double eps,
+                             double tol, int64_t maxit, int warm, double* A, double* B, double* err) {
+  const int64_t NM = N * M;
+  double* lt = (double*)malloc(sizeof(double) * (size_t)NM);
+  if (!warm) {
+    for (int64_t t = 0; t < NM; ++t) A[t] = B[t] = eps * log(1.0 / (double)NM);
+  }
+  int64_t it = 0;
+  double e = 0.0;
+  for (;;) {
+    log_apply2d_impl(x2, y2, x1, y1, N, M, eps, A, lt, 0);   /* log K^T phi on grid 2 */
+    nsum acc = {0.0, 0.0};
+    for (int64_t t = 0; t < NM; ++t) nadd(&acc, fabs(exp(B[t] / eps + lt[t]) - V[t]));
+    e = acc.s + acc.c;
+    if (it >= maxit || e <= tol) break;
+    for (int64_t t = 0; t < NM; ++t) B[t] = (V[t] > 0.0) ? eps * (log(V[t]) - lt[t]) : -INFINITY;
+    log_apply2d_impl(x1, y1, x2, y2, N, M, eps, B, lt, 0);   /* log K psi on grid 1 */
+    for (int64_t t = 0; t < NM; ++t) A[t] = (U[t] > 0.0) ? eps * (log(U[t]) - lt[t]) : -INFINITY;
+    ++it;
+  }
+  free(lt);
   *err = e;
   return it;
 }

@@ -53,6 +53,15 @@ def lib():
         L.finom_ref_sinkhorn.argtypes = [_dp, I64, _dp, I64, _dp, _dp, D, D, I64, ctypes.c_int,
                                          _dp, _dp, ctypes.POINTER(D)]
         L.finom_ref_sinkhorn.restype = I64
+        L.finom_ref_log_apply2d.argtypes = [_dp, _dp, _dp, _dp, I64, I64, D, _dp, _dp]
+        L.finom_ref_log_apply2d.restype = None
+        L.finom_ref_marginal_error2d.argtypes = [_dp, _dp, _dp, _dp, I64, I64, D, _dp, _dp, _dp]
+        L.finom_ref_marginal_error2d.restype = D
+        L.finom_ref_cost2d.argtypes = [_dp, _dp, _dp, _dp, I64, I64, D, _dp, _dp]
+        L.finom_ref_cost2d.restype = D
+        L.finom_ref_sinkhorn2d.argtypes = [_dp, _dp, _dp, _dp, I64, I64, _dp, _dp, D, D, I64,
+                                           ctypes.c_int, _dp, _dp, ctypes.POINTER(D)]
+        L.finom_ref_sinkhorn2d.restype = I64
         _lib = L
     return _lib
 
@@ -98,3 +107,48 @@ def sinkhorn(x, y, u, v, eps, tol, maxit, f0=None, g0=None):
     it = lib().finom_ref_sinkhorn(x, len(x), y, len(y), u, v, float(eps), float(tol), int(maxit),
                                   1 if warm else 0, f, g, ctypes.byref(err))
     return f, g, int(it), err.value
+
+
+# ------------------------------------------------------------------ 2D
+# Grid arrays are numpy (N, M) arrays G[k, i] (point (x_k, y_i)); the C side
+# takes them column-major (k + N i), i.e. G.ravel(order="F").
+
+def _g(G):
+    return np.ascontiguousarray(np.asarray(G, dtype=np.float64).ravel(order="F"))
+
+
+def _grid(flat, N, M):
+    return flat.reshape((N, M), order="F")
+
+
+def log_apply2d(x1, y1, x2, y2, eps, B):
+    """log sum_{l,j} exp((B[l,j] - |x1_k - x2_l| - |y1_i - y2_j|)/eps) on grid 1 (N x M)."""
+    x1, y1, x2, y2 = _a(x1), _a(y1), _a(x2), _a(y2)
+    N, M = len(x1), len(y1)
+    out = np.empty(N * M)
+    lib().finom_ref_log_apply2d(x1, y1, x2, y2, N, M, float(eps), _g(B), out)
+    return _grid(out, N, M)
+
+
+def marginal_error2d(x1, y1, x2, y2, eps, A, B, V):
+    x1, y1, x2, y2 = _a(x1), _a(y1), _a(x2), _a(y2)
+    return lib().finom_ref_marginal_error2d(x1, y1, x2, y2, len(x1), len(y1), float(eps), _g(A),
+                                            _g(B), _g(V))
+
+
+def cost2d(x1, y1, x2, y2, eps, A, B):
+    x1, y1, x2, y2 = _a(x1), _a(y1), _a(x2), _a(y2)
+    return lib().finom_ref_cost2d(x1, y1, x2, y2, len(x1), len(y1), float(eps), _g(A), _g(B))
+
+
+def sinkhorn2d(x1, y1, x2, y2, U, V, eps, tol, maxit, A0=None, B0=None):
+    """Algorithm 2 (absorbed log arithmetic); returns (A, B, iters, err), A, B as (N, M)."""
+    x1, y1, x2, y2 = _a(x1), _a(y1), _a(x2), _a(y2)
+    N, M = len(x1), len(y1)
+    warm = A0 is not None and B0 is not None
+    A = _g(A0).copy() if warm else np.empty(N * M)
+    B = _g(B0).copy() if warm else np.empty(N * M)
+    err = ctypes.c_double()
+    it = lib().finom_ref_sinkhorn2d(x1, y1, x2, y2, N, M, _g(U), _g(V), float(eps), float(tol),
+                                    int(maxit), 1 if warm else 0, A, B, ctypes.byref(err))
+    return _grid(A, N, M), _grid(B, N, M), int(it), err.value

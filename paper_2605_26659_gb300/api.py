@@ -61,6 +61,8 @@ _SIGS = {
     "finom_solve_end": ([_P, _P, _P, ctypes.POINTER(FinomResult), _P], ctypes.c_int),
     "finom_cost": ([_P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P], ctypes.c_int),
     "finom_kv_log_noalloc": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_plan_2d": ([_P, _P, _I64, _P, _P, _I64, _D, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "finom_plan_shape": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
 }
 
 
@@ -119,6 +121,9 @@ class Plan:
     eps: float
     precision: int
     device: int
+    dim: int = 1
+    nx: int = 0          # 2D: grid side along x (N)
+    ny: int = 0          # 2D: grid side along y (M)
 
     def __del__(self):
         try:
@@ -141,6 +146,25 @@ def finom_plan(x, y, eps, precision="f32_log", stream=None) -> Plan:
     _check(_lib.finom_plan(_dev(x, N, torch.float64, "x"), N, _dev(y, M, torch.float64, "y"), M,
                            float(eps), _PREC[precision], _stream(stream), ctypes.byref(h)))
     return Plan(h, N, M, float(eps), _PREC[precision], x.device.index or 0)
+
+
+def finom_plan_2d(x1, x2, y1, y2, eps, precision="f32_log", stream=None) -> Plan:
+    """Plan for the grids x1 (x) y1 and x2 (x) y2.  Grid arrays of the other
+    calls are flat, column-major: point (k, i) at k + N*i."""
+    import torch
+    load()
+    N, M = x1.numel(), y1.numel()
+    h = ctypes.c_void_p()
+    _check(_lib.finom_plan_2d(_dev(x1, N, torch.float64, "x1"), _dev(x2, N, torch.float64, "x2"), N,
+                              _dev(y1, M, torch.float64, "y1"), _dev(y2, M, torch.float64, "y2"), M,
+                              float(eps), _PREC[precision], _stream(stream), ctypes.byref(h)))
+    return Plan(h, N * M, N * M, float(eps), _PREC[precision], x1.device.index or 0, 2, N, M)
+
+
+def finom_plan_shape(plan: Plan):
+    d, n, m = _I32(), _I64(), _I64()
+    _check(_lib.finom_plan_shape(plan.handle, ctypes.byref(d), ctypes.byref(n), ctypes.byref(m)))
+    return d.value, n.value, m.value
 
 
 def finom_plan_destroy(plan: Plan):

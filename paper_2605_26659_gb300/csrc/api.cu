@@ -109,7 +109,7 @@ void free_state(finom_plan_s* p) {
     cudaFree(st.py[q]);
   }
   void* bufs[] = {st.mu, st.nu, st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part,
-                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm};
+                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.t2, st.z};
   for (void* b : bufs) cudaFree(b);
   if (st.stream) cudaStreamDestroy(st.stream);
   st = SolveState();
@@ -123,6 +123,9 @@ ApplyArgs<R> base_args(finom_plan_s* p) {
   a.tile_x0 = p->tile_x0;
   a.L = p->L;
   a.C = (int)p->C;
+  a.lines = 1;
+  a.o_es = 1;
+  a.w_es = 1;
   a.agg_out = (R*)p->st.aggs;
   a.carry_in = (const R*)p->st.carries;
   a.carry_out = (R*)p->st.carries;
@@ -461,6 +464,7 @@ finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const dou
   }
   DeviceGuard dg(p->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->dim == 2) return kv2d(p, transpose, logmode, a, b, out, s);
   return p->prec == FINOM_F32_LOG ? kv_impl<float>(p, transpose, logmode, a, b, out, s)
                                   : kv_impl<double>(p, transpose, logmode, a, b, out, s);
 }
@@ -506,13 +510,54 @@ finom_status finom_plan(const double* x, int64_t N, const double* y, int64_t M, 
   return FINOM_OK;
 }
 
+finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const double* y1,
+                           const double* y2, int64_t M, double eps, finom_precision prec,
+                           void* stream, finom_plan_t* out) {
+  if (!out) {
+    set_error("finom_plan_2d: out is NULL");
+    return FINOM_EINVAL;
+  }
+  *out = nullptr;
+  if (!x1 || !x2 || !y1 || !y2 || N < 1 || M < 1 || !(eps > 0.0) || !std::isfinite(eps) ||
+      (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
+    set_error("finom_plan_2d: need x1, x2, y1, y2 non-null, N, M >= 1, eps > 0 finite, known precision");
+    return FINOM_EINVAL;
+  }
+  if (N > (int64_t)INT32_MAX / 4 || M > (int64_t)INT32_MAX / 4 || N * M > ((int64_t)1 << 31)) {
+    set_error("finom_plan_2d: grid too large (N*M <= 2^31 points per grid)");
+    return FINOM_EINVAL;
+  }
+  finom_plan_s* p = new (std::nothrow) finom_plan_s();
+  if (!p) return FINOM_ENOMEM;
+  p->eps = eps;
+  p->prec = prec;
+  cudaGetDevice(&p->device);
+  finom_status rc = plan2d_build(p, x1, x2, N, y1, y2, M, (cudaStream_t)stream);
+  if (rc != FINOM_OK) {
+    plan2d_free(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return FINOM_OK;
+}
+
 finom_status finom_plan_destroy(finom_plan_t plan) {
   if (!plan) return FINOM_OK;
   DeviceGuard dg(plan->device);
   cudaDeviceSynchronize();
   free_state(plan);
   free_plan(plan);
+  plan2d_free(plan);
   delete plan;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64_t* M) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (dim) *dim = plan->dim;
+  if (N) *N = plan->dim == 2 ? plan->ax->N : plan->N;
+  if (M) *M = plan->dim == 2 ? plan->ay->N : plan->M;
   return FINOM_OK;
 }
 
@@ -528,6 +573,10 @@ finom_status finom_plan_info(finom_plan_t plan, int64_t* N, int64_t* M, double* 
 
 finom_status finom_dividing_index(finom_plan_t plan, int32_t* zeta, int32_t* zetaT, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->dim != 1) {
+    set_error("finom_dividing_index: a 2D plan has one dividing index per axis; use 1D plans of the axes");
+    return FINOM_ENOTSUP;
+  }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (zeta) FINOM_CUDA(cudaMemcpyAsync(zeta, plan->zeta, sizeof(int32_t) * plan->N, cudaMemcpyDeviceToDevice, s));
@@ -563,6 +612,11 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
     return FINOM_EINVAL;
   }
   DeviceGuard dg(plan->device);
+  if (plan->dim == 2) {
+    finom_status rc = solve2d(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
+    if (res && rc != FINOM_OK) res->status = rc;
+    return rc;
+  }
   finom_status rc = plan->prec == FINOM_F32_LOG
                         ? solve_blocking<float>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream)
                         : solve_blocking<double>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
@@ -579,6 +633,7 @@ finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double*
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->dim == 2) return solve2d_begin(plan, u, v, tol, maxit, f0, g0, s);
   return plan->prec == FINOM_F32_LOG ? solve_begin<float>(plan, u, v, tol, maxit, f0, g0, s)
                                      : solve_begin<double>(plan, u, v, tol, maxit, f0, g0, s);
 }
@@ -591,6 +646,7 @@ finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* strea
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->dim == 2) return solve2d_step(plan, iterations, s);
   return plan->prec == FINOM_F32_LOG ? solve_step<float>(plan, iterations, s)
                                      : solve_step<double>(plan, iterations, s);
 }
@@ -614,6 +670,7 @@ finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_resu
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->dim == 2) return solve2d_end(plan, f, g, res, s);
   return plan->prec == FINOM_F32_LOG ? solve_end<float>(plan, f, g, res, s)
                                      : solve_end<double>(plan, f, g, res, s);
 }
@@ -627,6 +684,7 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->dim == 2) return cost2d(plan, u, v, f, g, w1, err, s);
   finom_status rc = plan->prec == FINOM_F32_LOG ? ensure_state<float>(plan) : ensure_state<double>(plan);
   if (rc != FINOM_OK) return rc;
   SolveState& st = plan->st;

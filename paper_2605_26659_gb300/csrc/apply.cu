@@ -11,14 +11,29 @@ namespace finom {
 template <class R>
 finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) {
   const size_t smem = sizeof(TileSmem<R>);
-  const int mode = agg_only ? kModeAgg : a.flags;
+  const int mode = agg_only ? (kModeAgg | (a.flags & (F_FRAME_W | F_WVALID | F_CHECK_DONE))) : a.flags;
+  const unsigned grid = (unsigned)((int64_t)a.C * (int64_t)(a.lines > 0 ? a.lines : 1));
   switch (mode) {
-    case kModeAgg: k_apply<R, kModeAgg><<<a.C, kThreads, smem, s>>>(a); break;
-    case kModeHalfY: k_apply<R, kModeHalfY><<<a.C, kThreads, smem, s>>>(a); break;
-    case kModeHalfX: k_apply<R, kModeHalfX><<<a.C, kThreads, smem, s>>>(a); break;
-    case kModeCheck: k_apply<R, kModeCheck><<<a.C, kThreads, smem, s>>>(a); break;
-    case kModeLin: k_apply<R, kModeLin><<<a.C, kThreads, smem, s>>>(a); break;
-    case kModeLog: k_apply<R, kModeLog><<<a.C, kThreads, smem, s>>>(a); break;
+#define FINOM_CASE(M) \
+  case M: k_apply<R, M><<<grid, kThreads, smem, s>>>(a); break;
+    FINOM_CASE(kModeAgg)
+    FINOM_CASE(kModeHalfY)
+    FINOM_CASE(kModeHalfX)
+    FINOM_CASE(kModeCheck)
+    FINOM_CASE(kModeLin)
+    FINOM_CASE(kModeLog)
+    FINOM_CASE(kMode2Inner)
+    FINOM_CASE(kMode2HalfB)
+    FINOM_CASE(kMode2HalfA)
+    FINOM_CASE(kMode2Check)
+    FINOM_CASE(kMode2InnerP)
+    FINOM_CASE(kMode2Log)
+    FINOM_CASE(kMode2Lin)
+    FINOM_CASE(kMode2AggInner)
+    FINOM_CASE(kMode2AggOuter)
+    FINOM_CASE(kMode2AggInner | F_CHECK_DONE)
+    FINOM_CASE(kMode2AggOuter | F_CHECK_DONE)
+#undef FINOM_CASE
     default:
       set_error("k_apply: unsupported launch mode");
       return FINOM_EINVAL;
@@ -192,9 +207,34 @@ __global__ void k_dot_pos(const double* m, const double* f, int64_t n, double* o
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// dst(r, c) at c + cols r  <-  src(r, c) at r + rows c  (32 x 32 tiles via shared memory)
+template <class T>
+__global__ void k_transpose(const T* src, int64_t rows, int64_t cols, T* dst) {
+  __shared__ T t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + k;
+    if (r < rows && c < cols) t[k][threadIdx.x] = src[r + rows * c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + threadIdx.x, r = r0 + k;
+    if (r < rows && c < cols) dst[c + cols * r] = t[threadIdx.x][k];
+  }
+}
+
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
+
+template <class T>
+void transpose(const T* src, int64_t rows, int64_t cols, T* dst, cudaStream_t s) {
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  k_transpose<T><<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst);
+}
+template void transpose<double>(const double*, int64_t, int64_t, double*, cudaStream_t);
+template void transpose<float>(const float*, int64_t, int64_t, float*, cudaStream_t);
+template void transpose<float2>(const float2*, int64_t, int64_t, float2*, cudaStream_t);
 
 template <class R>
 void frame_from_log(const double* t0, int64_t n, void* pot, cudaStream_t s) {

@@ -23,6 +23,14 @@
 //      swapped, new potentials), so the next launch finds its carries ready;
 //   5. the last CTA to finish (ticket) scans the tile maps into per-tile
 //      carries, reduces the error in float64 and updates the loop control.
+//
+// Line batches (the 2D application of Appendix A): the grid is lines x tiles;
+// every line is one merged sequence of the same axis plan, with its own
+// offset (and element stride) into the O- and W-side arrays.  The first pass
+// of a 2D application has no O-side potentials (the paper's a_x = 0): its
+// frames are taken from the W side (F_FRAME_W) and it writes log2 of the sums
+// (F_QOUT); the second pass takes those as W potentials of unit mass
+// (F_WVALID) and performs the division.
 #pragma once
 
 #include "dev_common.cuh"
@@ -39,6 +47,9 @@ enum : int {
   F_ITER_END = 32,   // this launch ends a Sinkhorn iteration
   F_CHECK_DONE = 64, // exit at once when the loop is done
   F_AGG_ONLY = 128,  // only the tile maps of this application (no outputs)
+  F_FRAME_W = 256,   // O frames: minus the potential of the last W point before (no O data)
+  F_WVALID = 512,    // W masses: 1 where the W potential is finite, else 0 (no W masses)
+  F_QOUT = 1024,     // write log2 of the sums at the O points to q_out (no division)
 };
 
 // the launch kinds (compile-time flag sets)
@@ -48,6 +59,16 @@ constexpr int kModeCheck = F_ERR;                                           // l
 constexpr int kModeLin = F_OUT_LIN;
 constexpr int kModeLog = F_OUT_LOG;
 constexpr int kModeAgg = F_AGG_ONLY;
+// passes of the 2D application (line batches)
+constexpr int kMode2Inner = F_QOUT | F_FRAME_W | F_CHECK_DONE;            // first pass: Q
+constexpr int kMode2HalfB = F_OUT_POT | F_ERR | F_WVALID | F_CHECK_DONE;   // psi update + check
+constexpr int kMode2HalfA = F_OUT_POT | F_WVALID | F_ITER_END | F_CHECK_DONE;
+constexpr int kMode2Check = F_ERR | F_WVALID;
+constexpr int kMode2InnerP = F_QOUT | F_FRAME_W;                            // products
+constexpr int kMode2Log = F_OUT_LOG | F_WVALID;
+constexpr int kMode2Lin = F_OUT_LIN | F_WVALID;
+constexpr int kMode2AggInner = F_AGG_ONLY | F_FRAME_W;
+constexpr int kMode2AggOuter = F_AGG_ONLY | F_WVALID;
 
 template <class R>
 struct ApplyArgs {
@@ -57,20 +78,26 @@ struct ApplyArgs {
   const R* gap;
   const int32_t* tile_x0;
   int64_t L;
-  int C;
+  int C;              // tiles per line
+  int lines;          // lines in the batch (1 for a 1D plan)
   int o_is_x;
+  int64_t o_ls, o_es; // O-side arrays: offset between lines, stride between points
+  int64_t w_ls, w_es; // W-side arrays: the same
+  const int32_t* fw;  // F_FRAME_W: per tile, the W point whose potential frames the O point before it
   const Pot* pO;      // O-side absorbed potentials (the frame), log2 units
   const Mass* mO;     // O-side masses
   Pot* pO_out;        // O-side new potentials
   double* out;        // optional per-O-point output (F_OUT_LIN / F_OUT_LOG)
+  Pot* q_out;         // F_QOUT: log2 sums at the O points
+  int64_t q_ls, q_es; // F_QOUT: offset between lines, stride between points
   const Pot* pW;      // W-side absorbed potentials
   const Mass* mW;     // W-side masses
   R w_uniform;        // > 0: every W point has potential 0 and mass w_uniform
   R o_scale;          // > 0: the error uses psi = o_scale instead of mass * 2^P
-  const R* carry_in;  // 4*C: forward (m, s) | backward (m, s) state entering each tile
-  R* agg_out;         // 6*C: tile maps of the target application
-  R* carry_out;       // 4*C: carries of the target application (last CTA)
-  double* part;       // C partial error sums
+  const R* carry_in;  // 4 per tile: forward (m, s) | backward (m, s) entering it; NULL = none
+  R* agg_out;         // 6 per tile: tile maps of the target application
+  R* carry_out;       // 4 per tile: carries of the target application (last CTA)
+  double* part;       // one partial error sum per tile
   double* scal;       // [0] error of the last check
   int32_t* ctrl;      // [0] ticket [1] done [2] iteration [3] iterations at exit [4] converged
   double tol;
@@ -226,7 +253,7 @@ __device__ __forceinline__ void cp_async_commit_wait() {
 //   L1[e] = B_e - D[e], L2[e] = B_e + PB[e]   (weight levels carried to the
 //           segment start; kNegBig for points without weight)
 //   mt[e] = mass mantissa in [1, 2) (0 for points without weight)
-template <class R>
+template <class R, bool kWValid = false>
 __device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const R (&g)[kElems],
                                           const typename Tr<R>::Pot* po, int o0,
                                           const typename Tr<R>::Pot* pw,
@@ -254,7 +281,9 @@ __device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const 
     mt[e] = R(0);
     if ((wmask >> e) & 1u) {
       const typename T::Pot pv = (w_uniform > R(0)) ? T::zero() : pw[wi];
-      const typename T::Mass mv = (w_uniform > R(0)) ? (typename T::Mass)w_uniform : mw[wi];
+      typename T::Mass mv;
+      if constexpr (kWValid) mv = (T::hi(pv) > T::kNegBig * R(0.5)) ? R(1) : R(0);
+      else mv = (w_uniform > R(0)) ? (typename T::Mass)w_uniform : mw[wi];
       ++wi;
       R ex, mn;
       T::split(mv, ex, mn);
@@ -395,6 +424,29 @@ __device__ void carry_scan(const R* agg, R* carry, int C, TileSmem<R>& sm) {
   }
 }
 
+// Last CTA, line batches: each thread scans the tile maps of whole lines
+// (a line holds a few tiles) into their carries; lines start empty.
+template <class R>
+__device__ void carry_scan_lines(const R* agg, R* carry, int lines, int C) {
+  for (int l = threadIdx.x; l < lines; l += kThreads) {
+    const int64_t b = (int64_t)l * C;
+    LS<R> st = ls_empty<R>();
+    for (int t = 0; t < C; ++t) {
+      carry[4 * (b + t) + 0] = st.m;
+      carry[4 * (b + t) + 1] = st.s;
+      const R* q = agg + 6 * (b + t);
+      st = agg_apply(Agg<R>{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2)}, st);
+    }
+    st = ls_empty<R>();
+    for (int t = C - 1; t >= 0; --t) {
+      carry[4 * (b + t) + 2] = st.m;
+      carry[4 * (b + t) + 3] = st.s;
+      const R* q = agg + 6 * (b + t) + 3;
+      st = agg_apply(Agg<R>{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2)}, st);
+    }
+  }
+}
+
 // Last CTA: float64 sum of the C per-tile partial sums (all threads).
 template <class R>
 __device__ double sum_parts(const double* part, int C, TileSmem<R>& sm) {
@@ -416,6 +468,8 @@ template <class R, int kFlags>
 #endif
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_apply(ApplyArgs<R> a) {
   constexpr bool kAggOnly = (kFlags & F_AGG_ONLY) != 0;
+  constexpr bool kFrameW = (kFlags & F_FRAME_W) != 0;
+  constexpr bool kWValid = (kFlags & F_WVALID) != 0;
   using T = Tr<R>;
   using Pot = typename T::Pot;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -424,7 +478,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   if ((kFlags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return;
 
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
+  const int C = a.C;
+  const int line = (int)(blockIdx.x / (unsigned)C);
+  const int tile = (int)blockIdx.x - line * C;
+  const int64_t ob = (int64_t)line * a.o_ls, wb = (int64_t)line * a.w_ls;
   const int64_t k0 = (int64_t)tile * kTile;
   const int64_t kend = min(k0 + (int64_t)kTile, a.L);
   const int x0 = a.tile_x0[tile], x1 = a.tile_x0[tile + 1];
@@ -450,25 +507,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   load_gaps<R>(a.gap, seg, g);
 
   // stage the tile's O and W data (plus the point before the tile) in shared memory
-  for (int i = tid; i < n_o + 1; i += kThreads) {
-    const int gi = max(o_start - 1 + i, 0);
+  if (!kFrameW) {
+    for (int i = tid; i < n_o + 1; i += kThreads) {
+      const int64_t gi = ob + (int64_t)max(o_start - 1 + i, 0) * a.o_es;
 #if FINOM_CPASYNC
-    cp_async(&sm.pot[i], &a.pO[gi]);
-    cp_async(&sm.mass[i], &a.mO[gi]);
+      cp_async(&sm.pot[i], &a.pO[gi]);
+      cp_async(&sm.mass[i], &a.mO[gi]);
 #else
-    sm.pot[i] = a.pO[gi];
-    sm.mass[i] = a.mO[gi];
+      sm.pot[i] = a.pO[gi];
+      sm.mass[i] = a.mO[gi];
 #endif
+    }
   }
   if (a.w_uniform <= R(0) || (kFlags & F_NEXT)) {
     for (int i = tid; i < n_w + 1; i += kThreads) {
-      const int gi = max(w_start - 1 + i, 0);
+      const int64_t gi = wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
 #if FINOM_CPASYNC
       cp_async(&sm.pot[wofs + i], &a.pW[gi]);
-      cp_async(&sm.mass[wofs + i], &a.mW[gi]);
+      if (!kWValid) cp_async(&sm.mass[wofs + i], &a.mW[gi]);
 #else
       sm.pot[wofs + i] = a.pW[gi];
-      sm.mass[wofs + i] = a.mW[gi];
+      if (!kWValid) sm.mass[wofs + i] = a.mW[gi];
 #endif
     }
   }
@@ -480,20 +539,38 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   __syncthreads();
 #endif
 
-  using Pot = typename T::Pot;
+  if constexpr (kFrameW) {
+    // frame of an O point: minus the potential of the last W point before it
+    // (of the line's first W point when there is none); the O point before the
+    // tile gets the frame its own tile gave it
+    const bool uni = a.w_uniform > R(0);
+    int oi = o_before, wl = w_before;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      if ((omask >> e) & 1u) {
+        ++oi;
+        sm.pot[oi] = uni ? T::zero() : T::neg(sm.pot[wofs + wl]);
+      }
+      if ((wmask >> e) & 1u) ++wl;
+    }
+    if (tid == 0) sm.pot[0] = uni ? T::zero() : T::neg(a.pW[wb + (int64_t)a.fw[tile] * a.w_es]);
+    __syncthreads();
+  }
+
   R D[kElems], PB[kElems], L1[kElems], L2[kElems], mt[kElems], MF, MB;
   Agg<R> mapF, mapB;
-  seg_terms<R>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
-               a.w_uniform, D, PB, L1, L2, mt);
+  seg_terms<R, kWValid>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
+                        a.w_uniform, D, PB, L1, L2, mt);
   const bool fast = seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
 
   if constexpr (kAggOnly) {
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
-    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * tile);
-    if (last_cta<R>(a.ctrl, a.C, sm)) {
-      carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)blockIdx.x);
+    if (last_cta<R>(a.ctrl, a.lines * C, sm)) {
+      if (a.lines == 1) carry_scan<R>(a.agg_out, a.carry_out, C, sm);
+      else carry_scan_lines<R>(a.agg_out, a.carry_out, a.lines, C);
       if (tid == 0) a.ctrl[0] = 0;
     }
     return;
@@ -503,8 +580,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   // backward (from the right, in the frame of the thread's last point)
   LS<R> ef, eb;
   {
-    const R* c = a.carry_in + 4 * tile;
-    const LS<R> cf = {__ldg(c + 0), __ldg(c + 1)}, cb = {__ldg(c + 2), __ldg(c + 3)};
+    LS<R> cf = ls_empty<R>(), cb = ls_empty<R>();
+    if (a.carry_in) {
+      const R* c = a.carry_in + 4 * (int64_t)blockIdx.x;
+      cf = {__ldg(c + 0), __ldg(c + 1)};
+      cb = {__ldg(c + 2), __ldg(c + 3)};
+    }
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
@@ -574,11 +655,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
       ++oi;
       const R l2 = lam[e];
       if constexpr ((kFlags & F_OUT_POT) != 0) sm.pot[oi] = T::sub(sm.pot[oi], l2);
+      if constexpr ((kFlags & F_QOUT) != 0) {
+        // an empty sum (no weight on the line) stays empty
+        sm.pot[oi] = (l2 > T::kNegBig * R(0.5)) ? T::sub(sm.pot[oi], l2) : T::neg(T::none());
+      }
       if constexpr ((kFlags & (F_OUT_LIN | F_OUT_LOG)) != 0) {
         double v;
         if constexpr ((kFlags & F_OUT_LIN) != 0) v = exp2((double)l2);
         else v = 0.69314718055994530942 * (double)l2;
-        a.out[o_start + oi - 1] = v;
+        a.out[ob + (int64_t)(o_start + oi - 1) * a.o_es] = v;
       }
       if constexpr ((kFlags & F_ERR) != 0) {
         const R mo = (R)sm.mass[oi];
@@ -605,10 +690,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     double tot = 0.0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
-    a.part[tile] = tot;
+    a.part[blockIdx.x] = tot;
   }
-  if (kFlags & F_OUT_POT) {
-    for (int i = tid; i < n_o; i += kThreads) a.pO_out[o_start + i] = sm.pot[1 + i];
+  if constexpr ((kFlags & F_OUT_POT) != 0) {
+    for (int i = tid; i < n_o; i += kThreads) a.pO_out[ob + (int64_t)(o_start + i) * a.o_es] = sm.pot[1 + i];
+  }
+  if constexpr ((kFlags & F_QOUT) != 0) {
+    const int64_t qb = (int64_t)line * a.q_ls;
+    for (int i = tid; i < n_o; i += kThreads) a.q_out[qb + (int64_t)(o_start + i) * a.q_es] = T::neg(sm.pot[1 + i]);
   }
   if (kFlags & F_NEXT) {
     // next application: O' = current W (frames = current W potentials),
@@ -619,13 +708,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
-    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * tile);
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)blockIdx.x);
   }
 
-  if (last_cta<R>(a.ctrl, a.C, sm)) {
-    if (kFlags & F_NEXT) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+  if (last_cta<R>(a.ctrl, a.lines * C, sm)) {
+    if (kFlags & F_NEXT) carry_scan<R>(a.agg_out, a.carry_out, C, sm);
     double errsum = 0.0;
-    if (kFlags & F_ERR) errsum = sum_parts<R>(a.part, a.C, sm);
+    if (kFlags & F_ERR) errsum = sum_parts<R>(a.part, a.lines * C, sm);
     if (tid == 0) {
       int32_t* c = a.ctrl;
       if (kFlags & F_ERR) {

@@ -63,6 +63,10 @@ struct Tr<float> {
     return make_float2(hi, lo);
   }
   __device__ __forceinline__ static Pot zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static Pot neg(Pot a) { return make_float2(-a.x, -a.y); }
+  __device__ __forceinline__ static float hi(Pot a) { return a.x; }
+  // stands for -infinity in a potential (an empty sum)
+  __device__ __forceinline__ static Pot none() { return make_float2(kNegBig, 0.f); }
   __device__ __forceinline__ static double to_double(Pot a) { return (double)a.x + (double)a.y; }
   // mass = mant * 2^e, mant in [1, 2); zero (or subnormal) -> (kNegBig, 0)
   __device__ __forceinline__ static void split(float w, float& e, float& mant) {
@@ -86,6 +90,9 @@ struct Tr<double> {
   __device__ __forceinline__ static double sum(Pot a, Pot b, double e) { return (a + b) + e; }
   __device__ __forceinline__ static Pot sub(Pot a, double t) { return a - t; }
   __device__ __forceinline__ static Pot zero() { return 0.0; }
+  __device__ __forceinline__ static Pot neg(Pot a) { return -a; }
+  __device__ __forceinline__ static double hi(Pot a) { return a; }
+  __device__ __forceinline__ static Pot none() { return kNegBig; }
   __device__ __forceinline__ static double to_double(Pot a) { return a; }
   __device__ __forceinline__ static void split(double w, double& e, double& mant) {
     unsigned long long b = (unsigned long long)__double_as_longlong(w);

@@ -53,6 +53,9 @@ struct SolveState {
   void* qom = nullptr;                // products: O-side masses (read, unused)
   void* qw = nullptr;                 // products: W-side potentials
   void* qwm = nullptr;                // products: W-side masses
+  void* q2 = nullptr;                 // 2D: log2 sums between the two passes of an application
+  double* t2 = nullptr;               // 2D: float64 scratch, one grid
+  double* z = nullptr;                // 2D: float64 moments between the two cost passes (2 grids)
   cudaStream_t stream = nullptr;      // internal stream (graph capture needs a non-legacy stream)
   cudaGraphExec_t body = nullptr;     // two Sinkhorn iterations
   // the solve in progress
@@ -79,6 +82,13 @@ struct finom_plan_s {
   void* gap = nullptr;           // per merged point: (z_k - z_{k-1}) / (eps ln 2), plan precision
   double* gap64 = nullptr;       // float64 gaps (the cost kernel uses them)
   int32_t* tile_x0 = nullptr;    // C + 1 entries: number of x points before each tile
+  int32_t* fw[2] = {nullptr, nullptr};  // per tile, [o_is_x]: the W point before the O point
+                                        // that precedes the tile (frames of 2D first passes)
+  // 2D plans (Sec. 3): grids x1 (x) y1 and x2 (x) y2 with N points on the x
+  // axis and M on the y axis; ax merges x1 with x2, ay merges y1 with y2
+  int dim = 1;
+  finom_plan_s* ax = nullptr;
+  finom_plan_s* ay = nullptr;
   finom::SolveState st;
 };
 
@@ -87,4 +97,20 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
 void free_plan(finom_plan_s* p);
 finom_status cost64(finom_plan_s* p, const double* px, const double* py, const double* u,
                     const double* v, double* err, double* w1, cudaStream_t s);
+finom_status cost64_2d(finom_plan_s* p, const double* pa, const double* pb, const double* u,
+                       const double* v, double* err, double* w1, cudaStream_t s);
+// 2D plans (api2d.cu)
+finom_status plan2d_build(finom_plan_s* p, const double* x1, const double* x2, int64_t N,
+                          const double* y1, const double* y2, int64_t M, cudaStream_t s);
+void plan2d_free(finom_plan_s* p);
+finom_status kv2d(finom_plan_s* p, bool transpose_k, bool logmode, const double* a, const double* b,
+                  double* out, cudaStream_t s);
+finom_status solve2d(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                     double* f, double* g, int32_t warm, finom_result* res, cudaStream_t s);
+finom_status solve2d_begin(finom_plan_s* p, const double* u, const double* v, double tol,
+                           int64_t maxit, const double* f0, const double* g0, cudaStream_t s);
+finom_status solve2d_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
+finom_status solve2d_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
+finom_status cost2d(finom_plan_s* p, const double* u, const double* v, const double* f,
+                    const double* g, double* w1, double* err, cudaStream_t s);
 }  // namespace finom

@@ -239,6 +239,10 @@ finom_status noalloc_dispatch(finom_plan_t p, bool transpose, const double* a, c
     set_error("finom_kv_log_noalloc: null argument");
     return FINOM_EINVAL;
   }
+  if (p->dim != 1) {
+    set_error("finom_kv_log_noalloc: 1D plans only");
+    return FINOM_ENOTSUP;
+  }
   if (p->C > kNoAllocMaxTiles) {
     set_error("finom_kv_log_noalloc: N + M exceeds the static scratch (at most " +
               std::to_string((long long)kNoAllocMaxTiles * kTile) + " merged points)");

@@ -94,6 +94,23 @@ __global__ void k_tiles(const int64_t* posx, int64_t N, int64_t C, int32_t* tile
   tile_x0[t] = (int32_t)lo;
 }
 
+// fw[o_is_x][t]: index of the last W point before the O point that precedes
+// tile t (0 when there is none); the O point before the first O point of the
+// sequence is that point itself
+__global__ void k_frame_w(const double* x, int64_t N, const double* y, int64_t M, const int32_t* zeta,
+                          const int32_t* tile_x0, int64_t C, int64_t L, int32_t* fw_y, int32_t* fw_x) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t > C) return;
+  const int64_t k0 = min(t * (int64_t)kTile, L);
+  const int64_t x0 = tile_x0[t], y0 = k0 - x0;
+  // O = x: W points before x_o are the y_j <= x_o
+  const int64_t ox = x0 > 0 ? x0 - 1 : 0;
+  fw_x[t] = (int32_t)max((int64_t)zeta[ox] - 1, (int64_t)0);
+  // O = y: W points before y_o are the x_i < y_o
+  const int64_t oy = y0 > 0 ? min(y0 - 1, M - 1) : 0;
+  fw_y[t] = (int32_t)max(count_le(x, N, y[oy], true) - 1, (int64_t)0);
+}
+
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -156,6 +173,10 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
   const double inv = 1.0 / (p->eps * std::log(2.0));
   k_gaps_bits<<<nblk(words * 32, 256), 256, 0, s>>>(z, type, L, inv, p->gap64, gap32, p->tbits);
   k_tiles<<<nblk(p->C + 1, 256), 256, 0, s>>>(posx, N, p->C, p->tile_x0);
+  FINOM_CUDA(cudaMalloc(&p->fw[0], sizeof(int32_t) * (p->C + 1)));
+  FINOM_CUDA(cudaMalloc(&p->fw[1], sizeof(int32_t) * (p->C + 1)));
+  k_frame_w<<<nblk(p->C + 1, 256), 256, 0, s>>>(p->x, N, p->y, M, p->zeta, p->tile_x0, p->C, L,
+                                                  p->fw[0], p->fw[1]);
   FINOM_CUDA(cudaGetLastError());
   FINOM_CUDA(cudaStreamSynchronize(s));
   cudaFree(posx);
@@ -174,6 +195,8 @@ void free_plan(finom_plan_s* p) {
   if (p->gap && p->gap != p->gap64) cudaFree(p->gap);
   cudaFree(p->gap64);
   cudaFree(p->tile_x0);
+  cudaFree(p->fw[0]);
+  cudaFree(p->fw[1]);
 }
 
 }  // namespace finom

@@ -1,0 +1,269 @@
+"""GPU parity of the 2D path (Sec. 3, Algorithm 2, Appendix A) against the CPU oracle.
+
+Grids x1 (x) y1 and x2 (x) y2, cost |x1_k - x2_l| + |y1_i - y2_j|.  Grid
+arrays cross the C ABI flat and column-major (point (k, i) at k + N i).  The
+oracle is the plain-C line-by-line evaluation of the same products
+(oracle/finom_serial.c, pinned against the dense 2D definition), and the dense
+2D definition itself at small sizes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, serial_c
+from tests.gpu_util import H, T, relerr
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32_log": 1e-5}
+LOCK_TOL = {"f64": 1e-10, "f32_log": 3e-5}   # |f_gpu - f_oracle| / eps on points with mass
+# FP32: every half step rounds each weight level (~log2 of the grid size, 14
+# bits here) to float32 in both passes of an application, ~1e-6 eps per
+# iteration in these tests; the lock-step allowance grows with the iterations
+LOCK_F32_PER_ITER = 2.5e-6
+
+
+def _flat(G):
+    return np.ascontiguousarray(np.asarray(G, dtype=np.float64).ravel(order="F"))
+
+
+def _grid(f, N, M):
+    return np.asarray(f).reshape((N, M), order="F")
+
+
+def _axes(seed, N, M, kind="random"):
+    g = np.random.default_rng(seed)
+    if kind == "random":
+        return (np.sort(g.uniform(0, 1, N)), np.sort(g.uniform(0, 1, M)),
+                np.sort(g.uniform(0, 1, N)), np.sort(g.uniform(0, 1, M)))
+    if kind == "ties":
+        r = lambda n: np.sort(np.round(g.uniform(0, 1, n) * 41) / 41)
+        return r(N), r(M), r(N), r(M)
+    raise ValueError(kind)
+
+
+def _grid_masses(N, M, seed, zeros=False):
+    g = np.random.default_rng(seed)
+    U = g.uniform(0.05, 1, (N, M))
+    V = g.uniform(0.05, 1, (N, M))
+    if zeros:
+        U[g.random((N, M)) < 0.04] = 0.0
+        V[g.random((N, M)) < 0.04] = 0.0
+        if N > 2:
+            U[1, :] = 0.0     # a row of grid 1 without mass
+        if M > 3:
+            V[:, 2] = 0.0     # a column of grid 2 without mass
+    return U / U.sum(), V / V.sum()
+
+
+def _assert_lockstep(f, g, fo, go, u, v, eps, prec, iters):
+    """Potentials after the same iterations, up to the gauge (f + c, g - c)
+    that leaves the plan unchanged: float32 rounding accumulates partly into a
+    near-constant shift that the iteration carries from one side to the other."""
+    tol = LOCK_TOL[prec] if prec == "f64" else max(LOCK_TOL[prec], LOCK_F32_PER_ITER * iters)
+    c = np.sum(u[u > 0] * (f[u > 0] - fo[u > 0]))
+    assert np.max(np.abs(f[u > 0] - fo[u > 0] - c)) / eps <= tol
+    assert np.max(np.abs(g[v > 0] - go[v > 0] + c)) / eps <= tol
+    assert abs(c) / eps <= 20 * tol
+
+
+def f32_bound(axes, eps):
+    """The 1D float32 bound (4 ulp of the largest gap in bits) on each axis,
+    for the two passes of a 2D product."""
+    x1, y1, x2, y2 = axes
+    gm = 0.0
+    for a, b in ((x1, x2), (y1, y2)):
+        z = np.sort(np.concatenate([a, b]))
+        if len(z) > 1:
+            gm = max(gm, float(np.max(np.diff(z))) / (eps * math.log(2.0)))
+    return max(TOL["f32_log"], 2 * 2.4e-7 * gm)
+
+
+def _tol(prec, axes, eps):
+    return TOL["f64"] if prec == "f64" else f32_bound(axes, eps)
+
+
+SHAPES_2D = [(1, 1), (1, 7), (6, 1), (9, 7), (130, 70), (1024, 3), (1500, 40), (40, 2500)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("N,M", SHAPES_2D)
+def test_2d_log_products_match_oracle(lib, prec, N, M):
+    """K' psi and K'^T phi (eq. K'bpsi) on lines of one tile and of several
+    (N + N > 2048 merged points along x for N = 1500)."""
+    eps = 0.02
+    axes = _axes(N * 31 + M, N, M)
+    x1, y1, x2, y2 = axes
+    g = np.random.default_rng(N + 7 * M)
+    A = g.normal(0, 0.01, (N, M))
+    B = g.normal(0, 0.01, (N, M))
+    B[0, 0] = -np.inf
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    assert lib.finom_plan_shape(p) == (2, N, M)
+    got = H(lib.finom_kv_log(p, T(_flat(A)), T(_flat(B))))
+    want = _flat(A) / eps + _flat(serial_c.log_apply2d(x1, y1, x2, y2, eps, B))
+    tol = _tol(prec, axes, eps)
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), fin)
+    if fin.any():
+        assert np.max(np.abs(got[fin] - want[fin])) <= tol * 1.5
+    got_t = H(lib.finom_ktu_log(p, T(_flat(A)), T(_flat(B))))
+    want_t = _flat(B) / eps + _flat(serial_c.log_apply2d(x2, y2, x1, y1, eps, A))
+    fin = np.isfinite(want_t)
+    assert np.array_equal(np.isfinite(got_t), fin)
+    if fin.any():
+        assert np.max(np.abs(got_t[fin] - want_t[fin])) <= tol * 1.5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("kind", ["random", "ties"])
+def test_2d_linear_products_match_dense(lib, prec, kind):
+    N, M, eps = 23, 17, 0.05
+    axes = _axes(5, N, M, kind)
+    x1, y1, x2, y2 = axes
+    K = dense.kernel(dense.cost_2d(x1, y1, x2, y2), eps)
+    g = np.random.default_rng(6)
+    v = g.uniform(0, 1, N * M)
+    v[g.random(N * M) < 0.1] = 0.0
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    assert relerr(H(lib.finom_kv(p, T(v))), K @ v) <= _tol(prec, axes, eps) * 1.5
+    assert relerr(H(lib.finom_ktu(p, T(v))), K.T @ v) <= _tol(prec, axes, eps) * 1.5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("maxit", [0, 1, 6, 25])
+@pytest.mark.parametrize("N,M,eps", [(37, 29, 0.01), (300, 140, 0.004), (1100, 12, 0.01)])
+def test_2d_lockstep_with_oracle(lib, prec, maxit, N, M, eps):
+    axes = _axes(N + M, N, M)
+    x1, y1, x2, y2 = axes
+    U, V = _grid_masses(N, M, N * M, zeros=True)
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    f, g, res = lib.finom_solve(p, T(_flat(U)), T(_flat(V)), 0.0, maxit)
+    Ao, Bo, it, err = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, eps, 0.0, maxit)
+    assert res["iters"] == it == maxit
+    u, v = _flat(U), _flat(V)
+    fa, ga = H(f), H(g)
+    if maxit > 0:
+        _assert_lockstep(fa, ga, _flat(Ao), _flat(Bo), u, v, eps, prec, maxit)
+        assert np.all(np.isneginf(fa[u == 0])) and np.all(np.isneginf(ga[v == 0]))
+        assert res["marginal_err"] == pytest.approx(err, rel=1e-6 if prec == "f64" else 1e-3,
+                                                    abs=1e-9 if prec == "f64" else 3e-6)
+    else:
+        assert np.allclose(fa, _flat(Ao), rtol=1e-14) and np.allclose(ga, _flat(Bo), rtol=1e-14)
+        assert res["marginal_err_loop"] == pytest.approx(err, rel=1e-5)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32_log", 1e-6)])
+def test_2d_converged_matches_oracle(lib, prec, tol):
+    """Config-3 style problem (tanh-clustered axes, anisotropic Gaussian
+    mixtures, eps = 2e-3) at 96 x 80: W1 and the stopping iteration."""
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.config3(96, 80)
+    p = lib.finom_plan_2d(T(pr.x1), T(pr.x2), T(pr.y1), T(pr.y2), pr.eps, prec)
+    f, g, res = lib.finom_solve(p, T(_flat(pr.U)), T(_flat(pr.V)), tol, 100000)
+    Ao, Bo, it, err = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, tol, 100000)
+    w1o = serial_c.cost2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, Ao, Bo)
+    assert res["converged"] == 1
+    if prec == "f64":
+        assert res["iters"] == it
+        assert res["w1"] == pytest.approx(w1o, rel=1e-9)
+    else:
+        # the float32 loop's error estimate sits a few 1e-7 off the float64
+        # one, and near eps = 2e-3 the error falls slowly, so the (float64
+        # verified) stop may come some percent of the iterations later
+        assert abs(res["iters"] - it) <= max(3, 0.1 * it)
+        assert res["w1"] == pytest.approx(w1o, rel=1e-4)
+    A, B = _grid(H(f), 96, 80), _grid(H(g), 96, 80)
+    e_or = serial_c.marginal_error2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, A, B, pr.V)
+    assert e_or <= (tol if prec == "f64" else 3 * tol)
+    assert res["marginal_err"] == pytest.approx(e_or, rel=1e-6, abs=1e-13)
+    assert res["w1"] == pytest.approx(serial_c.cost2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, A, B), rel=1e-10)
+
+
+def test_2d_full_size_application_and_iterations(lib):
+    """1024 x 1024 grids of the 2D workload (FP32 log-domain): one stabilised
+    product over the whole grid, and three Sinkhorn iterations, against the
+    line-by-line oracle."""
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.config3()
+    N = M = 1024
+    axes = (pr.x1, pr.y1, pr.x2, pr.y2)
+    p = lib.finom_plan_2d(T(pr.x1), T(pr.x2), T(pr.y1), T(pr.y2), pr.eps, "f32_log")
+    g = np.random.default_rng(0)
+    A = g.normal(0, 0.002, (N, M))
+    B = np.where(pr.V > 0, pr.eps * np.log(np.maximum(pr.V, 1e-300)), -np.inf)
+    got = H(lib.finom_kv_log(p, T(_flat(A)), T(_flat(B))))
+    want = _flat(A) / pr.eps + _flat(serial_c.log_apply2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, B))
+    assert np.max(np.abs(got - want)) <= f32_bound(axes, pr.eps) * 1.5
+    f, gg, res = lib.finom_solve(p, T(_flat(pr.U)), T(_flat(pr.V)), 0.0, 3)
+    Ao, Bo, it, err = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 3)
+    u, v = _flat(pr.U), _flat(pr.V)
+    assert res["iters"] == 3
+    _assert_lockstep(H(f), H(gg), _flat(Ao), _flat(Bo), u, v, pr.eps, "f32_log", 3)
+    assert res["marginal_err"] == pytest.approx(err, rel=1e-3)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_2d_single_row_grid_is_the_1d_solve(lib, prec):
+    """M = 1: the 2D problem is the 1D one with a constant cost offset |y1 - y2|.
+    The offset is kept at a fraction of a bit (|y1 - y2| / (eps ln 2) < 1): a
+    single axis gap of G bits costs float32 plans ~2.4e-7 G relative precision."""
+    N, eps = 700, 0.01
+    x1, y1, x2, y2 = _axes(3, N, 1)
+    y2 = y1 + 0.004
+    U, V = _grid_masses(N, 1, 4)
+    p2 = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    p1 = lib.finom_plan(T(x1), T(x2), eps, prec)
+    tol = 1e-9 if prec == "f64" else 1e-6
+    _, _, r2 = lib.finom_solve(p2, T(_flat(U)), T(_flat(V)), tol, 100000)
+    _, _, r1 = lib.finom_solve(p1, T(U[:, 0]), T(V[:, 0]), tol, 100000)
+    assert r1["converged"] and r2["converged"]
+    assert r2["w1"] == pytest.approx(r1["w1"] + abs(y1[0] - y2[0]), rel=1e-9 if prec == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_2d_stepwise_equals_blocking_and_warm_start(lib, prec):
+    N, M, eps = 120, 90, 0.005
+    x1, y1, x2, y2 = _axes(8, N, M)
+    U, V = _grid_masses(N, M, 9)
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    f1, g1, r1 = lib.finom_solve(p, T(_flat(U)), T(_flat(V)), 0.0, 20)
+    lib.finom_solve_begin(p, T(_flat(U)), T(_flat(V)), 0.0, 20)
+    lib.finom_solve_step(p, 25)
+    done, it = lib.finom_solve_poll(p)
+    assert done and it == 20
+    f2, g2, r2 = lib.finom_solve_end(p)
+    assert np.array_equal(H(f1), H(f2)) and np.array_equal(H(g1), H(g2))
+    # warm start from 20 iterations + 10 more == 30 iterations (same arithmetic)
+    f3, g3, r3 = lib.finom_solve(p, T(_flat(U)), T(_flat(V)), 0.0, 30)
+    f4, g4, r4 = lib.finom_solve(p, T(_flat(U)), T(_flat(V)), 0.0, 10, f=f1.clone(), g=g1.clone(), warm=True)
+    _assert_lockstep(H(f3), H(g3), H(f4), H(g4), _flat(U), _flat(V), eps, prec, 30)
+
+
+def test_2d_cost_entry_matches_oracle(lib):
+    N, M, eps = 50, 40, 0.02
+    x1, y1, x2, y2 = _axes(12, N, M)
+    U, V = _grid_masses(N, M, 13)
+    Ao, Bo, it, err = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, eps, 0.0, 15)
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, "f64")
+    w1, e = lib.finom_cost(p, T(_flat(U)), T(_flat(V)), T(_flat(Ao)), T(_flat(Bo)))
+    assert w1 == pytest.approx(serial_c.cost2d(x1, y1, x2, y2, eps, Ao, Bo), rel=1e-11)
+    assert e == pytest.approx(serial_c.marginal_error2d(x1, y1, x2, y2, eps, Ao, Bo, V), rel=1e-9)
+
+
+def test_2d_invalid_inputs(lib):
+    x = T([0.1, 0.5, 0.3])      # unsorted
+    y = T([0.2, 0.4])
+    with pytest.raises(lib.FinomError) as e:
+        lib.finom_plan_2d(x, T([0.1, 0.2, 0.3]), y, y, 0.1)
+    assert e.value.status == lib.FINOM_EINVAL
+    p = lib.finom_plan_2d(T([0.1, 0.2, 0.3]), T([0.1, 0.25, 0.3]), y, y, 0.1)
+    with pytest.raises(lib.FinomError) as e:
+        lib.finom_dividing_index(p)
+    assert e.value.status == lib.FINOM_ENOTSUP
+    with pytest.raises(lib.FinomError) as e:
+        lib.finom_kv_log_noalloc(p, T(np.zeros(6)), T(np.zeros(6)))
+    assert e.value.status == lib.FINOM_ENOTSUP
+    with pytest.raises(lib.FinomError):
+        lib.finom_solve(p, T(np.ones(6)), T(-np.ones(6)), 1e-6, 10)
