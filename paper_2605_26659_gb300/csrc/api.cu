@@ -80,8 +80,9 @@ finom_status ensure_state(finom_plan_s* p) {
   FINOM_CUDA(cudaMalloc(&st.nu, mass_size<R>() * M));
   FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * N));
   FINOM_CUDA(cudaMalloc(&st.nu64, sizeof(double) * M));
-  FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * N));
-  FINOM_CUDA(cudaMalloc(&st.ty, sizeof(double) * M));
+  // (also the scratch of normalise_masses: at least 257 entries)
+  FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * std::max<int64_t>(N, 512)));
+  FINOM_CUDA(cudaMalloc(&st.ty, sizeof(double) * std::max<int64_t>(M, 512)));
   FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * 6 * C));
   FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * 4 * C));
   FINOM_CUDA(cudaMalloc(&st.part, sizeof(double) * C));

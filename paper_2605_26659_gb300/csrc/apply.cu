@@ -1,6 +1,7 @@
 // Launchers of the fused half-step kernel and small conversion kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "apply.cuh"
@@ -8,14 +9,50 @@
 
 namespace finom {
 
+// persistent grid: as many CTAs as fit on the device at once, at most one per unit
+template <class R, int M>
+unsigned grid_of(int64_t units, size_t smem) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply<R, M>, kThreads, smem) != cudaSuccess) n = 1;
+    per_sm = n < 1 ? 1 : n;
+  }
+#ifndef FINOM_PERSIST
+#define FINOM_PERSIST 1
+#endif
+  return (unsigned)(FINOM_PERSIST ? std::min<int64_t>(units, (int64_t)per_sm * sms) : units);
+}
+
 template <class R>
 finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) {
   const size_t smem = sizeof(TileSmem<R>);
   const int mode = agg_only ? (kModeAgg | (a.flags & (F_FRAME_W | F_WVALID | F_CHECK_DONE))) : a.flags;
-  const unsigned grid = (unsigned)((int64_t)a.C * (int64_t)(a.lines > 0 ? a.lines : 1));
+  const int64_t units = (int64_t)a.C * (int64_t)(a.lines > 0 ? a.lines : 1);
+  // programmatic dependent launch: the kernel stages what the previous
+  // kernel does not write before it waits for that kernel to finish
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+#ifndef FINOM_PDL
+#define FINOM_PDL 1
+#endif
+  cfg.attrs = attr;
+  cfg.numAttrs = FINOM_PDL ? 1 : 0;
+  cudaError_t e = cudaSuccess;
   switch (mode) {
-#define FINOM_CASE(M) \
-  case M: k_apply<R, M><<<grid, kThreads, smem, s>>>(a); break;
+#define FINOM_CASE(M)                                                                         \
+  case M:                                                                                     \
+    cfg.gridDim = dim3(grid_of<R, M>(units, smem));                                          \
+    e = cudaLaunchKernelEx(&cfg, k_apply<R, M>, a);                                           \
+    break;
     FINOM_CASE(kModeAgg)
     FINOM_CASE(kModeHalfY)
     FINOM_CASE(kModeHalfX)
@@ -38,7 +75,7 @@ finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) 
       set_error("k_apply: unsupported launch mode");
       return FINOM_EINVAL;
   }
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_apply launch");
   return FINOM_OK;
 }

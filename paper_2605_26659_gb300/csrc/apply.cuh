@@ -33,6 +33,8 @@
 // (F_WVALID) and performs the division.
 #pragma once
 
+#include <cstddef>
+
 #include "dev_common.cuh"
 #include "finom_internal.h"
 
@@ -119,10 +121,14 @@ struct TileSmem {
   Mass mass[kTile + 2];
   R tf[3][kSlots];   // per-thread forward maps (D, m, s); after the rake: carries (m, s)
   R tb[3][kSlots];   // per-thread backward maps; after the rake: carries
+  Agg<R> wf[kThreads / 32];   // warp totals (block scans at the end of a launch)
   double red[kThreads / 32];
   int iscan[kThreads / 32];
   int last;
 };
+// the last CTA reuses pot and mass as one scratch area (carry_scan)
+static_assert(offsetof(TileSmem<float>, mass) == sizeof(float2) * (kTile + 2), "layout");
+static_assert(offsetof(TileSmem<double>, mass) == sizeof(double) * (kTile + 2), "layout");
 
 // exclusive block sum of one int per thread
 template <int NT>
@@ -226,9 +232,14 @@ __device__ __forceinline__ void rake_reduce(TileSmem<R>& sm, R* out) {
 }
 
 
-#ifndef FINOM_CPASYNC
-#define FINOM_CPASYNC 1
-#endif
+// programmatic dependent launch: wait until the previous kernel of the
+// stream has completed and its writes are visible; allow the next kernel of
+// the stream to be scheduled (its blocks start as ours exit).  Both are
+// no-ops when the launch did not ask for programmatic serialisation.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
 
 // asynchronous global -> shared copies (LDGSTS): every load of the tile is in
 // flight at once and nothing passes through registers
@@ -394,64 +405,179 @@ __device__ __forceinline__ bool last_cta(int32_t* ticket, int C, TileSmem<R>& sm
   return sm.last != 0;
 }
 
+template <class R>
+__device__ __forceinline__ Agg<R> ld_map(const R* p) {
+  return {__ldcg(p), __ldcg(p + 1), __ldcg(p + 2)};
+}
+
+// Exclusive scan of one per-thread map per thread over the block, in one
+// direction, seeded with cin: the state entering thread t from the left
+// (forward) or from the right (backward).  Shuffle scans inside each warp,
+// warp totals through shared memory; *total receives the block's map.
+template <class R, bool kBackward>
+__device__ __forceinline__ LS<R> block_scan_dir(TileSmem<R>& sm, Agg<R> f, LS<R> cin, Agg<R>* total) {
+  // only the end of a launch runs this: loops stay rolled (small code, few
+  // instruction-cache misses on the SM that runs it)
+  constexpr int NW = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int o = 1; o < 32; o <<= 1) {
+    const Agg<R> t = kBackward ? shfl_down_agg(f, o) : shfl_up_agg(f, o);
+    if (kBackward ? (lane + o < 32) : (lane >= o)) f = agg_then(t, f);
+  }
+  __syncthreads();   // the warp-total slots may still be read by a previous scan
+  if (kBackward ? lane == 0 : lane == 31) sm.wf[warp] = f;
+  Agg<R> fx = kBackward ? shfl_down_agg(f, 1) : shfl_up_agg(f, 1);
+  if (kBackward ? lane == 31 : lane == 0) fx = agg_identity<R>();
+  __syncthreads();
+  LS<R> st = cin;
+  Agg<R> tot = agg_identity<R>();
+  if (!kBackward) {
+#pragma unroll 1
+    for (int w = 0; w < NW; ++w) {
+      if (w < warp) st = agg_apply(sm.wf[w], st);
+      tot = agg_then(tot, sm.wf[w]);
+    }
+  } else {
+#pragma unroll 1
+    for (int w = NW - 1; w >= 0; --w) {
+      if (w > warp) st = agg_apply(sm.wf[w], st);
+      tot = agg_then(tot, sm.wf[w]);
+    }
+  }
+  if (total) *total = tot;
+  return agg_apply(fx, st);
+}
+
 // Last CTA: scan the tile maps agg[6*C] into carries[4*C] (all threads).
+// One direction at a time, a chunk of tiles at a time: the chunk's maps are
+// copied with coalesced loads into the (now free) staging arrays, each thread
+// composes a run of them, a block scan gives every run its entry state, the
+// runs are replayed into carries in shared memory, and those are stored with
+// coalesced writes.  The state leaving a chunk enters the next one.
 template <class R>
 __device__ void carry_scan(const R* agg, R* carry, int C, TileSmem<R>& sm) {
+  R* buf = reinterpret_cast<R*>(sm.pot);   // pot and mass are adjacent: one scratch area
+  constexpr int kBytes = sizeof(sm.pot) + sizeof(sm.mass);
+  constexpr int kPerT = (kBytes / (int)sizeof(R)) / (5 * kThreads);   // tiles per thread per chunk
+  static_assert(kPerT >= 1, "scratch");
+  constexpr int kQ = kPerT * kThreads;                               // tiles per chunk
+  R* cbuf = buf + 3 * kQ;                                            // 2 carry values per tile
   const int tid = threadIdx.x;
-  const int per = (C + kThreads - 1) / kThreads;
-  const int t0 = min(C, tid * per), t1 = min(C, t0 + per);
-  Agg<R> f = agg_identity<R>(), b = agg_identity<R>();
-  for (int t = t0; t < t1; ++t)
-    f = agg_then(f, Agg<R>{__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)});
-  for (int t = t1 - 1; t >= t0; --t)
-    b = agg_then(b, Agg<R>{__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)});
-  put_map(sm.tf, tid, f);
-  put_map(sm.tb, tid, b);
-  __syncthreads();
-  if (tid < 64) rake_scan<R>(sm, ls_empty<R>(), ls_empty<R>());
-  __syncthreads();
-  LS<R> st = {sm.tf[1][slot(tid)], sm.tf[2][slot(tid)]};
-  for (int t = t0; t < t1; ++t) {
-    carry[4 * t + 0] = st.m;
-    carry[4 * t + 1] = st.s;
-    st = agg_apply(Agg<R>{__ldcg(agg + 6 * t + 0), __ldcg(agg + 6 * t + 1), __ldcg(agg + 6 * t + 2)}, st);
-  }
-  st = {sm.tb[1][slot(tid)], sm.tb[2][slot(tid)]};
-  for (int t = t1 - 1; t >= t0; --t) {
-    carry[4 * t + 2] = st.m;
-    carry[4 * t + 3] = st.s;
-    st = agg_apply(Agg<R>{__ldcg(agg + 6 * t + 3), __ldcg(agg + 6 * t + 4), __ldcg(agg + 6 * t + 5)}, st);
+#pragma unroll 1
+  for (int dir = 0; dir < 2; ++dir) {
+    LS<R> run = ls_empty<R>();   // state entering the next chunk
+    const int nch = (C + kQ - 1) / kQ;
+#pragma unroll 1
+    for (int ci = 0; ci < nch; ++ci) {
+      const int ch = dir == 0 ? ci : nch - 1 - ci;
+      const int c0 = ch * kQ, nq = min(kQ, C - c0);
+      __syncthreads();
+      for (int i = tid; i < 3 * nq; i += kThreads) {
+        const int j = i / 3, d = i - 3 * j;
+        buf[i] = __ldcg(agg + 6 * (int64_t)(c0 + j) + 3 * dir + d);
+      }
+      __syncthreads();
+      const int j0 = tid * kPerT;
+      Agg<R> f = agg_identity<R>();
+      if (dir == 0) {
+#pragma unroll 1
+        for (int k = 0; k < kPerT; ++k)
+          if (j0 + k < nq) f = agg_then(f, Agg<R>{buf[3 * (j0 + k)], buf[3 * (j0 + k) + 1], buf[3 * (j0 + k) + 2]});
+      } else {
+#pragma unroll 1
+        for (int k = kPerT - 1; k >= 0; --k)
+          if (j0 + k < nq) f = agg_then(f, Agg<R>{buf[3 * (j0 + k)], buf[3 * (j0 + k) + 1], buf[3 * (j0 + k) + 2]});
+      }
+      Agg<R> tot;
+      LS<R> st = dir == 0 ? block_scan_dir<R, false>(sm, f, run, &tot) : block_scan_dir<R, true>(sm, f, run, &tot);
+      if (dir == 0) {
+#pragma unroll 1
+        for (int k = 0; k < kPerT; ++k) {
+          if (j0 + k < nq) {
+            cbuf[2 * (j0 + k)] = st.m;
+            cbuf[2 * (j0 + k) + 1] = st.s;
+            st = agg_apply(Agg<R>{buf[3 * (j0 + k)], buf[3 * (j0 + k) + 1], buf[3 * (j0 + k) + 2]}, st);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int k = kPerT - 1; k >= 0; --k) {
+          if (j0 + k < nq) {
+            cbuf[2 * (j0 + k)] = st.m;
+            cbuf[2 * (j0 + k) + 1] = st.s;
+            st = agg_apply(Agg<R>{buf[3 * (j0 + k)], buf[3 * (j0 + k) + 1], buf[3 * (j0 + k) + 2]}, st);
+          }
+        }
+      }
+      run = agg_apply(tot, run);
+      __syncthreads();
+      for (int i = tid; i < 2 * nq; i += kThreads) {
+        const int j = i >> 1, d = i & 1;
+        carry[4 * (int64_t)(c0 + j) + 2 * dir + d] = cbuf[i];
+      }
+    }
   }
 }
 
 // Last CTA, line batches: each thread scans the tile maps of whole lines
-// (a line holds a few tiles) into their carries; lines start empty.
+// (a line holds a few tiles) into their carries; lines start empty.  The
+// maps of a chunk of tiles are requested before the chain uses them.
 template <class R>
 __device__ void carry_scan_lines(const R* agg, R* carry, int lines, int C) {
+  constexpr int kChunk = 4;
   for (int l = threadIdx.x; l < lines; l += kThreads) {
-    const int64_t b = (int64_t)l * C;
+    const int64_t b0 = (int64_t)l * C;
     LS<R> st = ls_empty<R>();
-    for (int t = 0; t < C; ++t) {
-      carry[4 * (b + t) + 0] = st.m;
-      carry[4 * (b + t) + 1] = st.s;
-      const R* q = agg + 6 * (b + t);
-      st = agg_apply(Agg<R>{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2)}, st);
+    for (int c = 0; c < C; c += kChunk) {
+      Agg<R> m[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) m[k] = (c + k < C) ? ld_map(agg + 6 * (b0 + c + k)) : agg_identity<R>();
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        if (c + k < C) {
+          carry[4 * (b0 + c + k) + 0] = st.m;
+          carry[4 * (b0 + c + k) + 1] = st.s;
+          st = agg_apply(m[k], st);
+        }
+      }
     }
     st = ls_empty<R>();
-    for (int t = C - 1; t >= 0; --t) {
-      carry[4 * (b + t) + 2] = st.m;
-      carry[4 * (b + t) + 3] = st.s;
-      const R* q = agg + 6 * (b + t) + 3;
-      st = agg_apply(Agg<R>{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2)}, st);
+    for (int c = C; c > 0; c -= kChunk) {
+      Agg<R> m[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        m[k] = (c - 1 - k >= 0) ? ld_map(agg + 6 * (b0 + c - 1 - k) + 3) : agg_identity<R>();
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        if (c - 1 - k >= 0) {
+          carry[4 * (b0 + c - 1 - k) + 2] = st.m;
+          carry[4 * (b0 + c - 1 - k) + 3] = st.s;
+          st = agg_apply(m[k], st);
+        }
+      }
     }
   }
 }
 
-// Last CTA: float64 sum of the C per-tile partial sums (all threads).
+// Last CTA: this thread's share of the float64 sum of the C per-tile partials
+__device__ __forceinline__ double load_parts(const double* part, int C) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int t = threadIdx.x;
+#pragma unroll 1
+  for (; t + 3 * kThreads < C; t += 4 * kThreads) {
+    s0 += __ldcg(part + t);
+    s1 += __ldcg(part + t + kThreads);
+    s2 += __ldcg(part + t + 2 * kThreads);
+    s3 += __ldcg(part + t + 3 * kThreads);
+  }
+  for (; t < C; t += kThreads) s0 += __ldcg(part + t);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Last CTA: sum over the block (all threads; every thread gets the total)
 template <class R>
-__device__ double sum_parts(const double* part, int C, TileSmem<R>& sm) {
-  double s = 0.0;
-  for (int t = threadIdx.x; t < C; t += kThreads) s += __ldcg(part + t);
+__device__ double block_sum(double s, TileSmem<R>& sm) {
   s = warp_sum(s);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = s;
@@ -462,25 +588,86 @@ __device__ double sum_parts(const double* part, int C, TileSmem<R>& sm) {
   return tot;
 }
 
+// Outputs at one O point (smem slot oi) from l2 = log2 S in its frame: the
+// division of eq. iteration in the log domain (new absorbed potential), the
+// log2 sums of a first 2D pass, products, and the marginal error term.
 template <class R, int kFlags>
-#ifndef FINOM_MINB
-#define FINOM_MINB 4
-#endif
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_apply(ApplyArgs<R> a) {
+__device__ __forceinline__ void emit_o(const ApplyArgs<R>& a, TileSmem<R>& sm, int oi, R l2, int64_t ob,
+                                       int o_start, R& err) {
+  using T = Tr<R>;
+  if constexpr ((kFlags & F_OUT_POT) != 0) sm.pot[oi] = T::sub(sm.pot[oi], l2);
+  if constexpr ((kFlags & F_QOUT) != 0) {
+    // an empty sum (no weight on the line) stays empty
+    sm.pot[oi] = (l2 > T::kNegBig * R(0.5)) ? T::sub(sm.pot[oi], l2) : T::neg(T::none());
+  }
+  if constexpr ((kFlags & (F_OUT_LIN | F_OUT_LOG)) != 0) {
+    double v;
+    if constexpr ((kFlags & F_OUT_LIN) != 0) v = exp2((double)l2);
+    else v = 0.69314718055994530942 * (double)l2;
+    a.out[ob + (int64_t)(o_start + oi - 1) * a.o_es] = v;
+  }
+  if constexpr ((kFlags & F_ERR) != 0) {
+    const R mo = (R)sm.mass[oi];
+    if (a.o_scale > R(0)) {
+      err += fabs(a.o_scale * T::ex2(l2) - mo);
+    } else {
+      // S - 1 without the cancellation of ex2(l2) - 1 near l2 = 0
+      const R x = l2 * R(0.69314718055994530942);
+      const R sm1 = (fabs(x) < R(0.03)) ? x * (R(1) + x * (R(0.5) + x * (R(1.0 / 6) + x * R(1.0 / 24))))
+                                        : T::ex2(l2) - R(1);
+      err += mo * fabs(sm1);
+    }
+  }
+}
+
+// The end of a launch, in the CTA that finishes last: carries of the next
+// application, the float64 error sum, the loop control.  This code runs once
+// per launch on one SM, mostly from a cold instruction cache: its loops stay
+// rolled.
+template <class R, int kFlags>
+__device__ void finish_launch(const ApplyArgs<R>& a, TileSmem<R>& sm, int units) {
+  // the error partials are requested first so that their loads overlap the scan
+  double ep = 0.0;
+  if (kFlags & F_ERR) ep = load_parts(a.part, units);
+  if (kFlags & (F_NEXT | F_AGG_ONLY)) {
+    if (a.lines == 1) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+    else carry_scan_lines<R>(a.agg_out, a.carry_out, a.lines, a.C);
+  }
+  double errsum = 0.0;
+  if (kFlags & F_ERR) errsum = block_sum<R>(ep, sm);
+  if (threadIdx.x == 0) {
+    int32_t* c = a.ctrl;
+    if (kFlags & F_ERR) {
+      a.scal[0] = errsum;
+      if (errsum <= a.tol) {
+        c[1] = 1;
+        c[3] = c[2];
+        c[4] = 1;
+      }
+    }
+    if ((kFlags & F_ITER_END) && !c[1]) {
+      c[2] += 1;
+      if ((int64_t)c[2] >= a.maxit) {
+        c[1] = 1;
+        c[3] = c[2];
+      }
+    }
+    c[0] = 0;
+  }
+}
+
+// One unit (line, tile) of a launch: steps 1-4 of the header comment.
+template <class R, int kFlags>
+__device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& sm, int unit, bool first) {
   constexpr bool kAggOnly = (kFlags & F_AGG_ONLY) != 0;
   constexpr bool kFrameW = (kFlags & F_FRAME_W) != 0;
   constexpr bool kWValid = (kFlags & F_WVALID) != 0;
   using T = Tr<R>;
   using Pot = typename T::Pot;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<R>& sm = *reinterpret_cast<TileSmem<R>*>(smem_raw);
-
-  if ((kFlags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return;
-
   const int tid = threadIdx.x;
   const int C = a.C;
-  const int line = (int)(blockIdx.x / (unsigned)C);
-  const int tile = (int)blockIdx.x - line * C;
+  const int line = unit / C;
+  const int tile = unit - line * C;
   const int64_t ob = (int64_t)line * a.o_ls, wb = (int64_t)line * a.w_ls;
   const int64_t k0 = (int64_t)tile * kTile;
   const int64_t kend = min(k0 + (int64_t)kTile, a.L);
@@ -506,38 +693,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   R g[kElems];
   load_gaps<R>(a.gap, seg, g);
 
-  // stage the tile's O and W data (plus the point before the tile) in shared memory
+  // stage the tile's O and W data (plus the point before the tile) in shared
+  // memory.  The O side is never written by the launch just before this one
+  // (every launch writes only its own O side, and consecutive launches
+  // alternate sides), so the first unit stages it before waiting for that
+  // launch (programmatic dependent launch); the W side, the carries and the
+  // loop control come after the wait.
   if (!kFrameW) {
     for (int i = tid; i < n_o + 1; i += kThreads) {
       const int64_t gi = ob + (int64_t)max(o_start - 1 + i, 0) * a.o_es;
-#if FINOM_CPASYNC
       cp_async(&sm.pot[i], &a.pO[gi]);
       cp_async(&sm.mass[i], &a.mO[gi]);
-#else
-      sm.pot[i] = a.pO[gi];
-      sm.mass[i] = a.mO[gi];
-#endif
-    }
-  }
-  if (a.w_uniform <= R(0) || (kFlags & F_NEXT)) {
-    for (int i = tid; i < n_w + 1; i += kThreads) {
-      const int64_t gi = wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
-#if FINOM_CPASYNC
-      cp_async(&sm.pot[wofs + i], &a.pW[gi]);
-      if (!kWValid) cp_async(&sm.mass[wofs + i], &a.mW[gi]);
-#else
-      sm.pot[wofs + i] = a.pW[gi];
-      if (!kWValid) sm.mass[wofs + i] = a.mW[gi];
-#endif
     }
   }
   const int o_before = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
   // threads past the end of the sequence own no points; keep their index in range
   const int w_before = min((int)(seg - k0) - o_before, n_w);
-#if FINOM_CPASYNC
+  if (first) {
+    griddep_wait();
+    if ((kFlags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) {
+      cp_async_commit_wait();
+      return false;
+    }
+    griddep_launch_dependents();
+  }
+  if (a.w_uniform <= R(0) || (kFlags & F_NEXT)) {
+    for (int i = tid; i < n_w + 1; i += kThreads) {
+      const int64_t gi = wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
+      cp_async(&sm.pot[wofs + i], &a.pW[gi]);
+      if (!kWValid) cp_async(&sm.mass[wofs + i], &a.mW[gi]);
+    }
+  }
   cp_async_commit_wait();
   __syncthreads();
-#endif
 
   if constexpr (kFrameW) {
     // frame of an O point: minus the potential of the last W point before it
@@ -567,13 +755,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
-    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)blockIdx.x);
-    if (last_cta<R>(a.ctrl, a.lines * C, sm)) {
-      if (a.lines == 1) carry_scan<R>(a.agg_out, a.carry_out, C, sm);
-      else carry_scan_lines<R>(a.agg_out, a.carry_out, a.lines, C);
-      if (tid == 0) a.ctrl[0] = 0;
-    }
-    return;
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)unit);
+    return true;
   }
 
   // entry states of the thread's points: forward (from the left) and
@@ -582,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   {
     LS<R> cf = ls_empty<R>(), cb = ls_empty<R>();
     if (a.carry_in) {
-      const R* c = a.carry_in + 4 * (int64_t)blockIdx.x;
+      const R* c = a.carry_in + 4 * (int64_t)unit;
       cf = {__ldg(c + 0), __ldg(c + 1)};
       cb = {__ldg(c + 2), __ldg(c + 3)};
     }
@@ -597,16 +780,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
 
   // lam_e = log2 S_e in the point's own frame (S = p + q, eq. decompose to p+q):
   //   p_e = D_e + log2(entry_f (+) weights t <= e),  q_e = -PB_e + log2(entry_b' (+) weights t > e)
-  // with entry_b' = the backward entry state carried to the segment start.
-  R lam[kElems];
+  // with entry_b' = the backward entry state carried to the segment start;
+  // each lam goes straight to its O point's outputs
   const R ebm = eb.m + PB[kElems - 1];
+  int oi = o_before;   // smem index of the O point before the current one
+  R err = R(0);
   if (fast) {
-    R qsuf[kElems];
+    // backward terms strictly after e, in place
     R acc = R(0);
 #pragma unroll
     for (int e = kElems - 1; e >= 0; --e) {
-      qsuf[e] = acc;         // backward terms strictly after e
-      acc += L2[e];
+      const R t = L2[e];
+      L2[e] = acc;
+      acc += t;
     }
     // fold each entry state into its local sum once per thread; a part with
     // no weight must not set the level
@@ -620,14 +806,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
       pf += L1[e];           // forward terms up to e
-      const R sf = fma(cF1, pf, cF0), sb = fma(cB1, qsuf[e], cB0);
-      const R a1 = (sf > R(0)) ? LF + D[e] : T::kNegBig;
-      const R a2 = (sb > R(0)) ? LB - PB[e] : T::kNegBig;
-      const R M = fmax(a1, a2);
-      lam[e] = M + T::lg2(fma(sf, T::ex2(a1 - M), sb * T::ex2(a2 - M)));
+      if ((omask >> e) & 1u) {
+        const R sf = fma(cF1, pf, cF0), sb = fma(cB1, L2[e], cB0);
+        const R a1 = (sf > R(0)) ? LF + D[e] : T::kNegBig;
+        const R a2 = (sb > R(0)) ? LB - PB[e] : T::kNegBig;
+        const R M = fmax(a1, a2);
+        emit_o<R, kFlags>(a, sm, ++oi, M + T::lg2(fma(sf, T::ex2(a1 - M), sb * T::ex2(a2 - M))), ob,
+                          o_start, err);
+      }
     }
   } else {
     // levels spread over more than 60 bits: running-max log-sums
+    R lam[kElems];
     R fm[kElems], fs[kElems];
     R m = ef.m, sv = ef.s;
 #pragma unroll
@@ -644,41 +834,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
       lam[e] = s2.m + T::lg2(s2.s);
       if (mt[e] > R(0)) ls_add_fast(m, sv, L2[e], mt[e]);
     }
-  }
-
-  // outputs at the O points: the division of eq. iteration in the log domain
-  int oi = o_before;   // smem index of the O point before the current one
-  R err = R(0);
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    if ((omask >> e) & 1u) {
-      ++oi;
-      const R l2 = lam[e];
-      if constexpr ((kFlags & F_OUT_POT) != 0) sm.pot[oi] = T::sub(sm.pot[oi], l2);
-      if constexpr ((kFlags & F_QOUT) != 0) {
-        // an empty sum (no weight on the line) stays empty
-        sm.pot[oi] = (l2 > T::kNegBig * R(0.5)) ? T::sub(sm.pot[oi], l2) : T::neg(T::none());
-      }
-      if constexpr ((kFlags & (F_OUT_LIN | F_OUT_LOG)) != 0) {
-        double v;
-        if constexpr ((kFlags & F_OUT_LIN) != 0) v = exp2((double)l2);
-        else v = 0.69314718055994530942 * (double)l2;
-        a.out[ob + (int64_t)(o_start + oi - 1) * a.o_es] = v;
-      }
-      if constexpr ((kFlags & F_ERR) != 0) {
-        const R mo = (R)sm.mass[oi];
-        if (a.o_scale > R(0)) {
-          err += fabs(a.o_scale * T::ex2(l2) - mo);
-        } else {
-          // S - 1 without the cancellation of ex2(l2) - 1 near l2 = 0
-          const R x = l2 * R(0.69314718055994530942);
-          const R sm1 = (fabs(x) < R(0.03))
-                            ? x * (R(1) + x * (R(0.5) + x * (R(1.0 / 6) + x * R(1.0 / 24))))
-                            : T::ex2(l2) - R(1);
-          err += mo * fabs(sm1);
-        }
-      }
-    }
+    for (int e = 0; e < kElems; ++e)
+      if ((omask >> e) & 1u) emit_o<R, kFlags>(a, sm, ++oi, lam[e], ob, o_start, err);
   }
 
   if (kFlags & F_ERR) {
@@ -690,7 +848,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     double tot = 0.0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
-    a.part[blockIdx.x] = tot;
+    a.part[unit] = tot;
   }
   if constexpr ((kFlags & F_OUT_POT) != 0) {
     for (int i = tid; i < n_o; i += kThreads) a.pO_out[ob + (int64_t)(o_start + i) * a.o_es] = sm.pot[1 + i];
@@ -701,40 +859,40 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   }
   if (kFlags & F_NEXT) {
     // next application: O' = current W (frames = current W potentials),
-    // W' = current O (new potentials, same masses); same gaps
+    // W' = current O (new potentials, same masses); same gaps (reloaded: they
+    // are not kept in registers through the outputs)
+    load_gaps<R>(a.gap, seg, g);
     seg_terms<R>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0), D,
                  PB, L1, L2, mt);
     (void)seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
-    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)blockIdx.x);
+    if (tid < 64) rake_reduce<R>(sm, a.agg_out + 6 * (int64_t)unit);
   }
+  return true;
+}
 
-  if (last_cta<R>(a.ctrl, a.lines * C, sm)) {
-    if (kFlags & F_NEXT) carry_scan<R>(a.agg_out, a.carry_out, C, sm);
-    double errsum = 0.0;
-    if (kFlags & F_ERR) errsum = sum_parts<R>(a.part, a.lines * C, sm);
-    if (tid == 0) {
-      int32_t* c = a.ctrl;
-      if (kFlags & F_ERR) {
-        a.scal[0] = errsum;
-        if (errsum <= a.tol) {
-          c[1] = 1;
-          c[3] = c[2];
-          c[4] = 1;
-        }
-      }
-      if ((kFlags & F_ITER_END) && !c[1]) {
-        c[2] += 1;
-        if ((int64_t)c[2] >= a.maxit) {
-          c[1] = 1;
-          c[3] = c[2];
-        }
-      }
-      c[0] = 0;
-    }
+#ifndef FINOM_MINB
+#define FINOM_MINB 4
+#endif
+// Persistent CTAs: as many as fit on the device; CTA b handles the units
+// b, b + G, b + 2G, ... (G = grid size; a counter shared by all CTAs costs
+// more in contention than it gains in balance).  The last CTA to finish
+// (ticket ctrl[0]) scans the new tile maps into carries, reduces the error
+// and updates the loop control.
+template <class R, int kFlags>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_apply(ApplyArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem<R>& sm = *reinterpret_cast<TileSmem<R>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int units = a.lines * a.C;
+  for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    if (!apply_unit<R, kFlags>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
+    __syncthreads();
   }
+  griddep_wait();   // (a no-op after the first unit's wait)
+  if (last_cta<R>(a.ctrl, (int)gridDim.x, sm)) finish_launch<R, kFlags>(a, sm, units);
 }
 
 }  // namespace finom
