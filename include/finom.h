@@ -116,6 +116,47 @@ finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const 
  */
 finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64_t* M);
 
+/*
+ * finom_plan_batch -- plan for B independent 1D problems solved together
+ * (batching: one launch per half step covers every instance; not a form the
+ * paper describes, its arithmetic per instance is Algorithm 1's).
+ *   x: sum of N_b doubles, y: sum of M_b doubles (device), instance b's points
+ *      at x[offx[b] .. offx[b+1]) and y[offy[b] .. offy[b+1]), each run sorted
+ *      non-decreasing and finite.
+ *   offx, offy: B + 1 int64 offsets (HOST arrays), offx[0] = offy[0] = 0,
+ *      every instance with N_b >= 1 and M_b >= 1.
+ *   eps: B doubles (HOST array), each > 0 and finite.
+ *   1 <= B <= 2^24; the padded merged length (each instance rounded up to
+ *   2048 points) and each of sum N_b, sum M_b must stay below 2^31.
+ * Only finom_solve_batch, finom_plan_info / finom_plan_shape (totals),
+ * finom_plan_instances and finom_plan_destroy take a batch plan; the other
+ * calls return FINOM_ENOTSUP.  Synchronous.  Errors as finom_plan.
+ */
+finom_status finom_plan_batch(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
+                              int64_t B, const double* eps, finom_precision prec, void* stream,
+                              finom_plan_t* out);
+
+/* Number of instances of a batch plan (0 for other plans). */
+finom_status finom_plan_instances(finom_plan_t plan, int64_t* B);
+
+/*
+ * finom_solve_batch -- Algorithm 1 for every instance of a batch plan, each
+ * with its own masses and eps: the start phi = 1/N_b, psi = 1/M_b, the
+ * check || diag(psi) K^T phi - v ||_1 <= tol at every loop head, at most
+ * maxit iterations.  An instance retires at its own stop (its tiles are
+ * skipped from then on); the call returns when the last one has retired.
+ *   u, v: masses in the layout of x, y (device), normalised per instance.
+ *   f, g: outputs in the same layout (cost units, -inf where the mass is 0),
+ *      the potentials of each instance's stop state.
+ *   res: B finom_result (HOST array): per instance W1 and the marginal error
+ *      of the returned potentials in float64, the loop's own error, the dual,
+ *      the iterations; converged = the float64 error is <= tol (FP32 plans)
+ *      or the loop's check passed (FP64 plans).
+ * Synchronous.  FINOM_EINVAL for bad masses (any instance).
+ */
+finom_status finom_solve_batch(finom_plan_t plan, const double* u, const double* v, double tol,
+                               int64_t maxit, double* f, double* g, finom_result* res, void* stream);
+
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 finom_status finom_plan_destroy(finom_plan_t plan);
 

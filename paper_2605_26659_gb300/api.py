@@ -63,6 +63,9 @@ _SIGS = {
     "finom_kv_log_noalloc": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "finom_plan_2d": ([_P, _P, _I64, _P, _P, _I64, _D, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_plan_shape": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_plan_batch": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "finom_plan_instances": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_solve_batch": ([_P, _P, _P, _D, _I64, _P, _P, _P, _P], ctypes.c_int),
 }
 
 
@@ -124,6 +127,7 @@ class Plan:
     dim: int = 1
     nx: int = 0          # 2D: grid side along x (N)
     ny: int = 0          # 2D: grid side along y (M)
+    batch: int = 0       # batch plans: number of instances
 
     def __del__(self):
         try:
@@ -165,6 +169,47 @@ def finom_plan_shape(plan: Plan):
     d, n, m = _I32(), _I64(), _I64()
     _check(_lib.finom_plan_shape(plan.handle, ctypes.byref(d), ctypes.byref(n), ctypes.byref(m)))
     return d.value, n.value, m.value
+
+
+def finom_plan_batch(x, offx, y, offy, eps, precision="f32_log", stream=None) -> Plan:
+    """Batch of independent 1D problems: x, y concatenated (device float64),
+    offx, offy: B + 1 offsets (host sequences), eps: B values (host)."""
+    import numpy as np
+    import torch
+    load()
+    ox = np.ascontiguousarray(offx, dtype=np.int64)
+    oy = np.ascontiguousarray(offy, dtype=np.int64)
+    ep = np.ascontiguousarray(eps, dtype=np.float64)
+    B = len(ep)
+    if len(ox) != B + 1 or len(oy) != B + 1:
+        raise ValueError("offx and offy need B + 1 entries")
+    h = ctypes.c_void_p()
+    _check(_lib.finom_plan_batch(_dev(x, int(ox[-1]), torch.float64, "x"), ox.ctypes.data,
+                                 _dev(y, int(oy[-1]), torch.float64, "y"), oy.ctypes.data, B, ep.ctypes.data,
+                                 _PREC[precision], _stream(stream), ctypes.byref(h)))
+    return Plan(h, int(ox[-1]), int(oy[-1]), float(ep[0]), _PREC[precision], x.device.index or 0, batch=B)
+
+
+def finom_plan_instances(plan: Plan):
+    b = _I64()
+    _check(_lib.finom_plan_instances(plan.handle, ctypes.byref(b)))
+    return b.value
+
+
+def finom_solve_batch(plan: Plan, u, v, tol, maxit, f=None, g=None, stream=None):
+    """Solve every instance; returns (f, g, list of per-instance result dicts)."""
+    import torch
+    dev = torch.device("cuda", plan.device)
+    if f is None:
+        f = torch.empty(plan.N, dtype=torch.float64, device=dev)
+    if g is None:
+        g = torch.empty(plan.M, dtype=torch.float64, device=dev)
+    res = (FinomResult * plan.batch)()
+    _check(_lib.finom_solve_batch(plan.handle, _dev(u, plan.N, torch.float64, "u"),
+                                  _dev(v, plan.M, torch.float64, "v"), float(tol), int(maxit),
+                                  _dev(f, plan.N, torch.float64, "f"), _dev(g, plan.M, torch.float64, "g"),
+                                  ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
+    return f, g, [r.as_dict() for r in res]
 
 
 def finom_plan_destroy(plan: Plan):

@@ -110,7 +110,8 @@ void free_state(finom_plan_s* p) {
     cudaFree(st.py[q]);
   }
   void* bufs[] = {st.mu, st.nu, st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part,
-                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.t2, st.z};
+                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.t2, st.z,
+                  st.ictl, st.ierr, st.itol, st.iuni};
   for (void* b : bufs) cudaFree(b);
   if (st.stream) cudaStreamDestroy(st.stream);
   st = SolveState();
@@ -417,6 +418,15 @@ bool bad_plan(finom_plan_t p) {
   return false;
 }
 
+// the calls for one problem refuse batch plans
+bool batch_plan(finom_plan_t p, const char* what) {
+  if (p && p->B > 0) {
+    set_error(std::string(what) + ": a batch plan takes finom_solve_batch");
+    return true;
+  }
+  return false;
+}
+
 }  // namespace
 }  // namespace finom
 
@@ -459,6 +469,7 @@ finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double*
 finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const double* a,
                          const double* b, double* out, void* stream) {
   if (bad_plan(p)) return FINOM_EINVAL;
+  if (batch_plan(p, "kernel product")) return FINOM_ENOTSUP;
   if (!out || (!logmode && !b) || (logmode && (!a || !b))) {
     set_error("kernel product: null argument");
     return FINOM_EINVAL;
@@ -550,8 +561,80 @@ finom_status finom_plan_destroy(finom_plan_t plan) {
   free_state(plan);
   free_plan(plan);
   plan2d_free(plan);
+  plan_batch_free(plan);
   delete plan;
   return FINOM_OK;
+}
+
+finom_status finom_plan_batch(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
+                              int64_t B, const double* eps, finom_precision prec, void* stream,
+                              finom_plan_t* out) {
+  if (!out) {
+    set_error("finom_plan_batch: out is NULL");
+    return FINOM_EINVAL;
+  }
+  *out = nullptr;
+  if (!x || !y || !offx || !offy || !eps || B < 1 || B > (int64_t)1 << 24 ||
+      (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
+    set_error("finom_plan_batch: need x, y, offx, offy, eps non-null, 1 <= B <= 2^24, known precision");
+    return FINOM_EINVAL;
+  }
+  if (offx[0] != 0 || offy[0] != 0) {
+    set_error("finom_plan_batch: offx[0] and offy[0] must be 0");
+    return FINOM_EINVAL;
+  }
+  int64_t tiles = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t n = offx[b + 1] - offx[b], m = offy[b + 1] - offy[b];
+    if (n < 1 || m < 1 || !(eps[b] > 0.0) || !std::isfinite(eps[b])) {
+      set_error("finom_plan_batch: instance " + std::to_string((long long)b) +
+                " needs at least one x and one y point and eps > 0 finite");
+      return FINOM_EINVAL;
+    }
+    tiles += (n + m + kTile - 1) / kTile;
+  }
+  if (tiles * kTile > (int64_t)INT32_MAX || offx[B] > (int64_t)INT32_MAX || offy[B] > (int64_t)INT32_MAX) {
+    set_error("finom_plan_batch: batch too large");
+    return FINOM_EINVAL;
+  }
+  finom_plan_s* p = new (std::nothrow) finom_plan_s();
+  if (!p) return FINOM_ENOMEM;
+  p->eps = eps[0];
+  p->prec = prec;
+  cudaGetDevice(&p->device);
+  finom_status rc = plan_batch_build(p, x, offx, y, offy, B, eps, (cudaStream_t)stream);
+  if (rc != FINOM_OK) {
+    free_plan(p);
+    plan_batch_free(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_instances(finom_plan_t plan, int64_t* B) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (B) *B = plan->B;
+  return FINOM_OK;
+}
+
+finom_status finom_solve_batch(finom_plan_t plan, const double* u, const double* v, double tol,
+                               int64_t maxit, double* f, double* g, finom_result* res, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->B == 0) {
+    set_error("finom_solve_batch: not a batch plan");
+    return FINOM_EINVAL;
+  }
+  if (!u || !v || !f || !g || !res || !(tol >= 0.0) || maxit < 0) {
+    set_error("finom_solve_batch: need u, v, f, g, res non-null, tol >= 0, maxit >= 0");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  finom_status rc = solve_batch(plan, u, v, tol, maxit, f, g, res, (cudaStream_t)stream);
+  if (rc != FINOM_OK)
+    for (int64_t b = 0; b < plan->B; ++b) res[b].status = rc;
+  return rc;
 }
 
 finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64_t* M) {
@@ -574,6 +657,7 @@ finom_status finom_plan_info(finom_plan_t plan, int64_t* N, int64_t* M, double* 
 
 finom_status finom_dividing_index(finom_plan_t plan, int32_t* zeta, int32_t* zetaT, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_dividing_index")) return FINOM_ENOTSUP;
   if (plan->dim != 1) {
     set_error("finom_dividing_index: a 2D plan has one dividing index per axis; use 1D plans of the axes");
     return FINOM_ENOTSUP;
@@ -608,6 +692,7 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
                          int64_t maxit, double* f, double* g, int32_t warm, finom_result* res,
                          void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve")) return FINOM_ENOTSUP;
   if (!u || !v || !f || !g || !(tol >= 0.0) || maxit < 0) {
     set_error("finom_solve: need u, v, f, g non-null, tol >= 0, maxit >= 0");
     return FINOM_EINVAL;
@@ -628,6 +713,7 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
 finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double* v, double tol,
                                int64_t maxit, const double* f0, const double* g0, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve_begin")) return FINOM_ENOTSUP;
   if (!u || !v || !(tol >= 0.0) || maxit < 0) {
     set_error("finom_solve_begin: need u, v non-null, tol >= 0, maxit >= 0");
     return FINOM_EINVAL;
@@ -641,6 +727,7 @@ finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double*
 
 finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve_step")) return FINOM_ENOTSUP;
   if (!plan->st.active || iterations < 0) {
     set_error("finom_solve_step: no solve in progress (finom_solve_begin first) or negative count");
     return FINOM_EINVAL;
@@ -665,6 +752,7 @@ finom_status finom_solve_poll(finom_plan_t plan, int32_t* done, int64_t* iters, 
 finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_result* res,
                              void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve_end")) return FINOM_ENOTSUP;
   if (!plan->st.active || !f || !g) {
     set_error("finom_solve_end: no solve in progress or null output");
     return FINOM_EINVAL;
@@ -679,6 +767,7 @@ finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_resu
 finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, const double* f,
                         const double* g, double* w1, double* err, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_cost")) return FINOM_ENOTSUP;
   if (!u || !v || !f || !g || !w1 || !err) {
     set_error("finom_cost: null argument");
     return FINOM_EINVAL;

@@ -70,6 +70,10 @@ finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) 
     FINOM_CASE(kMode2AggOuter)
     FINOM_CASE(kMode2AggInner | F_CHECK_DONE)
     FINOM_CASE(kMode2AggOuter | F_CHECK_DONE)
+    FINOM_CASE(kModeBHalfY)
+    FINOM_CASE(kModeBHalfX)
+    FINOM_CASE(kModeBAgg)
+    FINOM_CASE(kModeBCheck)
 #undef FINOM_CASE
     default:
       set_error("k_apply: unsupported launch mode");

@@ -52,6 +52,7 @@ enum : int {
   F_FRAME_W = 256,   // O frames: minus the potential of the last W point before (no O data)
   F_WVALID = 512,    // W masses: 1 where the W potential is finite, else 0 (no W masses)
   F_QOUT = 1024,     // write log2 of the sums at the O points to q_out (no division)
+  F_BATCH = 2048,    // units are the tiles of a batch of independent 1D instances
 };
 
 // the launch kinds (compile-time flag sets)
@@ -71,6 +72,12 @@ constexpr int kMode2Log = F_OUT_LOG | F_WVALID;
 constexpr int kMode2Lin = F_OUT_LIN | F_WVALID;
 constexpr int kMode2AggInner = F_AGG_ONLY | F_FRAME_W;
 constexpr int kMode2AggOuter = F_AGG_ONLY | F_WVALID;
+// batches of 1D instances: per-instance carries, errors and retirement come
+// from k_batch_end, launched after each of these
+constexpr int kModeBHalfY = F_OUT_POT | F_NEXT | F_ERR | F_CHECK_DONE | F_BATCH;
+constexpr int kModeBHalfX = F_OUT_POT | F_NEXT | F_CHECK_DONE | F_BATCH;
+constexpr int kModeBAgg = F_AGG_ONLY | F_BATCH;
+constexpr int kModeBCheck = F_ERR | F_BATCH;
 
 template <class R>
 struct ApplyArgs {
@@ -86,6 +93,15 @@ struct ApplyArgs {
   int64_t o_ls, o_es; // O-side arrays: offset between lines, stride between points
   int64_t w_ls, w_es; // W-side arrays: the same
   const int32_t* fw;  // F_FRAME_W: per tile, the W point whose potential frames the O point before it
+  // F_BATCH: units are global tiles; instance b owns tiles itile[b] .. itile[b+1]-1,
+  // its points x[ioffx[b] ..), y[ioffy[b] ..) of the packed arrays, and C_b + 1
+  // entries of tile_x0 from itile[b] + b.  Gaps and type bits are packed per tile.
+  const int32_t* tinst;   // per tile: its instance
+  const int32_t* itile;   // B + 1
+  const int64_t* ioffx;   // B + 1
+  const int64_t* ioffy;   // B + 1
+  const int32_t* idone;   // per instance: nonzero once retired (its tiles are skipped)
+  const R* iuni;          // per instance: (1/n_W, 1/n_O) while the start phi, psi apply, else NULL
   const Pot* pO;      // O-side absorbed potentials (the frame), log2 units
   const Mass* mO;     // O-side masses
   Pot* pO_out;        // O-side new potentials
@@ -593,7 +609,7 @@ __device__ double block_sum(double s, TileSmem<R>& sm) {
 // log2 sums of a first 2D pass, products, and the marginal error term.
 template <class R, int kFlags>
 __device__ __forceinline__ void emit_o(const ApplyArgs<R>& a, TileSmem<R>& sm, int oi, R l2, int64_t ob,
-                                       int o_start, R& err) {
+                                       int o_start, R o_scale, R& err) {
   using T = Tr<R>;
   if constexpr ((kFlags & F_OUT_POT) != 0) sm.pot[oi] = T::sub(sm.pot[oi], l2);
   if constexpr ((kFlags & F_QOUT) != 0) {
@@ -608,8 +624,8 @@ __device__ __forceinline__ void emit_o(const ApplyArgs<R>& a, TileSmem<R>& sm, i
   }
   if constexpr ((kFlags & F_ERR) != 0) {
     const R mo = (R)sm.mass[oi];
-    if (a.o_scale > R(0)) {
-      err += fabs(a.o_scale * T::ex2(l2) - mo);
+    if (o_scale > R(0)) {
+      err += fabs(o_scale * T::ex2(l2) - mo);
     } else {
       // S - 1 without the cancellation of ex2(l2) - 1 near l2 = 0
       const R x = l2 * R(0.69314718055994530942);
@@ -664,14 +680,42 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   constexpr bool kWValid = (kFlags & F_WVALID) != 0;
   using T = Tr<R>;
   using Pot = typename T::Pot;
+  constexpr bool kBatch = (kFlags & F_BATCH) != 0;
   const int tid = threadIdx.x;
   const int C = a.C;
-  const int line = unit / C;
-  const int tile = unit - line * C;
-  const int64_t ob = (int64_t)line * a.o_ls, wb = (int64_t)line * a.w_ls;
+  // geometry of the unit: its line (or instance), tile, sequence length, the
+  // offsets of its O and W data and of its packed gaps and type bits
+  int line, tile, x0, x1;
+  int64_t L, ob, wb, pos0 = 0;
+  R w_uniform = a.w_uniform, o_scale = a.o_scale;
+  if constexpr (kBatch) {
+    const int b = a.tinst[unit];
+    const int tb = a.itile[b];
+    line = b;
+    tile = unit - tb;
+    const int64_t xb = a.ioffx[b], yb = a.ioffy[b];
+    L = (a.ioffx[b + 1] - xb) + (a.ioffy[b + 1] - yb);
+    ob = a.o_is_x ? xb : yb;
+    wb = a.o_is_x ? yb : xb;
+    const int32_t* tx = a.tile_x0 + tb + b;
+    x0 = tx[tile];
+    x1 = tx[tile + 1];
+    pos0 = (int64_t)tb * kTile;
+    if (a.iuni) {
+      w_uniform = a.iuni[2 * b];
+      o_scale = a.iuni[2 * b + 1];
+    }
+  } else {
+    line = unit / C;
+    tile = unit - line * C;
+    L = a.L;
+    ob = (int64_t)line * a.o_ls;
+    wb = (int64_t)line * a.w_ls;
+    x0 = a.tile_x0[tile];
+    x1 = a.tile_x0[tile + 1];
+  }
   const int64_t k0 = (int64_t)tile * kTile;
-  const int64_t kend = min(k0 + (int64_t)kTile, a.L);
-  const int x0 = a.tile_x0[tile], x1 = a.tile_x0[tile + 1];
+  const int64_t kend = min(k0 + (int64_t)kTile, L);
   const int y0 = (int)(k0 - x0), y1 = (int)(kend - x1);
   const int o_start = a.o_is_x ? x0 : y0;
   const int n_o = a.o_is_x ? (x1 - x0) : (y1 - y0);
@@ -681,17 +725,18 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
 
   // this thread's points
   const int64_t seg = k0 + (int64_t)tid * kElems;
+  const int64_t gseg = seg + pos0;   // position in the packed gap / type-bit arrays
   uint32_t vmask = 0;
-  if (seg < a.L) {
-    int64_t nv = a.L - seg;
+  if (seg < L) {
+    int64_t nv = L - seg;
     vmask = nv >= kElems ? ((1u << kElems) - 1u) : ((1u << nv) - 1u);
   }
-  uint32_t bits = (seg < a.L) ? ((a.tbits[seg >> 5] >> (seg & 31)) & ((1u << kElems) - 1u)) : 0u;
+  uint32_t bits = (seg < L) ? ((a.tbits[gseg >> 5] >> (gseg & 31)) & ((1u << kElems) - 1u)) : 0u;
   const uint32_t xmask = bits & vmask, ymask = (~bits) & vmask;
   const uint32_t omask = a.o_is_x ? xmask : ymask;
   const uint32_t wmask = a.o_is_x ? ymask : xmask;
   R g[kElems];
-  load_gaps<R>(a.gap, seg, g);
+  load_gaps<R>(a.gap, gseg, g);
 
   // stage the tile's O and W data (plus the point before the tile) in shared
   // memory.  The O side is never written by the launch just before this one
@@ -717,7 +762,12 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     }
     griddep_launch_dependents();
   }
-  if (a.w_uniform <= R(0) || (kFlags & F_NEXT)) {
+  if (kBatch && (kFlags & F_CHECK_DONE) && a.idone[line]) {   // a retired instance
+    cp_async_commit_wait();
+    __syncthreads();
+    return true;
+  }
+  if (w_uniform <= R(0) || (kFlags & F_NEXT)) {
     for (int i = tid; i < n_w + 1; i += kThreads) {
       const int64_t gi = wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
       cp_async(&sm.pot[wofs + i], &a.pW[gi]);
@@ -731,7 +781,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     // frame of an O point: minus the potential of the last W point before it
     // (of the line's first W point when there is none); the O point before the
     // tile gets the frame its own tile gave it
-    const bool uni = a.w_uniform > R(0);
+    const bool uni = w_uniform > R(0);
     int oi = o_before, wl = w_before;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
@@ -748,7 +798,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   R D[kElems], PB[kElems], L1[kElems], L2[kElems], mt[kElems], MF, MB;
   Agg<R> mapF, mapB;
   seg_terms<R, kWValid>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
-                        a.w_uniform, D, PB, L1, L2, mt);
+                        w_uniform, D, PB, L1, L2, mt);
   const bool fast = seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
 
   if constexpr (kAggOnly) {
@@ -812,7 +862,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
         const R a2 = (sb > R(0)) ? LB - PB[e] : T::kNegBig;
         const R M = fmax(a1, a2);
         emit_o<R, kFlags>(a, sm, ++oi, M + T::lg2(fma(sf, T::ex2(a1 - M), sb * T::ex2(a2 - M))), ob,
-                          o_start, err);
+                          o_start, o_scale, err);
       }
     }
   } else {
@@ -836,7 +886,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     }
 #pragma unroll
     for (int e = 0; e < kElems; ++e)
-      if ((omask >> e) & 1u) emit_o<R, kFlags>(a, sm, ++oi, lam[e], ob, o_start, err);
+      if ((omask >> e) & 1u) emit_o<R, kFlags>(a, sm, ++oi, lam[e], ob, o_start, o_scale, err);
   }
 
   if (kFlags & F_ERR) {
@@ -861,7 +911,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     // next application: O' = current W (frames = current W potentials),
     // W' = current O (new potentials, same masses); same gaps (reloaded: they
     // are not kept in registers through the outputs)
-    load_gaps<R>(a.gap, seg, g);
+    load_gaps<R>(a.gap, gseg, g);
     seg_terms<R>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0), D,
                  PB, L1, L2, mt);
     (void)seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
@@ -892,6 +942,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     __syncthreads();
   }
   griddep_wait();   // (a no-op after the first unit's wait)
+  if (kFlags & F_BATCH) return;   // per-instance ends: k_batch_end
   if (last_cta<R>(a.ctrl, (int)gridDim.x, sm)) finish_launch<R, kFlags>(a, sm, units);
 }
 

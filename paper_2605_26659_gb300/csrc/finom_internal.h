@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "finom.h"
 
@@ -54,6 +55,10 @@ struct SolveState {
   void* qw = nullptr;                 // products: W-side potentials
   void* qwm = nullptr;                // products: W-side masses
   void* q2 = nullptr;                 // 2D: log2 sums between the two passes of an application
+  int32_t* ictl = nullptr;            // batch: 4 x B per-instance control (done | iteration | at exit | converged)
+  double* ierr = nullptr;             // batch: per instance, the error of its last check
+  double* itol = nullptr;             // batch: per instance, the loop tolerance
+  void* iuni = nullptr;               // batch: per instance (1/N, 1/M) for the start phi, psi
   double* t2 = nullptr;               // 2D: float64 scratch, one grid
   double* z = nullptr;                // 2D: float64 moments between the two cost passes (2 grids)
   cudaStream_t stream = nullptr;      // internal stream (graph capture needs a non-legacy stream)
@@ -89,6 +94,18 @@ struct finom_plan_s {
   int dim = 1;
   finom_plan_s* ax = nullptr;
   finom_plan_s* ay = nullptr;
+  // batches of independent 1D instances (batch.cu): instance b owns x[offx[b] ..
+  // offx[b+1]), y[offy[b] .. offy[b+1]) and the tiles itile[b] .. itile[b+1]-1
+  // of the packed merged arrays (every instance starts on a tile boundary)
+  int64_t B = 0;                 // instances (0: not a batch plan)
+  std::vector<int64_t> hoffx, hoffy;
+  std::vector<int32_t> hitile;
+  std::vector<double> heps;
+  int64_t* ioffx = nullptr;      // device copies (B + 1)
+  int64_t* ioffy = nullptr;
+  int32_t* itile = nullptr;
+  int32_t* tinst = nullptr;      // per tile: its instance
+  double* ieps = nullptr;        // per instance
   finom::SolveState st;
 };
 
@@ -113,4 +130,10 @@ finom_status solve2d_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
 finom_status solve2d_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
 finom_status cost2d(finom_plan_s* p, const double* u, const double* v, const double* f,
                     const double* g, double* w1, double* err, cudaStream_t s);
+// batches of 1D instances (batch.cu)
+finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* offx, const double* y,
+                              const int64_t* offy, int64_t B, const double* eps, cudaStream_t s);
+void plan_batch_free(finom_plan_s* p);
+finom_status solve_batch(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                         double* f, double* g, finom_result* res, cudaStream_t s);
 }  // namespace finom
