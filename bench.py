@@ -8,6 +8,10 @@ divide and marginal-error check, then the K psi half step): 2^21
 point-iterations.  L2 is flushed (256 MB write) before every timed step, and
 each step is timed with CUDA events on the launching stream.
 
+`--workload batch` times batches of independent 1D instances (4096 instances,
+N = M log-uniform in [256, 65536], clustered meshes, eps log-uniform in
+[1e-3, 1e-2]); one step = one iteration of every instance (four launches).
+
 `--workload 2d` times the 2D path instead (Algorithm 2 with the Appendix A
 stabilisation): 1024 x 1024 grids, tanh-clustered axes, four anisotropic
 Gaussians, eps = 2e-3; one step = one iteration = four line-batch launches,
@@ -50,7 +54,11 @@ def parse():
     ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
     ap.add_argument("--n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["1d", "2d"], default="1d")
+    ap.add_argument("--workload", choices=["1d", "2d", "batch"], default="1d")
+    ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
+    ap.add_argument("--e2e-count", type=int, default=512, help="batch: instances of the end-to-end solve")
+    ap.add_argument("--plain-count", type=int, default=16,
+                    help="batch: instances solved one at a time in FP64 for the plain-form comparison")
     ap.add_argument("--side", type=int, default=1024, help="2D grid side (default 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -364,6 +372,144 @@ def run_finom_2d(args, ws, rank, local):
     api.finom_plan_destroy(plan)
 
 
+def _concat_batch(probs):
+    import numpy as np
+    offx = np.concatenate([[0], np.cumsum([len(q.x) for q in probs])]).astype(np.int64)
+    offy = np.concatenate([[0], np.cumsum([len(q.y) for q in probs])]).astype(np.int64)
+    cat = lambda k: np.concatenate([getattr(q, k) for q in probs])
+    return cat("x"), cat("y"), cat("u"), cat("v"), offx, offy, [q.eps for q in probs]
+
+
+def run_finom_batch(args, ws, rank, local):
+    import torch
+
+    from paper_2605_26659_gb300 import api, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    probs = inputs.config4(args.count)
+    x, y, u, v, offx, offy, eps = _concat_batch(probs)
+    L = len(x) + len(y)
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = api.finom_plan_batch(T(x), offx, T(y), offy, eps, "f32_log", stream=stream)
+    api.finom_solve_batch_begin(plan, T(u), T(v), 0.0, 1 << 30, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        api.finom_solve_batch_step(plan, 1, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s_ev, e_ev in evs:
+        flush.zero_()
+        s_ev.record(stream)
+        api.finom_solve_batch_step(plan, 1, stream=stream)
+        e_ev.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(float(sum(s.elapsed_time(e) for s, e in evs)), ws)
+    step_s = total_ms / 1e3 / args.steps
+    value = ws * L * args.steps / (total_ms / 1e3)
+    bytes_per_step = 2 * 0.5 * (8.25 * L + 32.0 * L)   # two half steps, 20.125 B per merged point
+    peak, peak_kind = peaks()
+    achieved = bytes_per_step / step_s / 1e9
+    api.finom_plan_destroy(plan)
+
+    # end to end: a sub-batch solved to tol 1e-6 from host buffers (FP32, float64
+    # verified) against the plain form: the same instances one at a time in FP64
+    e2e = None
+    if args.e2e_steps > 0:
+        sub = probs[:args.e2e_count]
+        sx, sy, su, sv, soffx, soffy, seps = _concat_batch(sub)
+        hs = [torch.tensor(a, dtype=torch.float64).pin_memory() for a in (sx, sy, su, sv)]
+        hf = torch.empty(len(sx), dtype=torch.float64).pin_memory()
+        hg = torch.empty(len(sy), dtype=torch.float64).pin_memory()
+        times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dx, dy, du, dv = (t.to(dev, non_blocking=True) for t in hs)
+            pb = api.finom_plan_batch(dx, soffx, dy, soffy, seps, "f32_log", stream=stream)
+            f, g, res = api.finom_solve_batch(pb, du, dv, 1e-6, 100000, stream=stream)
+            hf.copy_(f, non_blocking=True)
+            hg.copy_(g, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            api.finom_plan_destroy(pb)
+            if k > 0:
+                times.append(dt)
+        secs = sum(times) / len(times)
+        pts = sum((len(q.x) + len(q.y)) * r["iters"] for q, r in zip(sub, res))
+        nconv = sum(r["converged"] for r in res)
+        # the plain form, a sample of the same instances
+        plain = []
+        for q in sub[:args.plain_count]:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p1 = api.finom_plan(T(q.x), T(q.y), q.eps, "f64", stream=stream)
+            _, _, r1 = api.finom_solve(p1, T(q.u), T(q.v), 1e-6, 100000, stream=stream)
+            torch.cuda.synchronize()
+            plain.append(time.perf_counter() - t0)
+            api.finom_plan_destroy(p1)
+        plain_per_solve = sum(plain) / len(plain)
+        e2e = {"value": ws * pts / secs, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (2 * len(sx) + 2 * len(sy)), "d2h_bytes_per_step": 8 * (len(sx) + len(sy)),
+               "instances": len(sub), "converged": int(nconv), "seconds_per_batch": secs,
+               "solves_per_s": len(sub) / secs,
+               "plain_fp64_one_at_a_time": {"solves_per_s": 1.0 / plain_per_solve, "sample": len(plain),
+                                            "seconds_per_solve": plain_per_solve}}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(probs)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched 1D instances: {len(probs)} problems, N = M log-uniform in "
+                                   f"[256, 65536], clustered meshes, Dirichlet-perturbed mixtures, eps "
+                                   f"log-uniform in [1e-3, 1e-2], FP32 log-domain; 1 iteration of every "
+                                   f"instance per step", "instances": len(probs), "merged_points": L,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "gpu_launches": 4 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "finom::k_apply<float, BHalfY|BHalfX> + k_batch_end",
+                         "algorithmic_bytes_per_step": bytes_per_step},
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_batch(probs, budget_s=12.0):
+    """The CPU oracle on instances of the batch, solved one after another on one
+    core until the time budget is spent."""
+    from oracle import serial_c
+    serial_c.lib()
+    pts, t0 = 0, time.perf_counter()
+    k = 0
+    for q in probs:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        _, _, it, _ = serial_c.sinkhorn(q.x, q.y, q.u, q.v, q.eps, 0.0, 20)
+        pts += (len(q.x) + len(q.y)) * it
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"20 Sinkhorn iterations of each of the first {k} instances, serial C float64 oracle "
+                      f"({dt:.1f} s)"}
+
+
 def run_finom(args, ws, rank, local):
     import numpy as np
     import torch
@@ -452,6 +598,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "2d":
         run_finom_2d(args, ws, rank, local)
+    elif args.workload == "batch":
+        run_finom_batch(args, ws, rank, local)
     else:
         run_finom(args, ws, rank, local)
     if ws > 1:

@@ -157,6 +157,22 @@ finom_status finom_plan_instances(finom_plan_t plan, int64_t* B);
 finom_status finom_solve_batch(finom_plan_t plan, const double* u, const double* v, double tol,
                                int64_t maxit, double* f, double* g, finom_result* res, void* stream);
 
+/*
+ * Stepwise form of finom_solve_batch (the loop without the float64 resume):
+ *   finom_solve_batch_begin  masses, start state, iteration 0 on `stream`
+ *                            (synchronous mass validation only);
+ *   finom_solve_batch_step   `iterations` more iterations of every active
+ *                            instance (four kernels each); asynchronous;
+ *   finom_solve_poll         on a batch plan: *done = every instance retired,
+ *                            *iters = iterations launched;
+ *   finom_solve_batch_end    f, g and res (as finom_solve_batch) for the state
+ *                            of each instance; synchronous.
+ */
+finom_status finom_solve_batch_begin(finom_plan_t plan, const double* u, const double* v, double tol,
+                                     int64_t maxit, void* stream);
+finom_status finom_solve_batch_step(finom_plan_t plan, int64_t iterations, void* stream);
+finom_status finom_solve_batch_end(finom_plan_t plan, double* f, double* g, finom_result* res, void* stream);
+
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 finom_status finom_plan_destroy(finom_plan_t plan);
 

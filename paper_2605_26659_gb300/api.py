@@ -66,6 +66,9 @@ _SIGS = {
     "finom_plan_batch": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_plan_instances": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
     "finom_solve_batch": ([_P, _P, _P, _D, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
+    "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
+    "finom_solve_batch_end": ([_P, _P, _P, _P, _P], ctypes.c_int),
 }
 
 
@@ -209,6 +212,30 @@ def finom_solve_batch(plan: Plan, u, v, tol, maxit, f=None, g=None, stream=None)
                                   _dev(v, plan.M, torch.float64, "v"), float(tol), int(maxit),
                                   _dev(f, plan.N, torch.float64, "f"), _dev(g, plan.M, torch.float64, "g"),
                                   ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
+    return f, g, [r.as_dict() for r in res]
+
+
+def finom_solve_batch_begin(plan: Plan, u, v, tol, maxit, stream=None):
+    import torch
+    _check(_lib.finom_solve_batch_begin(plan.handle, _dev(u, plan.N, torch.float64, "u"),
+                                        _dev(v, plan.M, torch.float64, "v"), float(tol), int(maxit),
+                                        _stream(stream)))
+
+
+def finom_solve_batch_step(plan: Plan, iterations, stream=None):
+    _check(_lib.finom_solve_batch_step(plan.handle, int(iterations), _stream(stream)))
+
+
+def finom_solve_batch_end(plan: Plan, f=None, g=None, stream=None):
+    import torch
+    dev = torch.device("cuda", plan.device)
+    if f is None:
+        f = torch.empty(plan.N, dtype=torch.float64, device=dev)
+    if g is None:
+        g = torch.empty(plan.M, dtype=torch.float64, device=dev)
+    res = (FinomResult * plan.batch)()
+    _check(_lib.finom_solve_batch_end(plan.handle, _dev(f, plan.N), _dev(g, plan.M),
+                                      ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
     return f, g, [r.as_dict() for r in res]
 
 

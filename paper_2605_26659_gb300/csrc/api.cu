@@ -111,7 +111,7 @@ void free_state(finom_plan_s* p) {
   }
   void* bufs[] = {st.mu, st.nu, st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part,
                   st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.t2, st.z,
-                  st.ictl, st.ierr, st.itol, st.iuni};
+                  st.ictl, st.ierr, st.itol, st.iuni, st.alist};
   for (void* b : bufs) cudaFree(b);
   if (st.stream) cudaStreamDestroy(st.stream);
   st = SolveState();
@@ -619,6 +619,37 @@ finom_status finom_plan_instances(finom_plan_t plan, int64_t* B) {
   return FINOM_OK;
 }
 
+finom_status finom_solve_batch_begin(finom_plan_t plan, const double* u, const double* v, double tol,
+                                     int64_t maxit, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->B == 0 || !u || !v || !(tol >= 0.0) || maxit < 0) {
+    set_error("finom_solve_batch_begin: need a batch plan, u, v non-null, tol >= 0, maxit >= 0");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  return solve_batch_begin(plan, u, v, tol, maxit, (cudaStream_t)stream);
+}
+
+finom_status finom_solve_batch_step(finom_plan_t plan, int64_t iterations, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->B == 0 || !plan->st.active || iterations < 0) {
+    set_error("finom_solve_batch_step: no batch solve in progress (finom_solve_batch_begin first)");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  return solve_batch_step(plan, iterations, (cudaStream_t)stream);
+}
+
+finom_status finom_solve_batch_end(finom_plan_t plan, double* f, double* g, finom_result* res, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->B == 0 || !plan->st.active || !f || !g || !res) {
+    set_error("finom_solve_batch_end: no batch solve in progress or null output");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  return solve_batch_end(plan, f, g, res, (cudaStream_t)stream);
+}
+
 finom_status finom_solve_batch(finom_plan_t plan, const double* u, const double* v, double tol,
                                int64_t maxit, double* f, double* g, finom_result* res, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
@@ -741,6 +772,19 @@ finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* strea
 
 finom_status finom_solve_poll(finom_plan_t plan, int32_t* done, int64_t* iters, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->B > 0) {   // batches: done = every instance retired, iters = iterations launched
+    if (!plan->st.ready) {
+      set_error("finom_solve_poll: no solve state");
+      return FINOM_EINVAL;
+    }
+    DeviceGuard dg(plan->device);
+    int32_t h[8];
+    FINOM_CUDA(cudaMemcpyAsync(h, plan->st.ctrl, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    FINOM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (done) *done = h[1];
+    if (iters) *iters = plan->st.launched;
+    return FINOM_OK;
+  }
   if (!plan->st.ready) {
     set_error("finom_solve_poll: no solve state");
     return FINOM_EINVAL;

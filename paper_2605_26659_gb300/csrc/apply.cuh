@@ -100,7 +100,9 @@ struct ApplyArgs {
   const int32_t* itile;   // B + 1
   const int64_t* ioffx;   // B + 1
   const int64_t* ioffy;   // B + 1
-  const int32_t* idone;   // per instance: nonzero once retired (its tiles are skipped)
+  const int32_t* idone;   // per instance: nonzero once retired
+  const int32_t* alist;   // the tiles of the active instances (rebuilt after each half step) ...
+  const int32_t* acount;  // ... and their number; units index this list
   const R* iuni;          // per instance: (1/n_W, 1/n_O) while the start phi, psi apply, else NULL
   const Pot* pO;      // O-side absorbed potentials (the frame), log2 units
   const Mass* mO;     // O-side masses
@@ -762,11 +764,6 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     }
     griddep_launch_dependents();
   }
-  if (kBatch && (kFlags & F_CHECK_DONE) && a.idone[line]) {   // a retired instance
-    cp_async_commit_wait();
-    __syncthreads();
-    return true;
-  }
   if (w_uniform <= R(0) || (kFlags & F_NEXT)) {
     for (int i = tid; i < n_w + 1; i += kThreads) {
       const int64_t gi = wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
@@ -936,13 +933,24 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<R>& sm = *reinterpret_cast<TileSmem<R>*>(smem_raw);
   const int tid = threadIdx.x;
+  if constexpr ((kFlags & F_BATCH) != 0) {
+    // batches: the units are the tiles of the still active instances
+    griddep_wait();
+    if ((kFlags & F_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return;
+    griddep_launch_dependents();
+    const int units = *(volatile const int32_t*)a.acount;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      apply_unit<R, kFlags>(a, sm, a.alist[u], false);
+      __syncthreads();
+    }
+    return;
+  }
   const int units = a.lines * a.C;
   for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
     if (!apply_unit<R, kFlags>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
     __syncthreads();
   }
   griddep_wait();   // (a no-op after the first unit's wait)
-  if (kFlags & F_BATCH) return;   // per-instance ends: k_batch_end
   if (last_cta<R>(a.ctrl, (int)gridDim.x, sm)) finish_launch<R, kFlags>(a, sm, units);
 }
 

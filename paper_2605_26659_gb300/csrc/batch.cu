@@ -227,7 +227,8 @@ struct BatchEndArgs {
   const R* agg;       // 6 per tile: maps of the next application
   R* carry;           // 4 per tile
   const double* part; // per tile: error partials
-  int32_t* ictl;      // 5 x B: done | completed iterations | iterations at exit | converged | parity flip
+  int32_t* ictl;      // 6 x B: done | completed iterations | iterations at exit | converged | parity flip |
+                      //        iteration budget (0: maxit)
   double* ierr;       // per instance: error of its last check
   const double* itol;
   int64_t maxit;
@@ -315,12 +316,40 @@ __global__ void k_batch_end(BatchEndArgs<R> a) {
   if (a.iter_end && lane == 0) {
     int32_t* it = a.ictl + a.B + b;
     *it += 1;
-    if ((int64_t)*it >= a.maxit) {
+    const int32_t cap = a.ictl[5 * a.B + b];
+    if ((int64_t)*it >= a.maxit || (cap > 0 && *it >= cap)) {
       *done = 1;
       a.ictl[2 * a.B + b] = *it;
       retire(a.ctrl);
     }
   }
+}
+
+// The tiles of the active instances, in instance order, and their number
+// (one CTA of 1024 threads: each takes a run of instances, a block scan
+// places the runs).
+__global__ void __launch_bounds__(1024) k_batch_compact(const int32_t* itile, const int32_t* idone, int B,
+                                                        int32_t* alist, int32_t* acount) {
+  __shared__ int32_t sh[1024];
+  const int tid = threadIdx.x;
+  const int per = (B + 1023) / 1024;
+  const int b0 = min(B, tid * per), b1 = min(B, b0 + per);
+  int32_t n = 0;
+  for (int b = b0; b < b1; ++b)
+    if (!idone[b]) n += itile[b + 1] - itile[b];
+  sh[tid] = n;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // inclusive scan (Hillis-Steele)
+    const int32_t v = tid >= o ? sh[tid - o] : 0;
+    __syncthreads();
+    sh[tid] += v;
+    __syncthreads();
+  }
+  int32_t at = sh[tid] - n;
+  for (int b = b0; b < b1; ++b)
+    if (!idone[b])
+      for (int32_t t = itile[b]; t < itile[b + 1]; ++t) alist[at++] = t;
+  if (tid == 1023) *acount = sh[1023];
 }
 
 template <class R>
@@ -345,10 +374,11 @@ finom_status ensure_state_batch(finom_plan_s* p) {
   FINOM_CUDA(cudaMalloc(&st.scal, sizeof(double) * std::max<int64_t>(520, 2 * B)));
   FINOM_CUDA(cudaMalloc(&st.ctrl, sizeof(int32_t) * 8));
   FINOM_CUDA(cudaMalloc(&st.bad, sizeof(int)));
-  FINOM_CUDA(cudaMalloc(&st.ictl, sizeof(int32_t) * 5 * B));
+  FINOM_CUDA(cudaMalloc(&st.ictl, sizeof(int32_t) * 6 * B));
   FINOM_CUDA(cudaMalloc(&st.ierr, sizeof(double) * B));
   FINOM_CUDA(cudaMalloc(&st.itol, sizeof(double) * B));
   FINOM_CUDA(cudaMalloc(&st.iuni, sizeof(R) * 2 * B));
+  FINOM_CUDA(cudaMalloc(&st.alist, sizeof(int32_t) * T));
   FINOM_CUDA(cudaMemset(st.ctrl, 0, sizeof(int32_t) * 8));
   FINOM_CUDA(cudaMemset(st.part, 0, sizeof(double) * T));
   FINOM_CUDA(cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking));
@@ -374,6 +404,8 @@ ApplyArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q, bool start) {
   a.ioffx = p->ioffx;
   a.ioffy = p->ioffy;
   a.idone = st.ictl;
+  a.alist = st.alist;
+  a.acount = st.ctrl + 3;
   a.iuni = start ? (const R*)st.iuni : nullptr;
   a.agg_out = (R*)st.aggs;
   a.carry_in = (const R*)st.carries;
@@ -418,6 +450,7 @@ finom_status launch_end(finom_plan_s* p, int maps, int err, int iter_end, cudaSt
   e.err = err;
   e.iter_end = iter_end;
   k_batch_end<R><<<nblk(p->B, 8), 256, 0, s>>>(e);
+  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)p->B, st.alist, st.ctrl + 3);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "k_batch_end launch");
   return FINOM_OK;
@@ -543,16 +576,15 @@ finom_status evaluate(finom_plan_s* p, double tol, int64_t maxit, double* f, dou
   return rc;
 }
 
+// Start of a batch solve on stream s: masses, start state, iteration 0
+// (maxit = 0: only the first loop-head check).
 template <class R>
-finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
-                              double* f, double* g, finom_result* res, cudaStream_t us) {
+finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                         cudaStream_t s) {
   using Mass = typename Tr<R>::Mass;
-  using Pot = typename Tr<R>::Pot;
-  FINOM_CUDA(cudaStreamSynchronize(us));
   finom_status rc = ensure_state_batch<R>(p);
   if (rc != FINOM_OK) return rc;
   SolveState& st = p->st;
-  cudaStream_t s = st.stream;
   const int64_t B = p->B, N = p->N, M = p->M;
   // masses, per instance
   FINOM_CUDA(cudaMemsetAsync(st.bad, 0, sizeof(int), s));
@@ -575,12 +607,13 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
   }
   FINOM_CUDA(cudaMemcpyAsync(st.iuni, uni.data(), sizeof(R) * 2 * B, cudaMemcpyHostToDevice, s));
   fill_d(st.itol, B, tol, s);
-  FINOM_CUDA(cudaMemsetAsync(st.ictl, 0, sizeof(int32_t) * 5 * B, s));
+  FINOM_CUDA(cudaMemsetAsync(st.ictl, 0, sizeof(int32_t) * 6 * B, s));
   FINOM_CUDA(cudaMemsetAsync(st.ierr, 0, sizeof(double) * B, s));
   int32_t c0[8] = {0, 0, (int32_t)B, 0, 0, 0, 0, 0};
   FINOM_CUDA(cudaMemcpyAsync(st.ctrl, c0, sizeof(c0), cudaMemcpyHostToDevice, s));
   st.tol = tol;
   st.maxit = maxit;
+  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3);
   // iteration 0: maps of the first K^T phi, then its half step with the
   // check at the first loop head, then the phi half step
   ApplyArgs<R> a0 = batch_args<R>(p, false, 0, true);
@@ -588,24 +621,45 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
   rc = launch_apply<R>(a0, false, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 0, s);
   if (rc != FINOM_OK) return rc;
+  st.active = true;
+  st.launched = 0;
   if (maxit == 0) {
     a0.flags = kModeBCheck;
     rc = launch_apply<R>(a0, false, s);
     if (rc == FINOM_OK) rc = launch_end<R>(p, 0, 1, 0, s);
-    if (rc != FINOM_OK) return rc;
-    return evaluate<R>(p, tol, maxit, f, g, res, s, nullptr);
+    return rc;
   }
   a0.flags = kModeBHalfY;
   rc = launch_apply<R>(a0, false, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 1, 0, s);
   if (rc == FINOM_OK) rc = launch_apply<R>(batch_args<R>(p, true, 0, false), false, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);
+  st.launched = 1;
+  return rc;
+}
+
+template <class R>
+finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                              double* f, double* g, finom_result* res, cudaStream_t us) {
+  using Pot = typename Tr<R>::Pot;
+  FINOM_CUDA(cudaStreamSynchronize(us));
+  finom_status rc = ensure_state_batch<R>(p);
   if (rc != FINOM_OK) return rc;
+  SolveState& st = p->st;
+  cudaStream_t s = st.stream;
+  const int64_t B = p->B, N = p->N, M = p->M;
+  rc = begin_batch<R>(p, u, v, tol, maxit, s);
+  if (rc != FINOM_OK) return rc;
+  if (maxit == 0) {
+    rc = evaluate<R>(p, tol, maxit, f, g, res, s, nullptr);
+    st.active = false;
+    return rc;
+  }
   rc = build_body_batch<R>(p);
   if (rc != FINOM_OK) return rc;
-  std::vector<double> err64(B);
-  std::vector<int32_t> ictl(5 * B);
-  std::vector<char> changed(B, 1);
+  std::vector<double> err64(B), prev64(B, INFINITY);
+  std::vector<int32_t> ictl(6 * B);
+  std::vector<char> changed(B, 1), final_(B, 0);
   for (int attempt = 0;; ++attempt) {
     rc = run_loop<R>(p, maxit, s);
     if (rc != FINOM_OK) return rc;
@@ -617,7 +671,7 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     // half step of its stop iteration) with a tighter loop tolerance.  Their
     // states are first moved to parity 0, so one sequence of launches serves
     // them all.
-    FINOM_CUDA(cudaMemcpyAsync(ictl.data(), st.ictl, sizeof(int32_t) * 5 * B, cudaMemcpyDeviceToHost, s));
+    FINOM_CUDA(cudaMemcpyAsync(ictl.data(), st.ictl, sizeof(int32_t) * 6 * B, cudaMemcpyDeviceToHost, s));
     std::vector<double> itol(B), ierr(B);
     FINOM_CUDA(cudaMemcpyAsync(itol.data(), st.itol, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     FINOM_CUDA(cudaMemcpyAsync(ierr.data(), st.ierr, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
@@ -627,7 +681,14 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     for (int64_t b = 0; b < B; ++b) {
       changed[b] = 0;
       const int32_t l = ictl[2 * B + b];
-      if (!ictl[3 * B + b] || l == 0 || err64[b] <= tol) continue;
+      if (!ictl[3 * B + b] || l == 0 || err64[b] <= tol || final_[b]) continue;
+      // a resume that did not lower the float64 error met the float32 floor
+      // of this instance
+      if (err64[b] >= prev64[b]) {
+        final_[b] = 1;
+        continue;
+      }
+      prev64[b] = err64[b];
       const double fr = std::max(0.1, std::min(0.8, 0.8 * tol / err64[b]));
       itol[b] = std::max(ierr[b] * fr, 0.0);
       ictl[b] = 0;              // active again
@@ -637,6 +698,9 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
       // l + 1 then runs at parity 1, i.e. flip = l & 1 from now on
       swap[b] = (l + ictl[4 * B + b]) & 1;
       ictl[4 * B + b] = l & 1;
+      // a resume gets a budget of iterations (a float32 floor above the
+      // tightened tolerance would otherwise run it to maxit)
+      ictl[5 * B + b] = (int32_t)std::min<int64_t>(maxit, (int64_t)l + std::max<int64_t>(1000, l / 2));
       changed[b] = 1;
       ++n_resume;
     }
@@ -644,19 +708,40 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     int32_t* dswap = nullptr;
     FINOM_CUDA(cudaMallocAsync(&dswap, sizeof(int32_t) * B, s));
     FINOM_CUDA(cudaMemcpyAsync(dswap, swap.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s));
-    FINOM_CUDA(cudaMemcpyAsync(st.ictl, ictl.data(), sizeof(int32_t) * 5 * B, cudaMemcpyHostToDevice, s));
+    FINOM_CUDA(cudaMemcpyAsync(st.ictl, ictl.data(), sizeof(int32_t) * 6 * B, cudaMemcpyHostToDevice, s));
     FINOM_CUDA(cudaMemcpyAsync(st.itol, itol.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
     k_bswap<Pot><<<nblk(N, 256), 256, 0, s>>>((Pot*)st.px[0], (const Pot*)st.px[1], p->ioffx, (int)B, dswap, N);
     k_bswap<Pot><<<nblk(M, 256), 256, 0, s>>>((Pot*)st.py[1], (const Pot*)st.py[0], p->ioffy, (int)B, dswap, M);
     cudaFreeAsync(dswap, s);
     int32_t c1[8] = {0, 0, n_resume, 0, 0, 0, 0, 0};
     FINOM_CUDA(cudaMemcpyAsync(st.ctrl, c1, sizeof(c1), cudaMemcpyHostToDevice, s));
+    k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3);
     // the phi half step of the stop iterations, at parity 0
     rc = launch_apply<R>(batch_args<R>(p, true, 0, false), false, s);
     if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);
     if (rc != FINOM_OK) return rc;
   }
   st.tol = tol;
+  st.active = false;
+  if (sizeof(R) == sizeof(double)) return FINOM_OK;
+  // instances whose float32 state cannot reach tol in float64 (a float32
+  // floor above tol: coarse gaps in bits) are finished in float64, warm
+  // started from their float32 potentials
+  for (int64_t b = 0; b < B; ++b) {
+    if (err64[b] <= tol || res[b].iters >= maxit) continue;
+    const int64_t xo = p->hoffx[b], yo = p->hoffy[b];
+    const int64_t nb = p->hoffx[b + 1] - xo, mb = p->hoffy[b + 1] - yo;
+    finom_plan_t p64 = nullptr;
+    rc = finom_plan(p->x + xo, nb, p->y + yo, mb, p->heps[b], FINOM_F64, s, &p64);
+    if (rc != FINOM_OK) return rc;
+    finom_result r64;
+    rc = finom_solve(p64, st.mu64 + xo, st.nu64 + yo, tol, maxit - res[b].iters, f + xo, g + yo, 1, &r64, s);
+    finom_plan_destroy(p64);
+    if (rc != FINOM_OK) return rc;
+    r64.iters += res[b].iters;
+    r64.marginal_err_loop = res[b].marginal_err_loop;
+    res[b] = r64;
+  }
   return FINOM_OK;
 }
 
@@ -758,6 +843,31 @@ finom_status solve_batch(finom_plan_s* p, const double* u, const double* v, doub
                          double* f, double* g, finom_result* res, cudaStream_t s) {
   return p->prec == FINOM_F32_LOG ? solve_batch_impl<float>(p, u, v, tol, maxit, f, g, res, s)
                                   : solve_batch_impl<double>(p, u, v, tol, maxit, f, g, res, s);
+}
+
+finom_status solve_batch_begin(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                               cudaStream_t s) {
+  return p->prec == FINOM_F32_LOG ? begin_batch<float>(p, u, v, tol, maxit, s)
+                                  : begin_batch<double>(p, u, v, tol, maxit, s);
+}
+
+finom_status solve_batch_step(finom_plan_s* p, int64_t iters, cudaStream_t s) {
+  SolveState& st = p->st;
+  for (int64_t k = 0; k < iters; ++k) {
+    const int q = (int)(st.launched & 1);
+    finom_status rc = p->prec == FINOM_F32_LOG ? batch_iteration<float>(p, q, s) : batch_iteration<double>(p, q, s);
+    if (rc != FINOM_OK) return rc;
+    ++st.launched;
+  }
+  return FINOM_OK;
+}
+
+finom_status solve_batch_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s) {
+  SolveState& st = p->st;
+  finom_status rc = p->prec == FINOM_F32_LOG ? evaluate<float>(p, st.tol, st.maxit, f, g, res, s, nullptr)
+                                             : evaluate<double>(p, st.tol, st.maxit, f, g, res, s, nullptr);
+  st.active = false;
+  return rc;
 }
 
 }  // namespace finom

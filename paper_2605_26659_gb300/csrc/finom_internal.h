@@ -59,6 +59,7 @@ struct SolveState {
   double* ierr = nullptr;             // batch: per instance, the error of its last check
   double* itol = nullptr;             // batch: per instance, the loop tolerance
   void* iuni = nullptr;               // batch: per instance (1/N, 1/M) for the start phi, psi
+  int32_t* alist = nullptr;           // batch: the tiles of the active instances
   double* t2 = nullptr;               // 2D: float64 scratch, one grid
   double* z = nullptr;                // 2D: float64 moments between the two cost passes (2 grids)
   cudaStream_t stream = nullptr;      // internal stream (graph capture needs a non-legacy stream)
@@ -136,4 +137,8 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
 void plan_batch_free(finom_plan_s* p);
 finom_status solve_batch(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
                          double* f, double* g, finom_result* res, cudaStream_t s);
+finom_status solve_batch_begin(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                               cudaStream_t s);
+finom_status solve_batch_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
+finom_status solve_batch_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
 }  // namespace finom

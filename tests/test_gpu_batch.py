@@ -168,3 +168,21 @@ def test_batch_invalid_inputs(lib):
     # the plan stays usable
     f, g, res = lib.finom_solve_batch(p, T(u), T(np.ones(4)), 1e-9, 5000)
     assert all(r["iters"] >= 1 for r in res)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_batch_stepwise_equals_blocking(lib, prec):
+    """begin + 12 steps + end gives what the blocking solve with maxit = 13 gives
+    (instances with a single point on a side can reach a zero error, which the
+    blocking float32 solve then re-verifies in float64; they are left out)."""
+    xs, ys, us, vs, eps, offx, offy = _batch(SHAPES[:2] + SHAPES[4:7], 90)
+    p = _plan(lib, xs, ys, eps, offx, offy, prec)
+    u, v = T(np.concatenate(us)), T(np.concatenate(vs))
+    f1, g1, r1 = lib.finom_solve_batch(p, u, v, 0.0, 13)
+    lib.finom_solve_batch_begin(p, u, v, 0.0, 13)
+    lib.finom_solve_batch_step(p, 12)
+    done, launched = lib.finom_solve_poll(p)
+    assert done and launched == 13
+    f2, g2, r2 = lib.finom_solve_batch_end(p)
+    assert np.array_equal(H(f1), H(f2)) and np.array_equal(H(g1), H(g2))
+    assert [r["iters"] for r in r1] == [r["iters"] for r in r2]
