@@ -12,6 +12,14 @@ each step is timed with CUDA events on the launching stream.
 N = M log-uniform in [256, 65536], clustered meshes, eps log-uniform in
 [1e-3, 1e-2]); one step = one iteration of every instance (four launches).
 
+`--workload serve` runs the serving loop: Poisson arrivals at 2000 req/s
+(the first `--requests` of them), 80 % 1D requests (N log-uniform in
+[1e3, 1e6], graded meshes) and 20 % 2D (side log-uniform in [64, 2048],
+tanh-clustered axes), eps in {1e-3, 5e-3, 1e-2}, tol 1e-6, FP32 log-domain
+with float64 verification; value = solves/s from the first arrival to the
+last completion, with p50/p99 latency, beside the plain form (the same kind
+of requests one at a time in FP64).
+
 `--workload 2d` times the 2D path instead (Algorithm 2 with the Appendix A
 stabilisation): 1024 x 1024 grids, tanh-clustered axes, four anisotropic
 Gaussians, eps = 2e-3; one step = one iteration = four line-batch launches,
@@ -54,7 +62,10 @@ def parse():
     ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
     ap.add_argument("--n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["1d", "2d", "batch"], default="1d")
+    ap.add_argument("--workload", choices=["1d", "2d", "batch", "serve"], default="1d")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
+    ap.add_argument("--slots", type=int, default=32, help="serve: concurrent solves (streams)")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
     ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
     ap.add_argument("--e2e-count", type=int, default=512, help="batch: instances of the end-to-end solve")
     ap.add_argument("--plain-count", type=int, default=16,
@@ -491,6 +502,127 @@ def run_finom_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def _submit_request(srv, pr):
+    if hasattr(pr, "x"):
+        return srv.submit_1d(pr.x, pr.y, pr.u, pr.v, pr.eps, pr.tol, pr.maxit)
+    return srv.submit_2d(pr.x1, pr.x2, pr.y1, pr.y2, pr.U, pr.V, pr.eps, pr.tol, pr.maxit)
+
+
+def _request_points(pr):
+    return len(pr.x) + len(pr.y) if hasattr(pr, "x") else 2 * pr.U.size
+
+
+def run_finom_serve(args, ws, rank, local):
+    """Served solves/s and latency of the serving loop on the arrival process."""
+    import numpy as np
+    import torch
+
+    from paper_2605_26659_gb300 import api, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    reqs = inputs.serving_requests()[:args.requests]
+    probs = [inputs.request_problem(r) for r in reqs]
+    n1d = sum(1 for r in reqs if r.kind == "1d")
+    # warm-up: a few small solves (plans, graphs, kernels loaded)
+    srv = api.Server(int(args.budget_gb * 2**30), max_active=args.slots, precision="f32_log")
+    warm = [q for q in probs if _request_points(q) < 200000][:max(args.warmup, 1)]
+    srv.run([_submit_request(srv, q) for q in warm])
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nxt, ids, done, peak_active = 0, {}, {}, 0
+    while len(done) < len(probs):
+        now = time.perf_counter() - t0
+        while nxt < len(probs) and reqs[nxt].t_arrival <= now:
+            ids[_submit_request(srv, probs[nxt])] = nxt
+            nxt += 1
+        pend, act, fin = srv.step()
+        peak_active = max(peak_active, act)
+        if fin:
+            for rid in [r for r in ids if ids[r] not in done]:
+                got = srv.result(rid)
+                if got is not None:
+                    done[ids[rid]] = got[0]
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    srv.close()
+    wall = max_over_ranks(wall, ws)
+    res = [done[k] for k in range(len(probs))]
+    lat = np.array([r["latency_s"] for r in res])
+    que = np.array([r["queue_s"] for r in res])
+    nconv = sum(r["converged"] for r in res)
+    pts = sum(_request_points(q) * r["iters"] for q, r in zip(probs, res))
+    solves_per_s = ws * len(probs) / wall
+    h2d = sum(8 * (2 * (len(q.x) + len(q.y)) if hasattr(q, "x") else 2 * (q.U.size + len(q.x1) + len(q.y1)))
+              for q in probs)
+    launches = sum(r["iters"] * (2 if hasattr(q, "x") else 4) for q, r in zip(probs, res))
+    d2h = sum(8 * _request_points(q) for q in probs)
+    # the plain form: requests of the same process, one at a time, FP64, from host arrays
+    T = lambda a: torch.tensor(np.asarray(a).ravel(order="F"), dtype=torch.float64, device=dev)
+    plain, w1_dev = [], []
+    stream = torch.cuda.current_stream(dev)
+    for k, q in enumerate(probs[:args.plain_count]):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if hasattr(q, "x"):
+            p1 = api.finom_plan(T(q.x), T(q.y), q.eps, "f64", stream=stream)
+            f1, g1, r1 = api.finom_solve(p1, T(q.u), T(q.v), q.tol, q.maxit, stream=stream)
+        else:
+            p1 = api.finom_plan_2d(T(q.x1), T(q.x2), T(q.y1), T(q.y2), q.eps, "f64", stream=stream)
+            f1, g1, r1 = api.finom_solve(p1, T(q.U), T(q.V), q.tol, q.maxit, stream=stream)
+        f1.cpu(), g1.cpu()
+        torch.cuda.synchronize()
+        plain.append(time.perf_counter() - t1)
+        api.finom_plan_destroy(p1)
+        if r1["converged"] and res[k]["converged"]:
+            w1_dev.append(abs(res[k]["w1"] - r1["w1"]) / abs(r1["w1"]))
+    plain_per_solve = sum(plain) / len(plain)
+    peak, peak_kind = peaks()
+    achieved = 20.125 * pts / wall / 1e9   # algorithmic bytes of every half step served
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws,
+            "steps": len(probs), "warmup": len(warm), "ms_per_step": 1e3 * wall / len(probs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving loop: the first {len(probs)} requests of Poisson arrivals at "
+                                   f"2000 req/s, {n1d} 1D (N log-uniform in [1e3, 1e6], graded meshes) and "
+                                   f"{len(probs) - n1d} 2D (side log-uniform in [64, 2048], tanh-clustered "
+                                   f"axes), eps in {{1e-3, 5e-3, 1e-2}}, tol 1e-6, maxit 10000, FP32 "
+                                   f"log-domain with float64 verification; one step = one request",
+                       "slots": args.slots, "budget_gb": args.budget_gb, "peak_active": peak_active,
+                       "l2": "inputs and potentials of the active solves exceed L2",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max()), "queue_p50": float(np.percentile(que, 50)),
+                          "queue_p99": float(np.percentile(que, 99))},
+            "converged": int(nconv), "point_iters_per_s": pts / wall,
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "every k_apply launch of the served solves, over the wall time",
+                         "algorithmic_bytes": 20.125 * pts},
+            "clocks": clocks,
+            "e2e": {"value": solves_per_s, "unit": "solves/s", "h2d_bytes_per_step": h2d / len(probs),
+                    "d2h_bytes_per_step": d2h / len(probs)},
+            "plain_fp64_one_at_a_time": {"solves_per_s": 1.0 / plain_per_solve, "sample": len(plain),
+                                         "seconds_per_solve": plain_per_solve,
+                                         "w1_max_relerr_served_vs_plain": max(w1_dev) if w1_dev else None},
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_batch(probs, budget_s=12.0):
     """The CPU oracle on instances of the batch, solved one after another on one
     core until the time budget is spent."""
@@ -600,6 +732,8 @@ def main():
         run_finom_2d(args, ws, rank, local)
     elif args.workload == "batch":
         run_finom_batch(args, ws, rank, local)
+    elif args.workload == "serve":
+        run_finom_serve(args, ws, rank, local)
     else:
         run_finom(args, ws, rank, local)
     if ws > 1:

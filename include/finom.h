@@ -41,7 +41,8 @@ typedef enum {
   FINOM_ENOMEM = 2,           /* a device allocation failed */
   FINOM_ECUDA = 3,            /* a CUDA runtime call failed (message in finom_last_error) */
   FINOM_EDEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up */
-  FINOM_ENOTSUP = 5           /* the plan's precision or kind does not support the call */
+  FINOM_ENOTSUP = 5,          /* the plan's precision or kind does not support the call */
+  FINOM_EPENDING = 6          /* finom_server_result: the request has not finished (or is unknown) */
 } finom_status;
 
 typedef enum {
@@ -172,6 +173,88 @@ finom_status finom_solve_batch_begin(finom_plan_t plan, const double* u, const d
                                      int64_t maxit, void* stream);
 finom_status finom_solve_batch_step(finom_plan_t plan, int64_t iterations, void* stream);
 finom_status finom_solve_batch_end(finom_plan_t plan, double* f, double* g, finom_result* res, void* stream);
+
+/*
+ * Serving loop: continuous batching of 1D and 2D solves (Algorithm 1 and
+ * Algorithm 2) of mixed sizes in one process on one GPU.  The paper has no
+ * counterpart; each solve's arithmetic is that of finom_solve, so a request's
+ * result does not depend on what else is being served.
+ *
+ * A server owns max_active CUDA streams (slots).  finom_server_submit_* copy a
+ * request's HOST arrays and queue it.  finom_server_step runs one scheduling
+ * round, without waiting for the GPU:
+ *   - admission, first come first served: the queue head is admitted while a
+ *     slot is free and the estimated device footprint of the active solves
+ *     plus its own stays within mem_budget_bytes (a request larger than the
+ *     budget is admitted alone); admission copies its inputs to the device,
+ *     builds its plan and launches iteration 0 on its slot's stream;
+ *   - progress: every active solve whose launches have completed and whose
+ *     loop is still running gets more iterations (1, 2, 4, ... up to 64 per
+ *     round; CUDA graphs of 16 iterations); the potentials stay on the device;
+ *   - retirement: a solve whose loop stopped (check <= tol, or maxit) is
+ *     finished: float64 W1 and marginal error; with FINOM_F32_LOG, a float64
+ *     error above tol (before maxit) continues the loop in float64 from the
+ *     float32 potentials, on a float64 plan of the same meshes, in later
+ *     rounds; then f, g are copied to the host and the slot and its memory
+ *     are freed.
+ * Solves on different slots overlap on the GPU.  All calls on one server
+ * must come from one host thread at a time; the server uses the device that
+ * was current at finom_server_create.
+ */
+typedef struct finom_server_s* finom_server_t;
+
+typedef struct {
+  int64_t id;             /* request id returned by finom_server_submit_* */
+  int32_t kind;           /* 1: 1D, 2: 2D */
+  int32_t status;         /* finom_status of the solve (plan, loop, cost) */
+  finom_result result;    /* as finom_solve; iters counts every iteration run */
+  double latency_s;       /* submit -> result ready (host wall clock) */
+  double queue_s;         /* submit -> admission */
+} finom_server_done;
+
+/*
+ * finom_server_create -- mem_budget_bytes > 0 (device bytes for the active
+ * solves), 1 <= max_active <= 256 slots, prec the precision of every solve.
+ */
+finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, finom_precision prec,
+                                 finom_server_t* out);
+
+/*
+ * finom_server_submit_1d -- queue a 1D solve (arguments as finom_plan and
+ * finom_solve; x, y, u, v are HOST arrays of N, M, N, M doubles, copied before
+ * the call returns).  *id receives the request id.  Sorting and mass checks
+ * happen at admission; a bad request finishes with that status.
+ */
+finom_status finom_server_submit_1d(finom_server_t srv, const double* x, int64_t N, const double* y, int64_t M,
+                                    const double* u, const double* v, double eps, double tol, int64_t maxit,
+                                    int64_t* id);
+
+/*
+ * finom_server_submit_2d -- queue a 2D solve (arguments as finom_plan_2d and
+ * finom_solve on it; x1, x2: N, y1, y2: M, U, V: N * M column-major doubles,
+ * HOST arrays, copied before the call returns).
+ */
+finom_status finom_server_submit_2d(finom_server_t srv, const double* x1, const double* x2, int64_t N,
+                                    const double* y1, const double* y2, int64_t M, const double* U,
+                                    const double* V, double eps, double tol, int64_t maxit, int64_t* id);
+
+/*
+ * finom_server_step -- one scheduling round (see above).  Returns the number
+ * of queued, active and finished-but-not-collected requests (any pointer may
+ * be NULL).  Errors of a request are reported through its result, not here.
+ */
+finom_status finom_server_step(finom_server_t srv, int32_t* n_pending, int32_t* n_active, int32_t* n_finished);
+
+/*
+ * finom_server_result -- collect a finished request: *out, and its potentials
+ * into f (N doubles for 1D, N * M for 2D, HOST, may be NULL) and g (M, or
+ * N * M).  The request is forgotten afterwards.  FINOM_EPENDING if it has
+ * not finished (or the id is unknown).
+ */
+finom_status finom_server_result(finom_server_t srv, int64_t id, finom_server_done* out, double* f, double* g);
+
+/* Release the server: waits for its active solves and drops every request. */
+finom_status finom_server_destroy(finom_server_t srv);
 
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 finom_status finom_plan_destroy(finom_plan_t plan);

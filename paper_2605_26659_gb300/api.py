@@ -14,7 +14,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfinom.so")
 
-FINOM_OK, FINOM_EINVAL, FINOM_ENOMEM, FINOM_ECUDA, FINOM_EDEVICE_TIMEOUT, FINOM_ENOTSUP = range(6)
+FINOM_OK, FINOM_EINVAL, FINOM_ENOMEM, FINOM_ECUDA, FINOM_EDEVICE_TIMEOUT, FINOM_ENOTSUP, FINOM_EPENDING = range(7)
 F64, F32_LOG = 0, 1
 _PREC = {"f64": F64, "fp64": F64, "float64": F64, F64: F64,
          "f32_log": F32_LOG, "fp32_log": F32_LOG, "f32": F32_LOG, F32_LOG: F32_LOG}
@@ -33,6 +33,11 @@ class FinomResult(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FinomServerDone(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("kind", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("result", FinomResult), ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double)]
 
 
 _lib = None
@@ -69,6 +74,13 @@ _SIGS = {
     "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
     "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
     "finom_solve_batch_end": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_server_create": ([_I64, _I32, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "finom_server_submit_1d": ([_P, _P, _I64, _P, _I64, _P, _P, _D, _D, _I64, ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_server_submit_2d": ([_P, _P, _P, _I64, _P, _P, _I64, _P, _P, _D, _D, _I64, ctypes.POINTER(_I64)],
+                               ctypes.c_int),
+    "finom_server_step": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "finom_server_result": ([_P, _I64, ctypes.POINTER(FinomServerDone), _P, _P], ctypes.c_int),
+    "finom_server_destroy": ([_P], ctypes.c_int),
 }
 
 
@@ -360,3 +372,102 @@ def finom_kv_log_noalloc(plan: Plan, a, b, out=None, stream=None):
     _check(_lib.finom_kv_log_noalloc(plan.handle, _dev(a, plan.N, torch.float64, "a"),
                                      _dev(b, plan.M, torch.float64, "b"), _dev(out, plan.N), _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# serving loop (host arrays in, host arrays out)
+
+def _host(a, n, name):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"{name} must have {n} entries, got {a.size}")
+    return a
+
+
+class Server:
+    """finom_server_*: continuous batching of 1D and 2D solves on one GPU."""
+
+    def __init__(self, mem_budget_bytes, max_active=16, precision="f32_log"):
+        load()
+        h = ctypes.c_void_p()
+        _check(_lib.finom_server_create(int(mem_budget_bytes), int(max_active), _PREC[precision],
+                                        ctypes.byref(h)))
+        self.handle = h
+        self._shape = {}
+
+    def submit_1d(self, x, y, u, v, eps, tol, maxit):
+        import numpy as np
+        N, M = np.size(x), np.size(y)
+        x, y, u, v = _host(x, N, "x"), _host(y, M, "y"), _host(u, N, "u"), _host(v, M, "v")
+        rid = ctypes.c_int64()
+        _check(_lib.finom_server_submit_1d(self.handle, x.ctypes.data, N, y.ctypes.data, M, u.ctypes.data,
+                                           v.ctypes.data, float(eps), float(tol), int(maxit), ctypes.byref(rid)))
+        self._shape[rid.value] = (N, M)
+        return rid.value
+
+    def submit_2d(self, x1, x2, y1, y2, U, V, eps, tol, maxit):
+        """U, V: (N, M) arrays, point (k, i) at [k, i] (passed column-major)."""
+        import numpy as np
+        N, M = np.size(x1), np.size(y1)
+        x1, x2, y1, y2 = _host(x1, N, "x1"), _host(x2, N, "x2"), _host(y1, M, "y1"), _host(y2, M, "y2")
+        U = _host(np.asarray(U).ravel(order="F"), N * M, "U")
+        V = _host(np.asarray(V).ravel(order="F"), N * M, "V")
+        rid = ctypes.c_int64()
+        _check(_lib.finom_server_submit_2d(self.handle, x1.ctypes.data, x2.ctypes.data, N, y1.ctypes.data,
+                                           y2.ctypes.data, M, U.ctypes.data, V.ctypes.data, float(eps),
+                                           float(tol), int(maxit), ctypes.byref(rid)))
+        self._shape[rid.value] = (N * M, N * M, (N, M))
+        return rid.value
+
+    def step(self):
+        """One scheduling round; returns (pending, active, finished)."""
+        a, b, c = _I32(), _I32(), _I32()
+        _check(_lib.finom_server_step(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def result(self, rid):
+        """(done dict, f, g) of a finished request, or None while it is pending.
+        2D potentials come back as (N, M) arrays."""
+        import numpy as np
+        shp = self._shape.get(rid)
+        if shp is None:
+            raise KeyError(rid)
+        f = np.empty(shp[0])
+        g = np.empty(shp[1])
+        d = FinomServerDone()
+        rc = _lib.finom_server_result(self.handle, int(rid), ctypes.byref(d), f.ctypes.data, g.ctypes.data)
+        if rc == FINOM_EPENDING:
+            return None
+        _check(rc)
+        del self._shape[rid]
+        out = {"id": d.id, "kind": d.kind, "status": d.status, "latency_s": d.latency_s, "queue_s": d.queue_s}
+        out.update(d.result.as_dict())
+        if len(shp) == 3:
+            f = f.reshape(shp[2], order="F")
+            g = g.reshape(shp[2], order="F")
+        return out, f, g
+
+    def run(self, ids):
+        """Step until every request in ids has finished; returns {id: (done, f, g)}."""
+        out = {}
+        ids = list(ids)
+        while len(out) < len(ids):
+            self.step()
+            for r in ids:
+                if r not in out:
+                    got = self.result(r)
+                    if got is not None:
+                        out[r] = got
+        return out
+
+    def close(self):
+        if self.handle:
+            _lib.finom_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -105,6 +105,7 @@ finom_status ensure_state(finom_plan_s* p) {
 void free_state(finom_plan_s* p) {
   SolveState& st = p->st;
   if (st.body) cudaGraphExecDestroy(st.body);
+  if (st.chunk) cudaGraphExecDestroy(st.chunk);
   for (int q = 0; q < 2; ++q) {
     cudaFree(st.px[q]);
     cudaFree(st.py[q]);
@@ -194,24 +195,28 @@ finom_status launch_iteration(finom_plan_s* p, int q, cudaStream_t s) {
   return launch_apply<R>(half_args<R>(p, true, q), false, s);
 }
 
+// graph of 2 * pairs iterations starting at an odd iteration (q = 1, 0, 1, ...)
 template <class R>
-finom_status build_body(finom_plan_s* p) {
+finom_status build_body(finom_plan_s* p, int pairs, cudaGraphExec_t* out) {
   SolveState& st = p->st;
-  if (st.body) {
-    cudaGraphExecDestroy(st.body);
-    st.body = nullptr;
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
   }
   cudaGraph_t g = nullptr;
   FINOM_CUDA(cudaStreamBeginCapture(st.stream, cudaStreamCaptureModeThreadLocal));
-  finom_status rc = launch_iteration<R>(p, 1, st.stream);
-  if (rc == FINOM_OK) rc = launch_iteration<R>(p, 0, st.stream);
+  finom_status rc = FINOM_OK;
+  for (int k = 0; k < pairs && rc == FINOM_OK; ++k) {
+    rc = launch_iteration<R>(p, 1, st.stream);
+    if (rc == FINOM_OK) rc = launch_iteration<R>(p, 0, st.stream);
+  }
   cudaError_t e = cudaStreamEndCapture(st.stream, &g);
   if (rc != FINOM_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&st.body, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   return FINOM_OK;
@@ -265,13 +270,28 @@ finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, doub
   return FINOM_OK;
 }
 
+// Iterations of a stepwise solve: single launches up to an odd iteration,
+// then graphs of kChunkIters iterations, then single launches for the rest.
 template <class R>
 finom_status solve_step(finom_plan_s* p, int64_t iters, cudaStream_t s) {
   SolveState& st = p->st;
-  for (int64_t k = 0; k < iters; ++k) {
+  for (int64_t k = 0; k < iters;) {
+    if ((st.launched & 1) && iters - k >= kChunkIters) {
+      if (!st.chunk || st.chunk_tol != st.tol || st.chunk_maxit != st.maxit) {
+        finom_status rc = build_body<R>(p, kChunkIters / 2, &st.chunk);
+        if (rc != FINOM_OK) return rc;
+        st.chunk_tol = st.tol;
+        st.chunk_maxit = st.maxit;
+      }
+      FINOM_CUDA(cudaGraphLaunch(st.chunk, s));
+      st.launched += kChunkIters;
+      k += kChunkIters;
+      continue;
+    }
     finom_status rc = launch_iteration<R>(p, (int)(st.launched & 1), s);
     if (rc != FINOM_OK) return rc;
     ++st.launched;
+    ++k;
   }
   return FINOM_OK;
 }
@@ -358,7 +378,7 @@ finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, d
     // still above tol, tighten the loop tolerance and resume from the exact
     // state at the stop (the skipped phi half step of iteration l).
     for (int attempt = 0;; ++attempt) {
-      rc = build_body<R>(p);
+      rc = build_body<R>(p, 1, &st.body);
       if (rc != FINOM_OK) return rc;
       int64_t bodies = 1;
       for (;;) {

@@ -222,24 +222,28 @@ finom_status iteration2d(finom_plan_s* p, int q, cudaStream_t s) {
   return half_phi<R>(p, q, s);
 }
 
+// graph of 2 * pairs iterations starting at an odd iteration (q = 1, 0, 1, ...)
 template <class R>
-finom_status build_body2d(finom_plan_s* p) {
+finom_status build_body2d(finom_plan_s* p, int pairs, cudaGraphExec_t* out) {
   SolveState& st = p->st;
-  if (st.body) {
-    cudaGraphExecDestroy(st.body);
-    st.body = nullptr;
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
   }
   cudaGraph_t g = nullptr;
   FINOM_CUDA(cudaStreamBeginCapture(st.stream, cudaStreamCaptureModeThreadLocal));
-  finom_status rc = iteration2d<R>(p, 1, st.stream);
-  if (rc == FINOM_OK) rc = iteration2d<R>(p, 0, st.stream);
+  finom_status rc = FINOM_OK;
+  for (int k = 0; k < pairs && rc == FINOM_OK; ++k) {
+    rc = iteration2d<R>(p, 1, st.stream);
+    if (rc == FINOM_OK) rc = iteration2d<R>(p, 0, st.stream);
+  }
   cudaError_t e = cudaStreamEndCapture(st.stream, &g);
   if (rc != FINOM_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&st.body, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   return FINOM_OK;
@@ -300,10 +304,23 @@ finom_status begin2d(finom_plan_s* p, const double* u, const double* v, double t
 template <class R>
 finom_status step2d(finom_plan_s* p, int64_t iters, cudaStream_t s) {
   SolveState& st = p->st;
-  for (int64_t k = 0; k < iters; ++k) {
+  for (int64_t k = 0; k < iters;) {
+    if ((st.launched & 1) && iters - k >= kChunkIters) {   // graphs of kChunkIters iterations
+      if (!st.chunk || st.chunk_tol != st.tol || st.chunk_maxit != st.maxit) {
+        finom_status rc = build_body2d<R>(p, kChunkIters / 2, &st.chunk);
+        if (rc != FINOM_OK) return rc;
+        st.chunk_tol = st.tol;
+        st.chunk_maxit = st.maxit;
+      }
+      FINOM_CUDA(cudaGraphLaunch(st.chunk, s));
+      st.launched += kChunkIters;
+      k += kChunkIters;
+      continue;
+    }
     finom_status rc = iteration2d<R>(p, (int)(st.launched & 1), s);
     if (rc != FINOM_OK) return rc;
     ++st.launched;
+    ++k;
   }
   return FINOM_OK;
 }
@@ -400,7 +417,7 @@ finom_status blocking2d(finom_plan_s* p, const double* u, const double* v, doubl
     // as in 1D: loop until the device-side check stops it; verify a float32
     // stop in float64 and resume with a tighter loop tolerance if needed
     for (int attempt = 0;; ++attempt) {
-      rc = build_body2d<R>(p);
+      rc = build_body2d<R>(p, 1, &st.body);
       if (rc != FINOM_OK) return rc;
       int64_t bodies = 1;
       for (;;) {

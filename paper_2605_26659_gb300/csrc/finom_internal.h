@@ -34,6 +34,9 @@ finom_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Device state of the Sinkhorn loop of one plan (allocated on first use).
+// iterations per graph launch of the stepwise solves (an even number)
+constexpr int kChunkIters = 16;
+
 struct SolveState {
   bool ready = false;
   void* px[2] = {nullptr, nullptr};   // absorbed x-side potential (log2 units), ping-pong
@@ -64,6 +67,9 @@ struct SolveState {
   double* z = nullptr;                // 2D: float64 moments between the two cost passes (2 grids)
   cudaStream_t stream = nullptr;      // internal stream (graph capture needs a non-legacy stream)
   cudaGraphExec_t body = nullptr;     // two Sinkhorn iterations
+  cudaGraphExec_t chunk = nullptr;    // kChunkIters iterations (stepwise solves)
+  double chunk_tol = -1.0;            // loop tolerance and iteration limit the
+  int64_t chunk_maxit = -1;           //   chunk was captured with
   // the solve in progress
   bool active = false;
   bool warm = false;

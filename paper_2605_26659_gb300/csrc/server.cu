@@ -1,0 +1,368 @@
+// Serving loop: continuous batching of 1D and 2D solves of mixed sizes.
+//
+// Requests are queued on the host; a scheduling round (finom_server_step)
+// admits queued requests first come first served while their estimated
+// device footprint fits the memory budget and a stream slot is free, builds
+// their plans and starts their solves on their own stream; for every active
+// solve whose previous launches have completed it either launches more
+// iterations (doubling, up to 64 per round) or, once the loop has stopped,
+// finishes it (float64 W1 and marginal error, potentials copied back; with
+// float32 scans, a float64 error above tol first continues in float64) and
+// frees its memory and slot.  Potentials stay resident on the device for
+// the whole solve, and the kernels of all active solves run concurrently on
+// the GPU from their streams; each solve's arithmetic is that of finom_solve,
+// whatever else is running.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "finom_internal.h"
+
+struct finom_server_s {
+  struct Req {
+    int64_t id = 0;
+    int kind = 1;                     // 1: 1D, 2: 2D
+    int64_t N = 0, M = 0;             // 1D: mesh sizes; 2D: grid sides
+    double eps = 0.0, tol = 0.0;
+    int64_t maxit = 0;
+    std::vector<double> in[6];        // 1D: x, y, u, v; 2D: x1, x2, y1, y2, U, V
+    int64_t footprint = 0;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    // while active
+    int slot = -1;
+    finom_plan_t plan = nullptr;
+    finom_plan_t plan64 = nullptr;    // after a switch to float64: the float32 plan
+    int64_t iters_before = 0;         // iterations before that switch
+    double* dev = nullptr;            // device inputs, then f and g
+    cudaEvent_t ev = nullptr;
+    int64_t step = 1;
+    // when finished
+    int32_t status = FINOM_OK;
+    finom_result res{};
+    std::vector<double> f, g;
+  };
+  int64_t budget = 0, used = 0;
+  int max_active = 8;
+  finom_precision prec = FINOM_F32_LOG;
+  int device = 0;
+  int64_t next_id = 1;
+  std::deque<Req*> pending;
+  std::vector<Req*> active;
+  std::map<int64_t, Req*> finished;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> free_slots;
+};
+
+namespace {
+
+using Req = finom_server_s::Req;
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// device bytes of a solve (plan, state, scratch), an estimate for admission
+int64_t footprint(int kind, int64_t N, int64_t M) {
+  if (kind == 1) return (N + M) * 240 + (1 << 20);
+  return N * M * 260 + (N + M) * 240 + (1 << 20);
+}
+
+int64_t npoints(const Req* r, int side) {   // points of the first (side 0) or second measure
+  (void)side;
+  return r->kind == 1 ? (side == 0 ? r->N : r->M) : r->N * r->M;
+}
+
+void release(finom_server_s* s, Req* r) {
+  if (r->plan) finom_plan_destroy(r->plan);
+  if (r->plan64) finom_plan_destroy(r->plan64);
+  if (r->dev) cudaFreeAsync(r->dev, s->streams[r->slot]);
+  if (r->ev) cudaEventDestroy(r->ev);
+  r->plan = nullptr;
+  r->plan64 = nullptr;
+  r->dev = nullptr;
+  r->ev = nullptr;
+  if (r->slot >= 0) s->free_slots.push_back(r->slot);
+  r->slot = -1;
+  s->used -= r->footprint;
+  for (auto& v : r->in) std::vector<double>().swap(v);
+}
+
+void fail(finom_server_s* s, Req* r, finom_status rc) {
+  r->status = rc;
+  r->res.status = rc;
+  r->t_done = now_s();
+  release(s, r);
+  s->finished[r->id] = r;
+}
+
+// admit: device copies of the inputs, the plan, the start of the solve
+finom_status admit(finom_server_s* s, Req* r) {
+  r->slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  s->used += r->footprint;
+  r->t_admit = now_s();
+  cudaStream_t st = s->streams[r->slot];
+  const int64_t n1 = npoints(r, 0), n2 = npoints(r, 1);
+  int64_t total = 0;
+  for (auto& v : r->in) total += (int64_t)v.size();
+  total += n1 + n2;   // f, g
+  FINOM_CUDA(cudaMallocAsync(&r->dev, sizeof(double) * total, st));
+  FINOM_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+  double* d[6];
+  int64_t off = 0;
+  for (int k = 0; k < 6; ++k) {
+    d[k] = r->dev + off;
+    if (!r->in[k].empty())
+      FINOM_CUDA(cudaMemcpyAsync(d[k], r->in[k].data(), sizeof(double) * r->in[k].size(),
+                                 cudaMemcpyHostToDevice, st));
+    off += (int64_t)r->in[k].size();
+  }
+  finom_status rc;
+  if (r->kind == 1) {
+    rc = finom_plan(d[0], r->N, d[1], r->M, r->eps, s->prec, st, &r->plan);
+    if (rc == FINOM_OK) rc = finom_solve_begin(r->plan, d[2], d[3], r->tol, r->maxit, nullptr, nullptr, st);
+  } else {
+    rc = finom_plan_2d(d[0], d[1], r->N, d[2], d[3], r->M, r->eps, s->prec, st, &r->plan);
+    if (rc == FINOM_OK) rc = finom_solve_begin(r->plan, d[4], d[5], r->tol, r->maxit, nullptr, nullptr, st);
+  }
+  if (rc != FINOM_OK) return rc;
+  FINOM_CUDA(cudaEventRecord(r->ev, st));
+  return FINOM_OK;
+}
+
+// A solve whose loop has stopped: its float64 result; with float32 scans, a
+// float64 marginal error above tol (the float32 check passed, or the float32
+// precision floor is above tol) continues in float64 from the float32
+// potentials on a float64 plan of the same meshes (*more = true); otherwise
+// the potentials go to the host and the request is released.
+finom_status finish(finom_server_s* s, Req* r, bool* more) {
+  *more = false;
+  cudaStream_t st = s->streams[r->slot];
+  const int64_t n1 = npoints(r, 0), n2 = npoints(r, 1);
+  int64_t off = 0;
+  for (auto& v : r->in) off += (int64_t)v.size();
+  double* f = r->dev + off;
+  double* g = f + n1;
+  const double* u = r->dev + (r->kind == 1 ? r->N + r->M : 2 * (r->N + r->M));
+  const double* v = u + n1;
+  finom_status rc = finom_solve_end(r->plan, f, g, &r->res, st);
+  if (rc != FINOM_OK) return rc;
+  r->res.iters += r->iters_before;
+  if (!r->res.converged && r->res.iters < r->maxit && !r->plan64 && s->prec != FINOM_F64) {
+    const double* d = r->dev;
+    if (r->kind == 1)
+      rc = finom_plan(d, r->N, d + r->N, r->M, r->eps, FINOM_F64, st, &r->plan64);
+    else
+      rc = finom_plan_2d(d, d + r->N, r->N, d + 2 * r->N, d + 2 * r->N + r->M, r->M, r->eps, FINOM_F64, st,
+                         &r->plan64);
+    if (rc != FINOM_OK) return rc;
+    rc = finom_solve_begin(r->plan64, u, v, r->tol, r->maxit - r->res.iters, f, g, st);
+    if (rc != FINOM_OK) return rc;
+    std::swap(r->plan, r->plan64);   // the float32 plan is released with the request
+    r->iters_before = r->res.iters;
+    r->step = 1;
+    FINOM_CUDA(cudaEventRecord(r->ev, st));
+    *more = true;
+    return FINOM_OK;
+  }
+  r->f.resize(n1);
+  r->g.resize(n2);
+  FINOM_CUDA(cudaMemcpyAsync(r->f.data(), f, sizeof(double) * n1, cudaMemcpyDeviceToHost, st));
+  FINOM_CUDA(cudaMemcpyAsync(r->g.data(), g, sizeof(double) * n2, cudaMemcpyDeviceToHost, st));
+  FINOM_CUDA(cudaStreamSynchronize(st));
+  r->t_done = now_s();
+  release(s, r);
+  return FINOM_OK;
+}
+
+finom_status submit(finom_server_s* s, Req* r, int64_t* id) {
+  r->id = s->next_id++;
+  r->footprint = footprint(r->kind, r->N, r->M);
+  r->t_submit = now_s();
+  s->pending.push_back(r);
+  if (id) *id = r->id;
+  return FINOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, finom_precision prec,
+                                 finom_server_t* out) {
+  if (!out || mem_budget_bytes <= 0 || max_active < 1 || max_active > 256 ||
+      (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
+    finom::set_error("finom_server_create: need out, a positive budget, 1 <= max_active <= 256, known precision");
+    return FINOM_EINVAL;
+  }
+  finom_server_s* s = new (std::nothrow) finom_server_s();
+  if (!s) return FINOM_ENOMEM;
+  s->budget = mem_budget_bytes;
+  s->max_active = max_active;
+  s->prec = prec;
+  cudaGetDevice(&s->device);
+  s->streams.resize(max_active);
+  for (int k = 0; k < max_active; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaStreamDestroy(s->streams[j]);
+      delete s;
+      return finom::cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    s->free_slots.push_back(max_active - 1 - k);
+  }
+  *out = s;
+  return FINOM_OK;
+}
+
+finom_status finom_server_submit_1d(finom_server_t s, const double* x, int64_t N, const double* y, int64_t M,
+                                    const double* u, const double* v, double eps, double tol, int64_t maxit,
+                                    int64_t* id) {
+  if (!s || !x || !y || !u || !v || N < 1 || M < 1 || !(eps > 0.0) || !(tol >= 0.0) || maxit < 0) {
+    finom::set_error("finom_server_submit_1d: bad argument");
+    return FINOM_EINVAL;
+  }
+  Req* r = new (std::nothrow) Req();
+  if (!r) return FINOM_ENOMEM;
+  r->kind = 1;
+  r->N = N;
+  r->M = M;
+  r->eps = eps;
+  r->tol = tol;
+  r->maxit = maxit;
+  r->in[0].assign(x, x + N);
+  r->in[1].assign(y, y + M);
+  r->in[2].assign(u, u + N);
+  r->in[3].assign(v, v + M);
+  return submit(s, r, id);
+}
+
+finom_status finom_server_submit_2d(finom_server_t s, const double* x1, const double* x2, int64_t N,
+                                    const double* y1, const double* y2, int64_t M, const double* U,
+                                    const double* V, double eps, double tol, int64_t maxit, int64_t* id) {
+  if (!s || !x1 || !x2 || !y1 || !y2 || !U || !V || N < 1 || M < 1 || !(eps > 0.0) || !(tol >= 0.0) ||
+      maxit < 0) {
+    finom::set_error("finom_server_submit_2d: bad argument");
+    return FINOM_EINVAL;
+  }
+  Req* r = new (std::nothrow) Req();
+  if (!r) return FINOM_ENOMEM;
+  r->kind = 2;
+  r->N = N;
+  r->M = M;
+  r->eps = eps;
+  r->tol = tol;
+  r->maxit = maxit;
+  r->in[0].assign(x1, x1 + N);
+  r->in[1].assign(x2, x2 + N);
+  r->in[2].assign(y1, y1 + M);
+  r->in[3].assign(y2, y2 + M);
+  r->in[4].assign(U, U + N * M);
+  r->in[5].assign(V, V + N * M);
+  return submit(s, r, id);
+}
+
+finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_active, int32_t* n_finished) {
+  if (!s) {
+    finom::set_error("finom_server_step: null server");
+    return FINOM_EINVAL;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
+  // admissions, first come first served: an empty server always admits
+  while (!s->pending.empty() && !s->free_slots.empty()) {
+    Req* r = s->pending.front();
+    if (!s->active.empty() && s->used + r->footprint > s->budget) break;
+    s->pending.pop_front();
+    finom_status rc = admit(s, r);
+    if (rc != FINOM_OK) fail(s, r, rc);
+    else s->active.push_back(r);
+  }
+  // progress of the active solves whose launches have completed
+  std::vector<Req*> still;
+  for (Req* r : s->active) {
+    if (cudaEventQuery(r->ev) == cudaErrorNotReady) {
+      still.push_back(r);
+      continue;
+    }
+    cudaStream_t st = s->streams[r->slot];
+    int32_t done = 0;
+    int64_t its = 0;
+    finom_status rc = finom_solve_poll(r->plan, &done, &its, st);
+    if (rc == FINOM_OK && !done) {
+      rc = finom_solve_step(r->plan, r->step, st);
+      r->step = std::min<int64_t>(2 * r->step, 64);
+      if (rc == FINOM_OK && cudaEventRecord(r->ev, st) != cudaSuccess) rc = FINOM_ECUDA;
+      if (rc == FINOM_OK) {
+        still.push_back(r);
+        continue;
+      }
+    }
+    bool more = false;
+    if (rc == FINOM_OK) rc = finish(s, r, &more);
+    if (rc != FINOM_OK) {
+      fail(s, r, rc);
+      continue;
+    }
+    if (more) {
+      still.push_back(r);
+      continue;
+    }
+    s->finished[r->id] = r;
+  }
+  s->active.swap(still);
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  if (n_pending) *n_pending = (int32_t)s->pending.size();
+  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_finished) *n_finished = (int32_t)s->finished.size();
+  return FINOM_OK;
+}
+
+finom_status finom_server_result(finom_server_t s, int64_t id, finom_server_done* out, double* f, double* g) {
+  if (!s || !out) {
+    finom::set_error("finom_server_result: null argument");
+    return FINOM_EINVAL;
+  }
+  auto it = s->finished.find(id);
+  if (it == s->finished.end()) {
+    finom::set_error("finom_server_result: request not finished (or unknown)");
+    return FINOM_EPENDING;
+  }
+  Req* r = it->second;
+  out->id = r->id;
+  out->kind = r->kind;
+  out->status = r->status;
+  out->result = r->res;
+  out->latency_s = r->t_done - r->t_submit;
+  out->queue_s = r->t_admit > 0.0 ? r->t_admit - r->t_submit : out->latency_s;
+  if (f && !r->f.empty()) std::copy(r->f.begin(), r->f.end(), f);
+  if (g && !r->g.empty()) std::copy(r->g.begin(), r->g.end(), g);
+  s->finished.erase(it);
+  delete r;
+  return FINOM_OK;
+}
+
+finom_status finom_server_destroy(finom_server_t s) {
+  if (!s) return FINOM_OK;
+  for (Req* r : s->active) {
+    cudaStreamSynchronize(s->streams[r->slot]);
+    release(s, r);
+    delete r;
+  }
+  for (Req* r : s->pending) delete r;
+  for (auto& kv : s->finished) delete kv.second;
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  delete s;
+  return FINOM_OK;
+}
+
+}  // extern "C"

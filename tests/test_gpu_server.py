@@ -1,0 +1,165 @@
+"""GPU tests of the serving loop (finom_server_*): continuous batching of 1D
+and 2D solves of mixed sizes.
+
+Each served solve runs the arithmetic of finom_solve on its own plan, so a
+request's result must be the same (bit for bit) alone and in a mix of
+concurrent requests, and must match the CPU oracle's solve of that problem
+(W1 relative error <= 1e-4, float64 marginal error <= tol).
+"""
+import numpy as np
+import pytest
+
+from oracle import serial_c
+from tests.gpu_util import meshes
+
+pytestmark = pytest.mark.gpu
+
+
+def _masses(N, M, seed):
+    g = np.random.default_rng(seed)
+    u = g.uniform(0.05, 1, N)
+    v = g.uniform(0.05, 1, M)
+    return u / u.sum(), v / v.sum()
+
+
+def _requests():
+    """1D and 2D problems of mixed sizes: (kind, arrays, eps, tol, maxit)."""
+    from paper_2605_26659_gb300 import inputs
+    out = []
+    for k, (N, M, kind, eps) in enumerate([(300, 257, "uniform_random", 0.02), (5000, 3100, "graded", 0.01),
+                                           (40, 1, "uniform_random", 0.05), (2049, 2047, "ties", 0.01),
+                                           (12000, 12000, "graded", 0.01)]):
+        x, y = meshes(kind, N, M, 300 + k)
+        u, v = _masses(N, M, 400 + k)
+        out.append(("1d", (x, y, u, v), eps, 1e-7, 20000))
+    for (N, M) in [(64, 48), (96, 80)]:
+        pr = inputs.config3(N, M)
+        out.append(("2d", (pr.x1, pr.x2, pr.y1, pr.y2, pr.U, pr.V), pr.eps, 1e-6, 20000))
+    return out
+
+
+def _submit(srv, req):
+    kind, a, eps, tol, maxit = req
+    if kind == "1d":
+        return srv.submit_1d(*a, eps, tol, maxit)
+    return srv.submit_2d(*a, eps, tol, maxit)
+
+
+def _oracle(req):
+    kind, a, eps, tol, maxit = req
+    if kind == "1d":
+        x, y, u, v = a
+        fo, go, it, err = serial_c.sinkhorn(x, y, u, v, eps, tol, maxit)
+        return serial_c.cost(x, y, eps, fo, go), it
+    x1, x2, y1, y2, U, V = a
+    Ao, Bo, it, err = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, eps, tol, maxit)
+    return serial_c.cost2d(x1, y1, x2, y2, eps, Ao, Bo), it
+
+
+def _oracle_err(req, f, g):
+    kind, a, eps, tol, maxit = req
+    if kind == "1d":
+        x, y, u, v = a
+        return serial_c.marginal_error(x, y, eps, f, g, v)
+    x1, x2, y1, y2, U, V = a
+    return serial_c.marginal_error2d(x1, y1, x2, y2, eps, f, g, V)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_served_alone_equals_in_the_mix_and_matches_oracle(lib, prec):
+    reqs = _requests()
+    alone = []
+    for r in reqs:   # each request on its own server, one slot
+        srv = lib.Server(1 << 34, max_active=1, precision=prec)
+        rid = _submit(srv, r)
+        alone.append(srv.run([rid])[rid])
+        srv.close()
+    # the mix: every request queued at once, three slots, a 12 MB budget that
+    # makes the N = M = 12000 request wait for memory
+    srv = lib.Server(12 << 20, max_active=3, precision=prec)
+    ids = [_submit(srv, r) for r in reqs]
+    peak_active = 0
+    out = {}
+    while len(out) < len(ids):
+        pend, act, fin = srv.step()
+        peak_active = max(peak_active, act)
+        assert act <= 3
+        for rid in ids:
+            if rid not in out:
+                got = srv.result(rid)
+                if got is not None:
+                    out[rid] = got
+    srv.close()
+    assert peak_active >= 2   # requests overlapped on the GPU
+    for r, a, rid in zip(reqs, alone, ids):
+        da, fa, ga = a
+        dm, fm, gm = out[rid]
+        assert da["status"] == dm["status"] == 0
+        assert da["converged"] == dm["converged"] == 1, (r[0], da, dm)
+        # the same result alone and in the mix, bit for bit
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+        assert da["iters"] == dm["iters"] and da["w1"] == dm["w1"]
+        assert da["marginal_err"] == dm["marginal_err"]
+        # and the oracle's
+        w1o, ito = _oracle(r)
+        assert dm["w1"] == pytest.approx(w1o, rel=1e-4 if prec == "f32_log" else 1e-9)
+        if prec == "f64" and min(np.size(r[1][0]), np.size(r[1][1])) > 1:
+            assert dm["iters"] == ito
+        e_or = _oracle_err(r, fm, gm)
+        assert e_or <= r[3] * (1 + 1e-6) + 1e-15
+        assert dm["marginal_err"] == pytest.approx(e_or, rel=1e-6, abs=1e-13)
+        assert dm["latency_s"] >= dm["queue_s"] >= 0.0
+
+
+def test_served_solve_equals_blocking_solve(lib):
+    """A served FP64 solve gives what finom_solve gives on the same inputs."""
+    from tests.gpu_util import T, H
+    x, y = meshes("graded", 3000, 2500, 7)
+    u, v = _masses(3000, 2500, 8)
+    srv = lib.Server(1 << 30, max_active=2, precision="f64")
+    rid = srv.submit_1d(x, y, u, v, 0.01, 1e-9, 5000)
+    d, f, g = srv.run([rid])[rid]
+    srv.close()
+    p = lib.finom_plan(T(x), T(y), 0.01, "f64")
+    fb, gb, rb = lib.finom_solve(p, T(u), T(v), 1e-9, 5000)
+    assert d["iters"] == rb["iters"] and d["converged"] == rb["converged"] == 1
+    assert np.max(np.abs(f - H(fb))) <= 1e-12 * 0.01 and d["w1"] == pytest.approx(rb["w1"], rel=1e-13)
+
+
+def test_admission_by_footprint_and_slots(lib):
+    reqs = _requests()[:4]
+    # a budget below every footprint: one solve at a time (an idle server
+    # still admits the queue head)
+    srv = lib.Server(1, max_active=4, precision="f32_log")
+    ids = [_submit(srv, r) for r in reqs]
+    done = {}
+    while len(done) < len(ids):
+        pend, act, fin = srv.step()
+        assert act <= 1
+        for rid in ids:
+            if rid not in done:
+                got = srv.result(rid)
+                if got is not None:
+                    done[rid] = got
+    srv.close()
+    # one at a time, first come first served: each request is admitted after
+    # its predecessor has finished
+    d = [done[rid][0] for rid in ids]
+    assert all(x["converged"] == 1 for x in d)
+    for a, b in zip(d, d[1:]):
+        assert b["queue_s"] >= a["latency_s"] - 0.05
+
+
+def test_bad_request_fails_alone(lib):
+    srv = lib.Server(1 << 30, max_active=4, precision="f32_log")
+    x, y = meshes("uniform_random", 500, 400, 1)
+    u, v = _masses(500, 400, 2)
+    good = srv.submit_1d(x, y, u, v, 0.02, 1e-6, 5000)
+    bad = srv.submit_1d(x[::-1].copy(), y, u, v, 0.02, 1e-6, 5000)   # unsorted mesh
+    neg = srv.submit_1d(x, y, -u, v, 0.02, 1e-6, 5000)               # negative masses
+    assert srv.result(good) is None                                    # not finished yet
+    out = srv.run([good, bad, neg])
+    srv.close()
+    assert out[good][0]["status"] == 0 and out[good][0]["converged"] == 1
+    assert out[bad][0]["status"] == lib.FINOM_EINVAL
+    assert out[neg][0]["status"] == lib.FINOM_EINVAL
