@@ -624,22 +624,27 @@ def run_finom_serve(args, ws, rank, local):
 
 
 def cpu_baseline_batch(probs, budget_s=12.0):
-    """The CPU oracle on instances of the batch, solved one after another on one
-    core until the time budget is spent."""
+    """The CPU oracle on instances of the batch, one instance per host thread
+    (the serial C oracle runs outside the GIL), until the time budget is spent."""
+    import concurrent.futures as cf
+
     from oracle import serial_c
     serial_c.lib()
-    pts, t0 = 0, time.perf_counter()
-    k = 0
-    for q in probs:
+    cores = max(1, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+
+    def one(q):
         if time.perf_counter() - t0 > budget_s:
-            break
+            return 0
         _, _, it, _ = serial_c.sinkhorn(q.x, q.y, q.u, q.v, q.eps, 0.0, 20)
-        pts += (len(q.x) + len(q.y)) * it
-        k += 1
+        return (len(q.x) + len(q.y)) * it
+
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        done = [p for p in ex.map(one, probs) if p > 0]
     dt = time.perf_counter() - t0
-    return {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"20 Sinkhorn iterations of each of the first {k} instances, serial C float64 oracle "
-                      f"({dt:.1f} s)"}
+    return {"value": sum(done) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"20 Sinkhorn iterations of each of the first {len(done)} instances, serial C float64 "
+                      f"oracle, one instance per thread on {cores} threads ({dt:.1f} s)"}
 
 
 def run_finom(args, ws, rank, local):

@@ -42,7 +42,8 @@ typedef enum {
   FINOM_ECUDA = 3,            /* a CUDA runtime call failed (message in finom_last_error) */
   FINOM_EDEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up */
   FINOM_ENOTSUP = 5,          /* the plan's precision or kind does not support the call */
-  FINOM_EPENDING = 6          /* finom_server_result: the request has not finished (or is unknown) */
+  FINOM_EPENDING = 6,         /* finom_server_result: the request has not finished (or is unknown) */
+  FINOM_ECANCELED = 7         /* a served request was cancelled (finom_server_cancel) */
 } finom_status;
 
 typedef enum {
@@ -136,6 +137,33 @@ finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64
 finom_status finom_plan_batch(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
                               int64_t B, const double* eps, finom_precision prec, void* stream,
                               finom_plan_t* out);
+
+/*
+ * Tile size of 1D plans (not a form of the paper: a property of the GPU
+ * kernel).  The fused half-step kernel processes tiles of 256 threads x E
+ * points, E in {1, 2, 4, 8}.  finom_plan picks E from a tuning table indexed
+ * by precision and the bucket b = ceil(log2(N + M)); results of different E
+ * agree to rounding (float64) or within the float32 bounds.
+ *   finom_plan_set_elems  forces E on a 1D plan (2D and batch plans: ENOTSUP);
+ *                         releases the plan's solve state (a solve in
+ *                         progress ends).  Synchronises `stream`.
+ *   finom_plan_elems      E and the number of tiles of a plan.
+ *   finom_tune_set/get    one entry of the table (b in 0..39; process-wide).
+ *   finom_autotune        the autotuner of one bucket: times `iters` Sinkhorn
+ *                         iterations (after 16 warm-up ones) of a synthetic
+ *                         problem with N = M = 2^(b-1) (sorted pseudo-random
+ *                         points, eps = 1e-2) for E = 1, 2, 4, 8 with CUDA
+ *                         events on `stream`, installs the fastest in the
+ *                         table, returns it in *best and the four times (us
+ *                         per iteration, HOST array of 4, may be NULL) in
+ *                         us_per_iter.  4 <= b <= 26.  Synchronous.
+ */
+finom_status finom_plan_set_elems(finom_plan_t plan, int32_t elems, void* stream);
+finom_status finom_plan_elems(finom_plan_t plan, int32_t* elems, int64_t* tiles);
+finom_status finom_tune_set(finom_precision prec, int32_t log2_bucket, int32_t elems);
+finom_status finom_tune_get(finom_precision prec, int32_t log2_bucket, int32_t* elems);
+finom_status finom_autotune(finom_precision prec, int32_t log2_bucket, int32_t iters, int32_t* best,
+                            double* us_per_iter, void* stream);
 
 /* Number of instances of a batch plan (0 for other plans). */
 finom_status finom_plan_instances(finom_plan_t plan, int64_t* B);
@@ -252,6 +280,15 @@ finom_status finom_server_step(finom_server_t srv, int32_t* n_pending, int32_t* 
  * not finished (or the id is unknown).
  */
 finom_status finom_server_result(finom_server_t srv, int64_t id, finom_server_done* out, double* f, double* g);
+
+/*
+ * finom_server_cancel -- stop a request: a queued one is dropped, an active
+ * one is stopped after its launched work completes (its stream is
+ * synchronised) and its memory and slot are freed.  Either then finishes with
+ * status FINOM_ECANCELED (collect it with finom_server_result).  A finished
+ * request is left as it is.  FINOM_EINVAL for an unknown id.
+ */
+finom_status finom_server_cancel(finom_server_t srv, int64_t id);
 
 /* Release the server: waits for its active solves and drops every request. */
 finom_status finom_server_destroy(finom_server_t srv);

@@ -14,7 +14,8 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfinom.so")
 
-FINOM_OK, FINOM_EINVAL, FINOM_ENOMEM, FINOM_ECUDA, FINOM_EDEVICE_TIMEOUT, FINOM_ENOTSUP, FINOM_EPENDING = range(7)
+(FINOM_OK, FINOM_EINVAL, FINOM_ENOMEM, FINOM_ECUDA, FINOM_EDEVICE_TIMEOUT, FINOM_ENOTSUP, FINOM_EPENDING,
+ FINOM_ECANCELED) = range(8)
 F64, F32_LOG = 0, 1
 _PREC = {"f64": F64, "fp64": F64, "float64": F64, F64: F64,
          "f32_log": F32_LOG, "fp32_log": F32_LOG, "f32": F32_LOG, F32_LOG: F32_LOG}
@@ -74,12 +75,18 @@ _SIGS = {
     "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
     "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
     "finom_solve_batch_end": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_plan_set_elems": ([_P, _I32, _P], ctypes.c_int),
+    "finom_plan_elems": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_tune_set": ([ctypes.c_int, _I32, _I32], ctypes.c_int),
+    "finom_tune_get": ([ctypes.c_int, _I32, ctypes.POINTER(_I32)], ctypes.c_int),
+    "finom_autotune": ([ctypes.c_int, _I32, _I32, ctypes.POINTER(_I32), _P, _P], ctypes.c_int),
     "finom_server_create": ([_I64, _I32, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_server_submit_1d": ([_P, _P, _I64, _P, _I64, _P, _P, _D, _D, _I64, ctypes.POINTER(_I64)], ctypes.c_int),
     "finom_server_submit_2d": ([_P, _P, _P, _I64, _P, _P, _I64, _P, _P, _D, _D, _I64, ctypes.POINTER(_I64)],
                                ctypes.c_int),
     "finom_server_step": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
     "finom_server_result": ([_P, _I64, ctypes.POINTER(FinomServerDone), _P, _P], ctypes.c_int),
+    "finom_server_cancel": ([_P, _I64], ctypes.c_int),
     "finom_server_destroy": ([_P], ctypes.c_int),
 }
 
@@ -101,6 +108,10 @@ def load(path: str | None = None):
         fn.argtypes = args
         fn.restype = res
     _lib = lib
+    cache = os.environ.get("FINOM_TUNE_CACHE")
+    if cache and os.path.exists(cache):
+        from . import autotune
+        autotune.apply(cache)
     return lib
 
 
@@ -249,6 +260,41 @@ def finom_solve_batch_end(plan: Plan, f=None, g=None, stream=None):
     _check(_lib.finom_solve_batch_end(plan.handle, _dev(f, plan.N), _dev(g, plan.M),
                                       ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
     return f, g, [r.as_dict() for r in res]
+
+
+def finom_plan_set_elems(plan: Plan, elems, stream=None):
+    """Force the kernel's points per thread (1, 2, 4 or 8) on a 1D plan."""
+    _check(_lib.finom_plan_set_elems(plan.handle, int(elems), _stream(stream)))
+
+
+def finom_plan_elems(plan: Plan):
+    """(points per thread, tiles) of a plan."""
+    e, t = _I32(), _I64()
+    _check(_lib.finom_plan_elems(plan.handle, ctypes.byref(e), ctypes.byref(t)))
+    return e.value, t.value
+
+
+def finom_tune_set(precision, log2_bucket, elems):
+    load()
+    _check(_lib.finom_tune_set(_PREC[precision], int(log2_bucket), int(elems)))
+
+
+def finom_tune_get(precision, log2_bucket):
+    load()
+    e = _I32()
+    _check(_lib.finom_tune_get(_PREC[precision], int(log2_bucket), ctypes.byref(e)))
+    return e.value
+
+
+def finom_autotune(precision, log2_bucket, iters=64, stream=None):
+    """Time E = 1, 2, 4, 8 on a synthetic problem of 2^log2_bucket merged
+    points, install the fastest; returns (best, {E: us per iteration})."""
+    load()
+    best = _I32()
+    t = (ctypes.c_double * 4)()
+    _check(_lib.finom_autotune(_PREC[precision], int(log2_bucket), int(iters), ctypes.byref(best),
+                               ctypes.cast(t, ctypes.c_void_p), _stream(stream)))
+    return best.value, dict(zip((1, 2, 4, 8), list(t)))
 
 
 def finom_plan_destroy(plan: Plan):
@@ -447,6 +493,9 @@ class Server:
             f = f.reshape(shp[2], order="F")
             g = g.reshape(shp[2], order="F")
         return out, f, g
+
+    def cancel(self, rid):
+        _check(_lib.finom_server_cancel(self.handle, int(rid)))
 
     def run(self, ids):
         """Step until every request in ids has finished; returns {id: (done, f, g)}."""

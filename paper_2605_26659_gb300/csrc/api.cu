@@ -71,7 +71,7 @@ template <class R>
 finom_status ensure_state(finom_plan_s* p) {
   SolveState& st = p->st;
   if (st.ready) return FINOM_OK;
-  const int64_t N = p->N, M = p->M, C = p->C, NM = std::max(N, M);
+  const int64_t N = p->N, M = p->M, C = p->Ce, NM = std::max(N, M);
   for (int q = 0; q < 2; ++q) {
     FINOM_CUDA(cudaMalloc(&st.px[q], pot_size<R>() * N));
     FINOM_CUDA(cudaMalloc(&st.py[q], pot_size<R>() * M));
@@ -123,9 +123,10 @@ ApplyArgs<R> base_args(finom_plan_s* p) {
   ApplyArgs<R> a{};
   a.tbits = p->tbits;
   a.gap = (const R*)p->gap;
-  a.tile_x0 = p->tile_x0;
+  a.tile_x0 = p->tile_x0e;
   a.L = p->L;
-  a.C = (int)p->C;
+  a.C = (int)p->Ce;
+  a.elems = p->elems;
   a.lines = 1;
   a.o_es = 1;
   a.w_es = 1;
@@ -533,6 +534,7 @@ finom_status finom_plan(const double* x, int64_t N, const double* y, int64_t M, 
   p->prec = prec;
   cudaGetDevice(&p->device);
   finom_status rc = build_plan(p, x, y, (cudaStream_t)stream);
+  if (rc == FINOM_OK) rc = build_tiles_e(p, tune_pick(prec, N + M), (cudaStream_t)stream);
   if (rc != FINOM_OK) {
     free_plan(p);
     delete p;
@@ -630,6 +632,26 @@ finom_status finom_plan_batch(const double* x, const int64_t* offx, const double
     return rc;
   }
   *out = p;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_set_elems(finom_plan_t plan, int32_t elems, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (plan->dim != 1 || plan->B > 0) {
+    set_error("finom_plan_set_elems: only 1D single-problem plans choose their tile size");
+    return FINOM_ENOTSUP;
+  }
+  if (elems == plan->elems) return FINOM_OK;
+  DeviceGuard dg(plan->device);
+  FINOM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  free_state(plan);   // the scan scratch is sized by the tile count
+  return build_tiles_e(plan, elems, (cudaStream_t)stream);
+}
+
+finom_status finom_plan_elems(finom_plan_t plan, int32_t* elems, int64_t* tiles) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (elems) *elems = plan->elems;
+  if (tiles) *tiles = plan->Ce;
   return FINOM_OK;
 }
 

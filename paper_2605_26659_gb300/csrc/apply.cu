@@ -4,28 +4,10 @@
 #include <algorithm>
 #include <cmath>
 
-#include "apply.cuh"
+#include "apply_launch.cuh"
 #include "finom_internal.h"
 
 namespace finom {
-
-// persistent grid: as many CTAs as fit on the device at once, at most one per unit
-template <class R, int M>
-unsigned grid_of(int64_t units, size_t smem) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_apply<R, M>, kThreads, smem) != cudaSuccess) n = 1;
-    per_sm = n < 1 ? 1 : n;
-  }
-#ifndef FINOM_PERSIST
-#define FINOM_PERSIST 1
-#endif
-  return (unsigned)(FINOM_PERSIST ? std::min<int64_t>(units, (int64_t)per_sm * sms) : units);
-}
 
 template <class R>
 finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) {
@@ -47,11 +29,16 @@ finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s) 
   cfg.attrs = attr;
   cfg.numAttrs = FINOM_PDL ? 1 : 0;
   cudaError_t e = cudaSuccess;
-  switch (mode) {
-#define FINOM_CASE(M)                                                                         \
-  case M:                                                                                     \
-    cfg.gridDim = dim3(grid_of<R, M>(units, smem));                                          \
-    e = cudaLaunchKernelEx(&cfg, k_apply<R, M>, a);                                           \
+  if (a.elems != 0 && a.elems != kElems) {
+    // smaller tiles (1D plans only): instantiated in their own translation units
+    if (!launch_apply_small<R>(cfg, a, mode, units, smem, &e)) {
+      set_error("k_apply: unsupported launch mode for this tile size");
+      return FINOM_EINVAL;
+    }
+  } else switch (mode) {
+#define FINOM_CASE(M)                                \
+  case M:                                            \
+    e = launch_mode<R, M, kElems>(cfg, a, units, smem); \
     break;
     FINOM_CASE(kModeAgg)
     FINOM_CASE(kModeHalfY)

@@ -1,7 +1,8 @@
 // Fused FINOM half step on the merged order of the two meshes.
 //
-// One CTA owns one tile of kTile merged points; thread t walks kElems
-// consecutive points.  For the application with output side O and weight
+// One CTA owns one tile of E * kThreads merged points; thread t walks E
+// consecutive points (E = kElems = 8 for 2D lines and batches; a 1D plan may
+// use 1, 2 or 4 to spread small problems over more SMs).  For the application with output side O and weight
 // side W (O = x: K psi; O = y: K^T phi) the stabilised sums (Remark
 // log-domain-stabilization) are carried in log2 form relative to a frame:
 // at an O point its own absorbed potential, at a W point the frame of the O
@@ -123,6 +124,7 @@ struct ApplyArgs {
   double tol;
   int64_t maxit;
   int flags;
+  int elems;          // points per thread of the launch (the plan's tile / kThreads)
 };
 
 // padded index of a per-thread slot: conflict-free both for the threads that
@@ -282,19 +284,19 @@ __device__ __forceinline__ void cp_async_commit_wait() {
 //   L1[e] = B_e - D[e], L2[e] = B_e + PB[e]   (weight levels carried to the
 //           segment start; kNegBig for points without weight)
 //   mt[e] = mass mantissa in [1, 2) (0 for points without weight)
-template <class R, bool kWValid = false>
-__device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const R (&g)[kElems],
+template <class R, bool kWValid = false, int E = kElems>
+__device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const R (&g)[E],
                                           const typename Tr<R>::Pot* po, int o0,
                                           const typename Tr<R>::Pot* pw,
                                           const typename Tr<R>::Mass* mw, int w0, R w_uniform,
-                                          R (&D)[kElems], R (&PB)[kElems], R (&L1)[kElems],
-                                          R (&L2)[kElems], R (&mt)[kElems]) {
+                                          R (&D)[E], R (&PB)[E], R (&L1)[E],
+                                          R (&L2)[E], R (&mt)[E]) {
   using T = Tr<R>;
   typename T::Pot cprev = po[o0];
   int oi = o0 + 1, wi = w0;
   R d = R(0), pb = R(0);
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
+  for (int e = 0; e < E; ++e) {
     R dc = R(0);
     if ((omask >> e) & 1u) {
       const typename T::Pot c = po[oi++];
@@ -330,16 +332,16 @@ __device__ __forceinline__ void seg_terms(uint32_t omask, uint32_t wmask, const 
 // levels are replaced in place by the scaled terms mt 2^{L - M}.  Returns the
 // maps of both recurrences over the thread's points:
 //   forward  (D_last,  MF + D_last, sum tF),  backward (PB_last, MB, sum tB).
-template <class R>
-__device__ __forceinline__ bool seg_maps(const R (&D)[kElems], const R (&PB)[kElems],
-                                         R (&L1)[kElems], R (&L2)[kElems], const R (&mt)[kElems],
+template <class R, int E = kElems>
+__device__ __forceinline__ bool seg_maps(const R (&D)[E], const R (&PB)[E],
+                                         R (&L1)[E], R (&L2)[E], const R (&mt)[E],
                                          Agg<R>& mapF, Agg<R>& mapB, R& MF, R& MB) {
   using T = Tr<R>;
   MF = T::kNegBig;
   MB = T::kNegBig;
   R mnF = R(1e30), mnB = R(1e30);
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
+  for (int e = 0; e < E; ++e) {
     MF = fmax(MF, L1[e]);
     MB = fmax(MB, L2[e]);
     if (mt[e] > R(0)) {
@@ -353,59 +355,60 @@ __device__ __forceinline__ bool seg_maps(const R (&D)[kElems], const R (&PB)[kEl
   R sF = R(0), sB = R(0);
   if (fast) {
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
+    for (int e = 0; e < E; ++e) {
       L1[e] = mt[e] * T::ex2(L1[e] - MF);
       L2[e] = mt[e] * T::ex2(L2[e] - MB);
       sF += L1[e];
       sB += L2[e];
     }
-    R m1 = MF + D[kElems - 1];
+    R m1 = MF + D[E - 1];
     renorm(m1, sF);
     R m2 = MB;
     renorm(m2, sB);
-    mapF = {D[kElems - 1], m1, sF};
-    mapB = {PB[kElems - 1], m2, sB};
+    mapF = {D[E - 1], m1, sF};
+    mapB = {PB[E - 1], m2, sB};
   } else {
     R m1 = T::kNegBig, m2 = T::kNegBig;
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
+    for (int e = 0; e < E; ++e) {
       if (mt[e] > R(0)) {
         ls_add_fast(m1, sF, L1[e], mt[e]);
         ls_add_fast(m2, sB, L2[e], mt[e]);
       }
     }
-    m1 += D[kElems - 1];
+    m1 += D[E - 1];
     renorm(m1, sF);
     renorm(m2, sB);
-    mapF = {D[kElems - 1], m1, sF};
-    mapB = {PB[kElems - 1], m2, sB};
+    mapF = {D[E - 1], m1, sF};
+    mapB = {PB[E - 1], m2, sB};
   }
   return fast;
 }
 
-template <class R>
-__device__ __forceinline__ void load_gaps(const R* gap, int64_t seg, R (&g)[kElems]);
-
-template <>
-__device__ __forceinline__ void load_gaps<float>(const float* gap, int64_t seg, float (&g)[kElems]) {
-  // gap arrays are padded to whole tiles, so the vector loads stay in bounds
-  static_assert(kElems % 4 == 0 && kElems <= 16, "kElems");
-  const float4* p = reinterpret_cast<const float4*>(gap + seg);
+// the E gaps of a thread's points (seg is a multiple of E; gap arrays are
+// padded to whole tiles, so the vector loads stay in bounds)
+template <class R, int E = kElems>
+__device__ __forceinline__ void load_gaps(const R* gap, int64_t seg, R (&g)[E]) {
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16, "points per thread");
+  if constexpr (sizeof(R) == 4 && E >= 4) {
+    const float4* p = reinterpret_cast<const float4*>(gap + seg);
 #pragma unroll
-  for (int q = 0; q < kElems / 4; ++q) {
-    float4 v = __ldg(p + q);
-    g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
-  }
-}
-
-template <>
-__device__ __forceinline__ void load_gaps<double>(const double* gap, int64_t seg, double (&g)[kElems]) {
-  const double2* p = reinterpret_cast<const double2*>(gap + seg);
+    for (int q = 0; q < E / 4; ++q) {
+      float4 v = __ldg(p + q);
+      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+    }
+  } else if constexpr (sizeof(R) == 4 && E == 2) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(gap + seg));
+    g[0] = v.x; g[1] = v.y;
+  } else if constexpr (sizeof(R) == 8 && E >= 2) {
+    const double2* p = reinterpret_cast<const double2*>(gap + seg);
 #pragma unroll
-  for (int q = 0; q < kElems / 2; ++q) {
-    double2 a = __ldg(p + q);
-    g[2 * q] = a.x;
-    g[2 * q + 1] = a.y;
+    for (int q = 0; q < E / 2; ++q) {
+      double2 v = __ldg(p + q);
+      g[2 * q] = v.x; g[2 * q + 1] = v.y;
+    }
+  } else {
+    g[0] = __ldg(gap + seg);
   }
 }
 
@@ -675,8 +678,10 @@ __device__ void finish_launch(const ApplyArgs<R>& a, TileSmem<R>& sm, int units)
 }
 
 // One unit (line, tile) of a launch: steps 1-4 of the header comment.
-template <class R, int kFlags>
+template <class R, int kFlags, int E>
 __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& sm, int unit, bool first) {
+  static_assert(E <= kElems, "the shared tile is sized for kElems points per thread");
+  constexpr int kT = E * kThreads;   // merged points per tile
   constexpr bool kAggOnly = (kFlags & F_AGG_ONLY) != 0;
   constexpr bool kFrameW = (kFlags & F_FRAME_W) != 0;
   constexpr bool kWValid = (kFlags & F_WVALID) != 0;
@@ -702,7 +707,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     const int32_t* tx = a.tile_x0 + tb + b;
     x0 = tx[tile];
     x1 = tx[tile + 1];
-    pos0 = (int64_t)tb * kTile;
+    pos0 = (int64_t)tb * kT;
     if (a.iuni) {
       w_uniform = a.iuni[2 * b];
       o_scale = a.iuni[2 * b + 1];
@@ -716,8 +721,8 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     x0 = a.tile_x0[tile];
     x1 = a.tile_x0[tile + 1];
   }
-  const int64_t k0 = (int64_t)tile * kTile;
-  const int64_t kend = min(k0 + (int64_t)kTile, L);
+  const int64_t k0 = (int64_t)tile * kT;
+  const int64_t kend = min(k0 + (int64_t)kT, L);
   const int y0 = (int)(k0 - x0), y1 = (int)(kend - x1);
   const int o_start = a.o_is_x ? x0 : y0;
   const int n_o = a.o_is_x ? (x1 - x0) : (y1 - y0);
@@ -726,19 +731,19 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   const int wofs = n_o + 1;   // smem index of the W point before the tile
 
   // this thread's points
-  const int64_t seg = k0 + (int64_t)tid * kElems;
+  const int64_t seg = k0 + (int64_t)tid * E;
   const int64_t gseg = seg + pos0;   // position in the packed gap / type-bit arrays
   uint32_t vmask = 0;
   if (seg < L) {
     int64_t nv = L - seg;
-    vmask = nv >= kElems ? ((1u << kElems) - 1u) : ((1u << nv) - 1u);
+    vmask = nv >= E ? ((1u << E) - 1u) : ((1u << nv) - 1u);
   }
-  uint32_t bits = (seg < L) ? ((a.tbits[gseg >> 5] >> (gseg & 31)) & ((1u << kElems) - 1u)) : 0u;
+  uint32_t bits = (seg < L) ? ((a.tbits[gseg >> 5] >> (gseg & 31)) & ((1u << E) - 1u)) : 0u;
   const uint32_t xmask = bits & vmask, ymask = (~bits) & vmask;
   const uint32_t omask = a.o_is_x ? xmask : ymask;
   const uint32_t wmask = a.o_is_x ? ymask : xmask;
-  R g[kElems];
-  load_gaps<R>(a.gap, gseg, g);
+  R g[E];
+  load_gaps<R, E>(a.gap, gseg, g);
 
   // stage the tile's O and W data (plus the point before the tile) in shared
   // memory.  The O side is never written by the launch just before this one
@@ -781,7 +786,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     const bool uni = w_uniform > R(0);
     int oi = o_before, wl = w_before;
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
+    for (int e = 0; e < E; ++e) {
       if ((omask >> e) & 1u) {
         ++oi;
         sm.pot[oi] = uni ? T::zero() : T::neg(sm.pot[wofs + wl]);
@@ -792,11 +797,11 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     __syncthreads();
   }
 
-  R D[kElems], PB[kElems], L1[kElems], L2[kElems], mt[kElems], MF, MB;
+  R D[E], PB[E], L1[E], L2[E], mt[E], MF, MB;
   Agg<R> mapF, mapB;
-  seg_terms<R, kWValid>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
+  seg_terms<R, kWValid, E>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
                         w_uniform, D, PB, L1, L2, mt);
-  const bool fast = seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
+  const bool fast = seg_maps<R, E>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
 
   if constexpr (kAggOnly) {
     put_map(sm.tf, tid, mapF);
@@ -829,14 +834,14 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   //   p_e = D_e + log2(entry_f (+) weights t <= e),  q_e = -PB_e + log2(entry_b' (+) weights t > e)
   // with entry_b' = the backward entry state carried to the segment start;
   // each lam goes straight to its O point's outputs
-  const R ebm = eb.m + PB[kElems - 1];
+  const R ebm = eb.m + PB[E - 1];
   int oi = o_before;   // smem index of the O point before the current one
   R err = R(0);
   if (fast) {
     // backward terms strictly after e, in place
     R acc = R(0);
 #pragma unroll
-    for (int e = kElems - 1; e >= 0; --e) {
+    for (int e = E - 1; e >= 0; --e) {
       const R t = L2[e];
       L2[e] = acc;
       acc += t;
@@ -851,7 +856,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     const R cB0 = eb.s * T::ex2(lb1 - LB), cB1 = T::ex2(MB - LB);
     R pf = R(0);
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
+    for (int e = 0; e < E; ++e) {
       pf += L1[e];           // forward terms up to e
       if ((omask >> e) & 1u) {
         const R sf = fma(cF1, pf, cF0), sb = fma(cB1, L2[e], cB0);
@@ -864,11 +869,11 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     }
   } else {
     // levels spread over more than 60 bits: running-max log-sums
-    R lam[kElems];
-    R fm[kElems], fs[kElems];
+    R lam[E];
+    R fm[E], fs[E];
     R m = ef.m, sv = ef.s;
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
+    for (int e = 0; e < E; ++e) {
       if (mt[e] > R(0)) ls_add_fast(m, sv, L1[e], mt[e]);
       fm[e] = m;
       fs[e] = sv;
@@ -876,13 +881,13 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     m = ebm;
     sv = eb.s;
 #pragma unroll
-    for (int e = kElems - 1; e >= 0; --e) {
+    for (int e = E - 1; e >= 0; --e) {
       LS<R> s2 = ls_add(fm[e] + D[e], fs[e], m - PB[e], sv);
       lam[e] = s2.m + T::lg2(s2.s);
       if (mt[e] > R(0)) ls_add_fast(m, sv, L2[e], mt[e]);
     }
 #pragma unroll
-    for (int e = 0; e < kElems; ++e)
+    for (int e = 0; e < E; ++e)
       if ((omask >> e) & 1u) emit_o<R, kFlags>(a, sm, ++oi, lam[e], ob, o_start, o_scale, err);
   }
 
@@ -908,10 +913,10 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
     // next application: O' = current W (frames = current W potentials),
     // W' = current O (new potentials, same masses); same gaps (reloaded: they
     // are not kept in registers through the outputs)
-    load_gaps<R>(a.gap, gseg, g);
-    seg_terms<R>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0), D,
+    load_gaps<R, E>(a.gap, gseg, g);
+    seg_terms<R, false, E>(wmask, omask, g, sm.pot + wofs, w_before, sm.pot, sm.mass, o_before + 1, R(0), D,
                  PB, L1, L2, mt);
-    (void)seg_maps<R>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
+    (void)seg_maps<R, E>(D, PB, L1, L2, mt, mapF, mapB, MF, MB);
     put_map(sm.tf, tid, mapF);
     put_map(sm.tb, tid, mapB);
     __syncthreads();
@@ -928,7 +933,7 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
 // more in contention than it gains in balance).  The last CTA to finish
 // (ticket ctrl[0]) scans the new tile maps into carries, reduces the error
 // and updates the loop control.
-template <class R, int kFlags>
+template <class R, int kFlags, int E = kElems>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_apply(ApplyArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<R>& sm = *reinterpret_cast<TileSmem<R>*>(smem_raw);
@@ -940,14 +945,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? FINOM_MINB : 1) k_a
     griddep_launch_dependents();
     const int units = *(volatile const int32_t*)a.acount;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
-      apply_unit<R, kFlags>(a, sm, a.alist[u], false);
+      apply_unit<R, kFlags, E>(a, sm, a.alist[u], false);
       __syncthreads();
     }
     return;
   }
   const int units = a.lines * a.C;
   for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
-    if (!apply_unit<R, kFlags>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
+    if (!apply_unit<R, kFlags, E>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
     __syncthreads();
   }
   griddep_wait();   // (a no-op after the first unit's wait)

@@ -94,6 +94,13 @@ struct finom_plan_s {
   void* gap = nullptr;           // per merged point: (z_k - z_{k-1}) / (eps ln 2), plan precision
   double* gap64 = nullptr;       // float64 gaps (the cost kernel uses them)
   int32_t* tile_x0 = nullptr;    // C + 1 entries: number of x points before each tile
+  // tiles of the fused half-step kernel on a 1D plan: elems points per thread
+  // (kElems, or 1, 2, 4 for small problems), Ce tiles of elems * kThreads
+  // points, tile_x0e the number of x points before each (tile_x0 when elems
+  // = kElems)
+  int elems = finom::kElems;
+  int64_t Ce = 0;
+  int32_t* tile_x0e = nullptr;
   int32_t* fw[2] = {nullptr, nullptr};  // per tile, [o_is_x]: the W point before the O point
                                         // that precedes the tile (frames of 2D first passes)
   // 2D plans (Sec. 3): grids x1 (x) y1 and x2 (x) y2 with N points on the x
@@ -118,6 +125,11 @@ struct finom_plan_s {
 
 namespace finom {
 finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaStream_t s);
+// tile table of a 1D plan for elems points per thread (plan.cu); the solve
+// state must be released by the caller when Ce changes
+finom_status build_tiles_e(finom_plan_s* p, int elems, cudaStream_t s);
+// points per thread that the tuning table gives a 1D plan of L merged points
+int tune_pick(finom_precision prec, int64_t L);
 void free_plan(finom_plan_s* p);
 finom_status cost64(finom_plan_s* p, const double* px, const double* py, const double* u,
                     const double* v, double* err, double* w1, cudaStream_t s);

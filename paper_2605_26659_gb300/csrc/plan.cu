@@ -10,6 +10,8 @@
 // are products of these factors over the merged points between two rows.
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include <cmath>
 #include <vector>
 
@@ -90,6 +92,20 @@ __global__ void k_tiles(const int64_t* posx, int64_t N, int64_t C, int32_t* tile
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
     if (posx[mid] < bound) lo = mid + 1; else hi = mid;
+  }
+  tile_x0[t] = (int32_t)lo;
+}
+
+// the same table for tiles of `tile` points from the dividing index: the
+// merged position of x_i is i + zeta(i) (y before x on ties), increasing in i
+__global__ void k_tiles_zeta(const int32_t* zeta, int64_t N, int64_t C, int64_t tile, int32_t* tile_x0) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t > C) return;
+  const int64_t bound = t * tile;
+  int64_t lo = 0, hi = N;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (mid + (int64_t)zeta[mid] < bound) lo = mid + 1; else hi = mid;
   }
   tile_x0[t] = (int32_t)lo;
 }
@@ -183,6 +199,37 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
   cudaFree(posy);
   cudaFree(z);
   cudaFree(type);
+  p->elems = kElems;
+  p->Ce = p->C;
+  p->tile_x0e = p->tile_x0;
+  return FINOM_OK;
+}
+
+finom_status build_tiles_e(finom_plan_s* p, int elems, cudaStream_t s) {
+  if (elems != 1 && elems != 2 && elems != 4 && elems != kElems) {
+    set_error("points per thread must be 1, 2, 4 or " + std::to_string(kElems));
+    return FINOM_EINVAL;
+  }
+  if (elems == p->elems) return FINOM_OK;
+  if (p->tile_x0e && p->tile_x0e != p->tile_x0) cudaFree(p->tile_x0e);
+  p->tile_x0e = p->tile_x0;
+  p->Ce = p->C;
+  p->elems = kElems;
+  if (elems == kElems) return FINOM_OK;
+  const int64_t tile = (int64_t)elems * kThreads;
+  const int64_t Ce = (p->L + tile - 1) / tile;
+  int32_t* t0 = nullptr;
+  FINOM_CUDA(cudaMalloc(&t0, sizeof(int32_t) * (Ce + 1)));
+  k_tiles_zeta<<<nblk(Ce + 1, 256), 256, 0, s>>>(p->zeta, p->N, Ce, tile, t0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(t0);
+    return cuda_fail(e, "k_tiles_zeta");
+  }
+  p->tile_x0e = t0;
+  p->Ce = Ce;
+  p->elems = elems;
   return FINOM_OK;
 }
 
@@ -194,6 +241,7 @@ void free_plan(finom_plan_s* p) {
   cudaFree(p->tbits);
   if (p->gap && p->gap != p->gap64) cudaFree(p->gap);
   cudaFree(p->gap64);
+  if (p->tile_x0e && p->tile_x0e != p->tile_x0) cudaFree(p->tile_x0e);
   cudaFree(p->tile_x0);
   cudaFree(p->fw[0]);
   cudaFree(p->fw[1]);

@@ -351,6 +351,37 @@ finom_status finom_server_result(finom_server_t s, int64_t id, finom_server_done
   return FINOM_OK;
 }
 
+finom_status finom_server_cancel(finom_server_t s, int64_t id) {
+  if (!s) {
+    finom::set_error("finom_server_cancel: null server");
+    return FINOM_EINVAL;
+  }
+  if (s->finished.count(id)) return FINOM_OK;
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+    if ((*it)->id != id) continue;
+    Req* r = *it;
+    s->pending.erase(it);
+    r->status = r->res.status = FINOM_ECANCELED;
+    r->t_done = now_s();
+    s->finished[id] = r;
+    return FINOM_OK;
+  }
+  for (auto it = s->active.begin(); it != s->active.end(); ++it) {
+    if ((*it)->id != id) continue;
+    Req* r = *it;
+    s->active.erase(it);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->device) cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->streams[r->slot]);
+    fail(s, r, FINOM_ECANCELED);
+    if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    return FINOM_OK;
+  }
+  finom::set_error("finom_server_cancel: unknown request id");
+  return FINOM_EINVAL;
+}
+
 finom_status finom_server_destroy(finom_server_t s) {
   if (!s) return FINOM_OK;
   for (Req* r : s->active) {

@@ -58,3 +58,28 @@ def test_null_plan_is_rejected_without_gpu(libpath):
     # bad sizes / eps are rejected before any CUDA call
     assert lib.finom_plan(None, 0, None, 5, 0.1, 1, None, ctypes.byref(h)) == 1
     assert lib.finom_plan(None, 5, None, 5, -1.0, 1, None, ctypes.byref(h)) == 1
+
+
+def test_tuning_table_round_trip_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.finom_tune_set.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32]
+    lib.finom_tune_set.restype = ctypes.c_int
+    lib.finom_tune_get.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.finom_tune_get.restype = ctypes.c_int
+    e = ctypes.c_int32()
+    for prec in (0, 1):
+        for b in (0, 10, 20, 39):
+            assert lib.finom_tune_get(prec, b, ctypes.byref(e)) == 0
+            assert e.value in (1, 2, 4, 8)
+    old = ctypes.c_int32()
+    lib.finom_tune_get(1, 12, ctypes.byref(old))
+    assert lib.finom_tune_set(1, 12, 4) == 0
+    assert lib.finom_tune_get(1, 12, ctypes.byref(e)) == 0 and e.value == 4
+    assert lib.finom_tune_set(1, 12, old.value) == 0
+    # invalid entries are refused and change nothing
+    assert lib.finom_tune_set(1, 12, 3) == 1
+    assert lib.finom_tune_set(1, 40, 2) == 1
+    assert lib.finom_tune_set(7, 12, 2) == 1
+    assert lib.finom_tune_get(1, -1, ctypes.byref(e)) == 1
+    lib.finom_tune_get(1, 12, ctypes.byref(e))
+    assert e.value == old.value

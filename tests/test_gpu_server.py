@@ -163,3 +163,23 @@ def test_bad_request_fails_alone(lib):
     assert out[good][0]["status"] == 0 and out[good][0]["converged"] == 1
     assert out[bad][0]["status"] == lib.FINOM_EINVAL
     assert out[neg][0]["status"] == lib.FINOM_EINVAL
+
+
+def test_cancel_queued_and_active(lib):
+    srv = lib.Server(1 << 30, max_active=1, precision="f32_log")
+    x, y = meshes("graded", 20000, 20000, 3)
+    u, v = _masses(20000, 20000, 4)
+    a = srv.submit_1d(x, y, u, v, 0.001, 1e-9, 100000)   # long: still active when cancelled
+    b = srv.submit_1d(x, y, u, v, 0.02, 1e-6, 5000)      # queued behind it
+    c = srv.submit_1d(x, y, u, v, 0.02, 1e-6, 5000)
+    srv.step()
+    srv.step()
+    srv.cancel(b)
+    srv.cancel(a)
+    with pytest.raises(lib.FinomError):
+        srv.cancel(12345)
+    out = srv.run([a, b, c])
+    srv.close()
+    assert out[a][0]["status"] == lib.FINOM_ECANCELED
+    assert out[b][0]["status"] == lib.FINOM_ECANCELED
+    assert out[c][0]["status"] == 0 and out[c][0]["converged"] == 1

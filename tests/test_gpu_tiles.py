@@ -1,0 +1,114 @@
+"""The fused half-step kernel with every tile size (points per thread E in
+{1, 2, 4, 8}) on 1D plans: products and solves against the CPU oracle, the
+tile counts, agreement across E, and the autotuner.
+
+Small problems run with small tiles by default (the tuning table), so the
+other GPU tests cover E < 8 too; here every E runs on the same inputs, with
+problems that span many tiles of the smallest size and end in a ragged tile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, serial_c
+from tests.test_gpu_products import f32_gap_bound
+from tests.gpu_util import H, T, meshes, relerr
+
+pytestmark = pytest.mark.gpu
+
+ELEMS = [1, 2, 4, 8]
+TOL = {"f64": 1e-12, "f32_log": 1e-5}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("E", ELEMS)
+@pytest.mark.parametrize("N,M,kind", [(3000, 2500, "uniform_random"), (777, 5003, "graded"),
+                                      (2049, 2047, "ties"), (1, 300, "uniform_random")])
+def test_products_every_tile_size(lib, prec, E, N, M, kind):
+    x, y = meshes(kind, N, M, 11 * N + M)
+    eps = 0.01
+    p = lib.finom_plan(T(x), T(y), eps, prec)
+    lib.finom_plan_set_elems(p, E)
+    e, tiles = lib.finom_plan_elems(p)
+    assert e == E and tiles == math.ceil((N + M) / (256 * E))
+    g = np.random.default_rng(N + M)
+    v = g.uniform(0, 1, M)
+    v[g.random(M) < 0.05] = 0.0
+    u = g.uniform(0, 1, N)
+    C = dense.cost_1d(x, y)
+    tol = TOL[prec] if prec == "f64" else f32_gap_bound(x, y, eps)
+    assert relerr(H(lib.finom_kv(p, T(v))), dense.kv_dense(C, v, eps)) <= tol
+    assert relerr(H(lib.finom_ktu(p, T(u))), dense.ktu_dense(C, u, eps)) <= tol
+    a = 0.3 * eps * np.sin(7 * x)
+    b = np.where(v > 0, 0.3 * eps * np.cos(5 * y), -np.inf)
+    got = H(lib.finom_kv_log(p, T(a), T(b)))
+    want = dense.log_apply_dense(C, a, b, eps)
+    assert np.max(np.abs(got - want)) <= tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("E", ELEMS)
+def test_solve_every_tile_size(lib, prec, E):
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.config1()
+    p = lib.finom_plan(T(pr.x), T(pr.y), pr.eps, prec)
+    lib.finom_plan_set_elems(p, E)
+    f, g, res = lib.finom_solve(p, T(pr.u), T(pr.v), 0.0, 25)
+    fo, go, it, err = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 25)
+    assert res["iters"] == it == 25
+    lock = 1e-10 if prec == "f64" else 2e-5
+    assert np.max(np.abs(H(f) - fo)) / pr.eps <= lock and np.max(np.abs(H(g) - go)) / pr.eps <= lock
+    # a problem that converges in ~900 iterations (eps = 0.03)
+    x, y = meshes("uniform_random", 1500, 1300, 4)
+    gg = np.random.default_rng(2)
+    u, v = gg.uniform(0.1, 1, 1500), gg.uniform(0.1, 1, 1300)
+    u, v = u / u.sum(), v / v.sum()
+    p = lib.finom_plan(T(x), T(y), 0.03, prec)
+    lib.finom_plan_set_elems(p, E)
+    tol = 1e-9 if prec == "f64" else 1e-6
+    f, g, res = lib.finom_solve(p, T(u), T(v), tol, 100000)
+    fo, go, it, err = serial_c.sinkhorn(x, y, u, v, 0.03, tol, 100000)
+    assert res["converged"] == 1
+    assert res["w1"] == pytest.approx(serial_c.cost(x, y, 0.03, fo, go), rel=1e-9 if prec == "f64" else 1e-4)
+    if prec == "f64":
+        assert res["iters"] == it
+
+
+def test_tile_sizes_agree_fp64(lib):
+    x, y = meshes("graded", 6000, 5000, 5)
+    g = np.random.default_rng(1)
+    u, v = g.uniform(0.1, 1, 6000), g.uniform(0.1, 1, 5000)
+    outs = []
+    for E in ELEMS:
+        p = lib.finom_plan(T(x), T(y), 0.005, "f64")
+        lib.finom_plan_set_elems(p, E)
+        f, gg, res = lib.finom_solve(p, T(u), T(v), 0.0, 40)
+        outs.append((H(f), H(gg), res["w1"]))
+    for f, gg, w1 in outs[1:]:
+        assert np.max(np.abs(f - outs[0][0])) <= 1e-13 and np.max(np.abs(gg - outs[0][1])) <= 1e-13
+        assert w1 == pytest.approx(outs[0][2], rel=1e-13)
+
+
+def test_set_elems_refuses_other_plans(lib):
+    x, y = meshes("uniform_random", 100, 90, 2)
+    p = lib.finom_plan(T(x), T(y), 0.01, "f32_log")
+    with pytest.raises(lib.FinomError) as e:
+        lib.finom_plan_set_elems(p, 3)
+    assert e.value.status == lib.FINOM_EINVAL
+    p2 = lib.finom_plan_2d(T(x), T(x), T(y), T(y), 0.01, "f32_log")
+    with pytest.raises(lib.FinomError) as e:
+        lib.finom_plan_set_elems(p2, 2)
+    assert e.value.status == lib.FINOM_ENOTSUP
+
+
+def test_autotune_installs_the_fastest(lib):
+    old = lib.finom_tune_get("f32_log", 12)
+    best, times = lib.finom_autotune("f32_log", 12, iters=32)
+    assert best in ELEMS and set(times) == set(ELEMS)
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    assert lib.finom_tune_get("f32_log", 12) == best
+    x, y = meshes("uniform_random", 1500, 1400, 3)   # 2900 merged points: bucket 12
+    p = lib.finom_plan(T(x), T(y), 0.01, "f32_log")
+    assert lib.finom_plan_elems(p)[0] == best
+    lib.finom_tune_set("f32_log", 12, old)
