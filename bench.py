@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["1d", "2d", "batch", "serve"], default="1d")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
-    ap.add_argument("--slots", type=int, default=32, help="serve: concurrent solves (streams)")
+    ap.add_argument("--slots", type=int, default=64, help="serve: concurrent solves (streams)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
     ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
     ap.add_argument("--e2e-count", type=int, default=512, help="batch: instances of the end-to-end solve")

@@ -641,21 +641,72 @@ __device__ __forceinline__ void emit_o(const ApplyArgs<R>& a, TileSmem<R>& sm, i
   }
 }
 
+// Last CTA of a launch with at most kSmallTail tiles on one line: warp 0
+// scans the forward tile maps, warp 1 the backward ones, 32 tiles per round
+// (one per lane, shuffle scans; the state leaving a round enters the next),
+// warp 2 sums the error partials; every thread gets the error sum.  Short
+// dependent chains and little code for the small problems whose launches
+// this tail would otherwise dominate.
+constexpr int kSmallTail = 128;
+
+template <class R, int kFlags>
+__device__ double finish_small(const ApplyArgs<R>& a, TileSmem<R>& sm, int units) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((kFlags & (F_NEXT | F_AGG_ONLY)) && warp < 2) {
+    const bool bwd = warp == 1;
+    LS<R> run = ls_empty<R>();
+    const int rounds = (a.C + 31) >> 5;
+#pragma unroll 1
+    for (int r = 0; r < rounds; ++r) {
+      const int t = bwd ? a.C - 1 - (32 * r + lane) : 32 * r + lane;   // this lane's tile
+      Agg<R> f = t >= 0 && t < a.C ? ld_map(a.agg_out + 6 * t + (bwd ? 3 : 0)) : agg_identity<R>();
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const Agg<R> u = shfl_up_agg(f, o);
+        if (lane >= o) f = agg_then(u, f);
+      }
+      Agg<R> fx = shfl_up_agg(f, 1);
+      if (lane == 0) fx = agg_identity<R>();
+      const LS<R> st = agg_apply(fx, run);
+      if (t >= 0 && t < a.C) {
+        a.carry_out[4 * t + (bwd ? 2 : 0)] = st.m;
+        a.carry_out[4 * t + (bwd ? 3 : 1)] = st.s;
+      }
+      const Agg<R> tot = {__shfl_sync(0xffffffffu, f.D, 31), __shfl_sync(0xffffffffu, f.m, 31),
+                          __shfl_sync(0xffffffffu, f.s, 31)};
+      run = agg_apply(tot, run);
+    }
+  }
+  if ((kFlags & F_ERR) && warp == 2) {
+    double e = 0.0;
+#pragma unroll 1
+    for (int i = lane; i < units; i += 32) e += __ldcg(a.part + i);
+    e = warp_sum(e);
+    if (lane == 0) sm.red[0] = e;
+  }
+  __syncthreads();
+  return (kFlags & F_ERR) ? sm.red[0] : 0.0;
+}
+
 // The end of a launch, in the CTA that finishes last: carries of the next
 // application, the float64 error sum, the loop control.  This code runs once
 // per launch on one SM, mostly from a cold instruction cache: its loops stay
 // rolled.
 template <class R, int kFlags>
 __device__ void finish_launch(const ApplyArgs<R>& a, TileSmem<R>& sm, int units) {
-  // the error partials are requested first so that their loads overlap the scan
-  double ep = 0.0;
-  if (kFlags & F_ERR) ep = load_parts(a.part, units);
-  if (kFlags & (F_NEXT | F_AGG_ONLY)) {
-    if (a.lines == 1) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
-    else carry_scan_lines<R>(a.agg_out, a.carry_out, a.lines, a.C);
-  }
   double errsum = 0.0;
-  if (kFlags & F_ERR) errsum = block_sum<R>(ep, sm);
+  if (a.lines == 1 && a.C <= kSmallTail) {
+    errsum = finish_small<R, kFlags>(a, sm, units);
+  } else {
+    // the error partials are requested first so that their loads overlap the scan
+    double ep = 0.0;
+    if (kFlags & F_ERR) ep = load_parts(a.part, units);
+    if (kFlags & (F_NEXT | F_AGG_ONLY)) {
+      if (a.lines == 1) carry_scan<R>(a.agg_out, a.carry_out, a.C, sm);
+      else carry_scan_lines<R>(a.agg_out, a.carry_out, a.lines, a.C);
+    }
+    if (kFlags & F_ERR) errsum = block_sum<R>(ep, sm);
+  }
   if (threadIdx.x == 0) {
     int32_t* c = a.ctrl;
     if (kFlags & F_ERR) {

@@ -27,15 +27,16 @@ std::mutex g_tune_mu;
 
 // Defaults from a tuning run on GB300 (finom_autotune, 64 iterations per
 // candidate, buckets 2^10 .. 2^22): float64 up to 2^15 merged points takes
-// E = 1 (278 us per iteration against 416-485 us with E = 8), 2^16 E = 2,
-// 2^17 E = 4, larger E = 8; float32 up to 2^14 takes E = 1 (21-23 us against
-// 28-31 us), 2^15-2^16 E = 2, 2^17-2^19 E = 4, from 2^20 on E = 8.
+// E = 1 (127-165 us per iteration against 279-337 us with E = 8), 2^16 E = 2,
+// 2^17 E = 4, larger E = 8; float32 up to 2^13 takes E = 1 (12-14 us against
+// 20-23 us), 2^14-2^15 E = 2, 2^16-2^17 E = 4, 2^18 E = 8, 2^19 E = 4, from
+// 2^20 on E = 8.
 struct Table {
   int e[2][kBuckets];
   Table() {
     for (int b = 0; b < kBuckets; ++b) {
       e[FINOM_F64][b] = b <= 15 ? 1 : (b == 16 ? 2 : (b == 17 ? 4 : kElems));
-      e[FINOM_F32_LOG][b] = b <= 14 ? 1 : (b <= 16 ? 2 : (b <= 19 ? 4 : kElems));
+      e[FINOM_F32_LOG][b] = b <= 13 ? 1 : (b <= 15 ? 2 : (b <= 17 || b == 19 ? 4 : kElems));
     }
   }
 };
