@@ -688,6 +688,79 @@ __device__ double finish_small(const ApplyArgs<R>& a, TileSmem<R>& sm, int units
   return (kFlags & F_ERR) ? sm.red[0] : 0.0;
 }
 
+// Last CTA of a launch with kSmallTail < C <= mid_tail<R>() tiles on one line
+// (1025 float32, 683 float64):
+// four warps per direction.  Warp q of a direction scans the q-th quarter of
+// the tiles (in scan order: left to right forward, right to left backward)
+// in rounds of 32 and keeps each tile's exclusive prefix map within its
+// quarter in shared memory; the quarter totals then give each quarter its
+// entry state, which the same warp pushes through its tiles' prefix maps.
+template <class R>
+constexpr int mid_tail() {   // tiles whose prefix maps (6 values) fit in the staging arrays
+  return (int)((sizeof(TileSmem<R>::pot) + sizeof(TileSmem<R>::mass)) / (6 * sizeof(R)));
+}
+
+template <class R, int kFlags>
+__device__ double finish_mid(const ApplyArgs<R>& a, TileSmem<R>& sm, int units) {
+  constexpr int kMidTail = mid_tail<R>();
+  R* pre = reinterpret_cast<R*>(sm.pot);   // [dir][tile][3]: prefix maps (pot and mass are adjacent)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int C = a.C;
+  const bool bwd = warp >= 4;
+  const int q = warp & 3;
+  const int Q = (C + 3) >> 2;
+  const int k0 = q * Q, k1 = min(k0 + Q, C);
+  R* mine = pre + (bwd ? 3 * kMidTail : 0);
+  Agg<R> run = agg_identity<R>();
+  double e = 0.0;
+  if (kFlags & (F_NEXT | F_AGG_ONLY)) {
+#pragma unroll 1
+    for (int kb = k0; kb < k1; kb += 32) {
+      const int k = kb + lane;
+      const int t = bwd ? C - 1 - k : k;
+      Agg<R> f = k < k1 ? ld_map(a.agg_out + 6 * t + (bwd ? 3 : 0)) : agg_identity<R>();
+#pragma unroll 1
+      for (int o = 1; o < 32; o <<= 1) {
+        const Agg<R> u = shfl_up_agg(f, o);
+        if (lane >= o) f = agg_then(u, f);
+      }
+      Agg<R> fx = shfl_up_agg(f, 1);
+      if (lane == 0) fx = agg_identity<R>();
+      if (k < k1) {
+        const Agg<R> p = agg_then(run, fx);
+        mine[3 * k] = p.D;
+        mine[3 * k + 1] = p.m;
+        mine[3 * k + 2] = p.s;
+      }
+      const Agg<R> tot = {__shfl_sync(0xffffffffu, f.D, 31), __shfl_sync(0xffffffffu, f.m, 31),
+                          __shfl_sync(0xffffffffu, f.s, 31)};
+      run = agg_then(run, tot);
+    }
+    if (lane == 0) sm.wf[warp] = run;
+  }
+  if (kFlags & F_ERR) {
+    // error partials: every thread sums a strided share (float64)
+#pragma unroll 1
+    for (int i = threadIdx.x; i < units; i += kThreads) e += __ldcg(a.part + i);
+  }
+  __syncthreads();
+  if (kFlags & (F_NEXT | F_AGG_ONLY)) {
+    LS<R> in = ls_empty<R>();
+#pragma unroll 1
+    for (int w = 0; w < q; ++w) in = agg_apply(sm.wf[(bwd ? 4 : 0) + w], in);
+#pragma unroll 1
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const int t = bwd ? C - 1 - k : k;
+      const LS<R> st = agg_apply(Agg<R>{mine[3 * k], mine[3 * k + 1], mine[3 * k + 2]}, in);
+      a.carry_out[4 * t + (bwd ? 2 : 0)] = st.m;
+      a.carry_out[4 * t + (bwd ? 3 : 1)] = st.s;
+    }
+  }
+  double errsum = 0.0;
+  if (kFlags & F_ERR) errsum = block_sum<R>(e, sm);
+  return errsum;
+}
+
 // The end of a launch, in the CTA that finishes last: carries of the next
 // application, the float64 error sum, the loop control.  This code runs once
 // per launch on one SM, mostly from a cold instruction cache: its loops stay
@@ -697,6 +770,8 @@ __device__ void finish_launch(const ApplyArgs<R>& a, TileSmem<R>& sm, int units)
   double errsum = 0.0;
   if (a.lines == 1 && a.C <= kSmallTail) {
     errsum = finish_small<R, kFlags>(a, sm, units);
+  } else if (a.lines == 1 && a.C <= mid_tail<R>()) {
+    errsum = finish_mid<R, kFlags>(a, sm, units);
   } else {
     // the error partials are requested first so that their loads overlap the scan
     double ep = 0.0;
