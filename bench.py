@@ -218,32 +218,65 @@ def cpu_baseline_2d(pr, budget_s=12.0):
                       f"{pr.U.shape[0]}x{pr.U.shape[1]} grids ({dt:.1f} s)"}
 
 
+def config_1d(N, M, eps, ws):
+    return {"workload": f"1D graded meshes N=M={N} (x=((i+1/2)/N)^2, tanh-stretched y, stretch 3), "
+                        f"3-Gaussian mixtures, eps=1e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
+            "N": N, "M": M, "eps": eps, "point_iters_per_step": N + M,
+            "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"}
+
+
+def config_2d(N, M, eps, ws):
+    return {"workload": f"2D grids {N}x{M} (tanh-clustered axes, stretch 2.5), 4 anisotropic "
+                        f"Gaussians, eps=2e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
+            "N": N, "M": M, "eps": eps, "point_iters_per_step": 2 * N * M,
+            "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"}
+
+
+def _sample_stride(t_full, steps, warmup, budget_s=150.0, power=1):
+    """Smallest power-of-two stride s with (steps + warmup) iterations of the
+    strided sample (t_full / s^power each) inside the time budget."""
+    s = 1
+    while (steps + warmup) * t_full / s ** power > budget_s and s < 1 << 12:
+        s *= 2
+    return s
+
+
 def run_reference(args, ws, rank):
+    """The oracle on the host cores, on this arm's workload and config: each
+    step is one Sinkhorn iteration of the serial C float64 oracle on a strided
+    sample of the meshes (every s-th point, masses renormalised; s the
+    smallest power of two that keeps the whole run within a few minutes),
+    reported per point-iteration."""
     if rank != 0:
         return
+    import numpy as np
     if args.workload == "2d":
         return run_reference_2d(args)
     from paper_2605_26659_gb300 import inputs
     pr = inputs.config2(args.n)
     from oracle import serial_c
     serial_c.lib()
-    # each step: one Sinkhorn iteration of the oracle at full size
-    f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 0)
+    t0 = time.perf_counter()
+    f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1)
+    t_full = time.perf_counter() - t0
+    st = _sample_stride(t_full, args.steps, args.warmup)
+    x, y = pr.x[::st], pr.y[::st]
+    u, v = pr.u[::st] / pr.u[::st].sum(), pr.v[::st] / pr.v[::st].sum()
+    f, g, _, _ = serial_c.sinkhorn(x, y, u, v, pr.eps, 0.0, 0)
     for _ in range(args.warmup):
-        f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1, f0=f, g0=g)
+        f, g, _, _ = serial_c.sinkhorn(x, y, u, v, pr.eps, 0.0, 1, f0=f, g0=g)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f, g, _, _ = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, 1, f0=f, g0=g)
+        f, g, _, _ = serial_c.sinkhorn(x, y, u, v, pr.eps, 0.0, 1, f0=f, g0=g)
     dt = time.perf_counter() - t0
-    val = (len(pr.x) + len(pr.y)) * args.steps / dt
+    val = (len(x) + len(y)) * args.steps / dt
+    sample = (f"{args.steps} Sinkhorn iterations of the serial C float64 oracle on every {st}-th point of the "
+              f"N=M={args.n} graded meshes ({len(x)}+{len(y)} points, {dt:.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "gpu_launches": 0,
-            "config": {"workload": f"1D graded meshes N=M={args.n}, eps=1e-3, one Sinkhorn iteration per step",
-                       "N": args.n, "M": args.n, "eps": pr.eps},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} Sinkhorn iterations of the serial C float64 oracle"},
+            "data": "synthetic", "gpu_launches": 0, "config": config_1d(args.n, args.n, pr.eps, 1),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -253,23 +286,29 @@ def run_reference_2d(args):
     from oracle import serial_c
     pr = inputs.config3(args.side)
     serial_c.lib()
-    A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 0)
+    t0 = time.perf_counter()
+    serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1)
+    t_full = time.perf_counter() - t0
+    st = _sample_stride(t_full, args.steps, args.warmup, power=2)
+    x1, y1, x2, y2 = pr.x1[::st], pr.y1[::st], pr.x2[::st], pr.y2[::st]
+    U, V = pr.U[::st, ::st], pr.V[::st, ::st]
+    U, V = U / U.sum(), V / V.sum()
+    A, B, _, _ = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, pr.eps, 0.0, 0)
     for _ in range(args.warmup):
-        A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1, A, B)
+        A, B, _, _ = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, pr.eps, 0.0, 1, A, B)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        A, B, _, _ = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 1, A, B)
+        A, B, _, _ = serial_c.sinkhorn2d(x1, y1, x2, y2, U, V, pr.eps, 0.0, 1, A, B)
     dt = time.perf_counter() - t0
-    n = pr.U.size + pr.V.size
+    n = U.size + V.size
     val = n * args.steps / dt
+    sample = (f"{args.steps} Sinkhorn iterations of the serial C float64 2D oracle on every {st}-th grid line "
+              f"of the {args.side}x{args.side} grids ({U.shape[0]}x{U.shape[1]}, {dt:.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "gpu_launches": 0,
-            "config": {"workload": f"2D grids {args.side}x{args.side}, eps=2e-3, one Sinkhorn iteration per step",
-                       "side": args.side, "eps": pr.eps},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} Sinkhorn iterations of the serial C float64 2D oracle"},
+            "data": "synthetic", "gpu_launches": 0, "config": config_2d(args.side, args.side, pr.eps, 1),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -368,10 +407,7 @@ def run_finom_2d(args, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"2D grids {N}x{M} (tanh-clustered axes, stretch 2.5), 4 anisotropic "
-                                   f"Gaussians, eps=2e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
-                       "N": N, "M": M, "eps": pr.eps, "point_iters_per_step": pts,
-                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "config": config_2d(N, M, pr.eps, ws),
             "gpu_launches": 4 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
@@ -711,10 +747,7 @@ def run_finom(args, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"1D graded meshes N=M={N} (x=((i+1/2)/N)^2, tanh-stretched y, stretch 3), "
-                                   f"3-Gaussian mixtures, eps=1e-3, FP32 log-domain; 1 Sinkhorn iteration per step",
-                       "N": N, "M": M, "eps": pr.eps, "point_iters_per_step": L,
-                       "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "config": config_1d(N, M, pr.eps, ws),
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,

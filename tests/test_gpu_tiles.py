@@ -112,3 +112,28 @@ def test_autotune_installs_the_fastest(lib):
     p = lib.finom_plan(T(x), T(y), 0.01, "f32_log")
     assert lib.finom_plan_elems(p)[0] == best
     lib.finom_tune_set("f32_log", 12, old)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_launch_tail_paths_agree(lib, prec):
+    """The last CTA of a launch scans the tile maps with one warp per direction
+    (up to 128 tiles), four warps per direction (up to 1025 float32 / 683
+    float64 tiles) or the whole block: N + M = 200,000 points give 98 tiles
+    with E = 8, 196 with E = 4, 391 with E = 2 and 782 with E = 1, so every
+    path runs on the same problem; a 30-iteration solve must agree."""
+    x, y = meshes("uniform_random", 110000, 90000, 8)
+    g = np.random.default_rng(3)
+    u, v = g.uniform(0.1, 1, 110000), g.uniform(0.1, 1, 90000)
+    outs = {}
+    for E in ELEMS:
+        p = lib.finom_plan(T(x), T(y), 0.002, prec)
+        lib.finom_plan_set_elems(p, E)
+        assert lib.finom_plan_elems(p)[1] == math.ceil(200000 / (256 * E))
+        f, gg, res = lib.finom_solve(p, T(u), T(v), 0.0, 30)
+        outs[E] = (H(f), H(gg), res)
+    ref = outs[8]
+    lock = 1e-12 if prec == "f64" else 3e-5
+    for E in (1, 2, 4):
+        f, gg, res = outs[E]
+        assert np.max(np.abs(f - ref[0])) / 0.002 <= lock and np.max(np.abs(gg - ref[1])) / 0.002 <= lock
+        assert res["marginal_err"] == pytest.approx(ref[2]["marginal_err"], rel=1e-9 if prec == "f64" else 1e-3)
