@@ -139,6 +139,31 @@ finom_status finom_plan_batch(const double* x, const int64_t* offx, const double
                               finom_plan_t* out);
 
 /*
+ * Queries of the transport plan Gamma = diag(phi) K diag(psi) that a solve
+ * returns (Algorithm 1 and Sec. 2.1: Gamma_ij = exp((f_i + g_j - |x_i - y_j|)
+ * / eps)), from potentials f (N), g (M) in cost units as finom_solve returns
+ * them (-inf where a mass is zero).  1D single-problem plans only (other
+ * plans: FINOM_ENOTSUP).  All arrays are device arrays; asynchronous on
+ * `stream`.
+ *   finom_transport_row  out (M doubles) = row i of Gamma, 0 <= i < N.
+ *   finom_transport_col  out (N doubles) = column j of Gamma, 0 <= j < M.
+ *   finom_barycentric    barycentric projections: tx (N doubles, may be
+ *                        NULL) tx_i = sum_j Gamma_ij y_j / sum_j Gamma_ij,
+ *                        ty (M doubles, may be NULL) ty_j = sum_i Gamma_ij
+ *                        x_i / sum_i Gamma_ij; two stabilised kernel
+ *                        products per side, O(N + M), in the plan's
+ *                        precision (float32 plans: absolute error ~1e-5 of
+ *                        the mesh extent).  Uses the plan's product scratch:
+ *                        a solve in progress on the plan ends.
+ */
+finom_status finom_transport_row(finom_plan_t plan, const double* f, const double* g, int64_t i, double* out,
+                                 void* stream);
+finom_status finom_transport_col(finom_plan_t plan, const double* f, const double* g, int64_t j, double* out,
+                                 void* stream);
+finom_status finom_barycentric(finom_plan_t plan, const double* f, const double* g, double* tx, double* ty,
+                               void* stream);
+
+/*
  * Tile size of 1D plans (not a form of the paper: a property of the GPU
  * kernel).  The fused half-step kernel processes tiles of 256 threads x E
  * points, E in {1, 2, 4, 8}.  finom_plan picks E from a tuning table indexed
@@ -352,6 +377,22 @@ finom_status finom_ktu_log(finom_plan_t plan, const double* a, const double* b, 
 finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, double tol,
                          int64_t maxit, double* f, double* g, int32_t warm, finom_result* res,
                          void* stream);
+
+/*
+ * finom_solve_eps_scaling -- finom_solve preceded by solves of the same
+ * problem at eps0, eps0 * factor, eps0 * factor^2, ... (while above the
+ * plan's eps), each to tol_stage on a plan of its own and warm-started from
+ * the previous stage's potentials; the last stage is finom_solve on `plan`
+ * (warm-started) to tol.  Not a form of the paper: the fixed point at the
+ * plan's eps is unchanged, only the starting potentials differ, which cuts
+ * the iterations at small eps.  res->iters counts the iterations of every
+ * stage (all within maxit); res->converged is the last stage's.  1D and 2D
+ * plans.  Arguments as finom_solve; eps0 > eps, 0 < factor < 1,
+ * tol_stage >= tol.  Synchronous.
+ */
+finom_status finom_solve_eps_scaling(finom_plan_t plan, const double* u, const double* v, double tol,
+                                     int64_t maxit, double eps0, double factor, double tol_stage, double* f,
+                                     double* g, finom_result* res, void* stream);
 
 /*
  * Stepwise form of finom_solve (same loop, driven by the caller):

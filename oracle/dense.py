@@ -33,7 +33,7 @@ from scipy.special import logsumexp
 __all__ = [
     "cost_1d", "cost_2d", "kernel", "kv_dense", "ktu_dense", "log_apply_dense",
     "SinkhornResult", "sinkhorn_log", "sinkhorn_linear", "marginal_error",
-    "transport_cost", "plan_from_potentials", "kron_2d",
+    "transport_cost", "plan_from_potentials", "barycentric", "kron_2d",
 ]
 
 
@@ -106,6 +106,17 @@ def plan_from_potentials(C, f, g, eps):
     """Gamma_ij = exp((f_i + g_j - C_ij)/eps) = phi_i k_ij psi_j (Sec. 2.1),
     with f = eps log phi and g = eps log psi."""
     return np.exp((f[:, None] + g[None, :] - C) / eps)
+
+
+def barycentric(C, f, g, eps, x, y):
+    """Barycentric projections of the plan Gamma returned by Algorithm 1:
+    the image of x_i is the Gamma-weighted mean of the y_j in row i,
+    sum_j Gamma_ij y_j / sum_j Gamma_ij, and that of y_j the weighted mean of
+    the x_i in column j.  Returns (tx [N], ty [M])."""
+    G = plan_from_potentials(C, np.asarray(f, dtype=np.float64), np.asarray(g, dtype=np.float64), eps)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    return G @ y / G.sum(axis=1), G.T @ x / G.sum(axis=0)
 
 
 def _col_logsum(C, f, g, eps):

@@ -75,6 +75,11 @@ _SIGS = {
     "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
     "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
     "finom_solve_batch_end": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_solve_eps_scaling": ([_P, _P, _P, _D, _I64, _D, _D, _D, _P, _P, ctypes.POINTER(FinomResult), _P],
+                                ctypes.c_int),
+    "finom_transport_row": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "finom_transport_col": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "finom_barycentric": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "finom_plan_set_elems": ([_P, _I32, _P], ctypes.c_int),
     "finom_plan_elems": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)], ctypes.c_int),
     "finom_tune_set": ([ctypes.c_int, _I32, _I32], ctypes.c_int),
@@ -260,6 +265,49 @@ def finom_solve_batch_end(plan: Plan, f=None, g=None, stream=None):
     _check(_lib.finom_solve_batch_end(plan.handle, _dev(f, plan.N), _dev(g, plan.M),
                                       ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
     return f, g, [r.as_dict() for r in res]
+
+
+def finom_solve_eps_scaling(plan: Plan, u, v, tol, maxit, eps0, factor=0.5, tol_stage=1e-4, stream=None):
+    """finom_solve preceded by warm-started solves at eps0, eps0*factor, ...;
+    returns (f, g, result dict)."""
+    import torch
+    dev = torch.device("cuda", plan.device)
+    f = torch.empty(plan.N, dtype=torch.float64, device=dev)
+    g = torch.empty(plan.M, dtype=torch.float64, device=dev)
+    res = FinomResult()
+    _check(_lib.finom_solve_eps_scaling(plan.handle, _dev(u, plan.N, torch.float64, "u"),
+                                        _dev(v, plan.M, torch.float64, "v"), float(tol), int(maxit), float(eps0),
+                                        float(factor), float(max(tol_stage, tol)), _dev(f, plan.N),
+                                        _dev(g, plan.M), ctypes.byref(res), _stream(stream)))
+    return f, g, res.as_dict()
+
+
+def finom_transport_row(plan: Plan, f, g, i, out=None, stream=None):
+    """Row i of the transport plan (M entries)."""
+    import torch
+    out = _out(plan.M, plan, out)
+    _check(_lib.finom_transport_row(plan.handle, _dev(f, plan.N, torch.float64, "f"),
+                                    _dev(g, plan.M, torch.float64, "g"), int(i), _dev(out, plan.M), _stream(stream)))
+    return out
+
+
+def finom_transport_col(plan: Plan, f, g, j, out=None, stream=None):
+    """Column j of the transport plan (N entries)."""
+    import torch
+    out = _out(plan.N, plan, out)
+    _check(_lib.finom_transport_col(plan.handle, _dev(f, plan.N, torch.float64, "f"),
+                                    _dev(g, plan.M, torch.float64, "g"), int(j), _dev(out, plan.N), _stream(stream)))
+    return out
+
+
+def finom_barycentric(plan: Plan, f, g, stream=None):
+    """Barycentric projections (tx on x, ty on y) of the transport plan."""
+    import torch
+    tx, ty = _out(plan.N, plan, None), _out(plan.M, plan, None)
+    _check(_lib.finom_barycentric(plan.handle, _dev(f, plan.N, torch.float64, "f"),
+                                  _dev(g, plan.M, torch.float64, "g"), _dev(tx, plan.N), _dev(ty, plan.M),
+                                  _stream(stream)))
+    return tx, ty
 
 
 def finom_plan_set_elems(plan: Plan, elems, stream=None):

@@ -783,6 +783,43 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
   return rc;
 }
 
+finom_status finom_solve_eps_scaling(finom_plan_t plan, const double* u, const double* v, double tol,
+                                     int64_t maxit, double eps0, double factor, double tol_stage, double* f,
+                                     double* g, finom_result* res, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve_eps_scaling")) return FINOM_ENOTSUP;
+  if (!u || !v || !f || !g || !res || !(tol >= 0.0) || maxit < 0 || !(eps0 > plan->eps) || !std::isfinite(eps0) ||
+      !(factor > 0.0 && factor < 1.0) || !(tol_stage >= tol)) {
+    set_error("finom_solve_eps_scaling: need u, v, f, g, res non-null, tol >= 0, maxit >= 0, eps0 > eps finite, "
+              "0 < factor < 1, tol_stage >= tol");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  int64_t done = 0;
+  int32_t warm = 0;
+  for (double e = eps0; e > plan->eps * (1.0 + 1e-12) && done < maxit; e *= factor) {
+    // the same meshes at the larger eps: a plan of its own, warm-started from
+    // the potentials of the previous stage
+    finom_plan_t q = nullptr;
+    finom_status rc = plan->dim == 2
+                          ? finom_plan_2d(plan->ax->x, plan->ax->y, plan->ax->N, plan->ay->x, plan->ay->y,
+                                          plan->ay->N, e, plan->prec, stream, &q)
+                          : finom_plan(plan->x, plan->N, plan->y, plan->M, e, plan->prec, stream, &q);
+    finom_result r{};
+    if (rc == FINOM_OK) rc = finom_solve(q, u, v, tol_stage, maxit - done, f, g, warm, &r, stream);
+    finom_plan_destroy(q);
+    if (rc != FINOM_OK) {
+      res->status = rc;
+      return rc;
+    }
+    done += r.iters;
+    warm = 1;
+  }
+  finom_status rc = finom_solve(plan, u, v, tol, maxit - done, f, g, warm, res, stream);
+  res->iters += done;
+  return rc;
+}
+
 finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double* v, double tol,
                                int64_t maxit, const double* f0, const double* g0, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;

@@ -340,3 +340,34 @@ def test_2d_with_one_row_reduces_to_1d():
     r2 = dense.sinkhorn_log(C2, U.ravel(), V.ravel(), eps, 1e-12, 100000)
     r1 = dense.sinkhorn_log(dense.cost_1d(x1, x2), U.ravel(), V.ravel(), eps, 1e-12, 100000)
     assert r2.w1 == pytest.approx(r1.w1 + abs(y1[0] - y2[0]), rel=1e-9)
+
+
+def test_barycentric_single_source_point_is_the_mean():
+    """With one source point every column of the converged plan holds v_j,
+    so x_0 maps to the mean of nu and every y_j maps back to x_0."""
+    x, y = np.array([0.37]), np.array([0.1, 0.25, 0.6, 0.8])
+    u, v = np.array([1.0]), np.array([0.1, 0.2, 0.3, 0.4])
+    C = dense.cost_1d(x, y)
+    res = dense.sinkhorn_log(C, u, v, 0.05, tol=1e-14, maxit=100)
+    tx, ty = dense.barycentric(C, res.f, res.g, 0.05, x, y)
+    assert tx[0] == pytest.approx(float(v @ y), abs=1e-13)
+    np.testing.assert_allclose(ty, 0.37, atol=1e-14)
+
+
+def test_barycentric_small_eps_is_the_monotone_matching():
+    """Equal masses on sorted, separated points: as eps -> 0 the entropic plan
+    tends to the sorted matching (the 1D optimal plan for W1 with equal masses
+    is monotone), so x_i maps to y_i and y_i to x_i; and swapping the roles of
+    the measures transposes the maps."""
+    x = np.array([0.05, 0.3, 0.55, 0.8])
+    y = np.array([0.12, 0.41, 0.6, 0.95])
+    w = np.full(4, 0.25)
+    C = dense.cost_1d(x, y)
+    res = dense.sinkhorn_log(C, w, w, 0.002, tol=1e-13, maxit=50000)
+    tx, ty = dense.barycentric(C, res.f, res.g, 0.002, x, y)
+    np.testing.assert_allclose(tx, y, atol=1e-6)
+    np.testing.assert_allclose(ty, x, atol=1e-6)
+    rs = dense.sinkhorn_log(C.T, w, w, 0.002, tol=1e-13, maxit=50000)
+    sx, sy = dense.barycentric(C.T, rs.f, rs.g, 0.002, y, x)
+    np.testing.assert_allclose(sx, ty, atol=1e-6)
+    np.testing.assert_allclose(sy, tx, atol=1e-6)
