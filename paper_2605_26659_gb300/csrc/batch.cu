@@ -232,12 +232,14 @@ struct BatchEndArgs {
   double* ierr;       // per instance: error of its last check
   const double* itol;
   int64_t maxit;
-  int32_t* ctrl;      // [1] every instance retired, [2] active instances
+  int32_t* ctrl;      // [1] every instance retired, [2] active instances, [6] an instance retired
+                      //     since the last compaction
   int maps, err, iter_end;
 };
 
 // retire instance b (lane 0): the last active instance ends the loop
 __device__ __forceinline__ void retire(int32_t* ctrl) {
+  ctrl[6] = 1;
   if (atomicSub(ctrl + 2, 1) == 1) ctrl[1] = 1;
 }
 
@@ -327,11 +329,13 @@ __global__ void k_batch_end(BatchEndArgs<R> a) {
 
 // The tiles of the active instances, in instance order, and their number
 // (one CTA of 1024 threads: each takes a run of instances, a block scan
-// places the runs).
+// places the runs).  Only when an instance retired since the last
+// compaction (*dirty); most half steps retire none and return at once.
 __global__ void __launch_bounds__(1024) k_batch_compact(const int32_t* itile, const int32_t* idone, int B,
-                                                        int32_t* alist, int32_t* acount) {
+                                                        int32_t* alist, int32_t* acount, int32_t* dirty) {
   __shared__ int32_t sh[1024];
   const int tid = threadIdx.x;
+  if (*(volatile int32_t*)dirty == 0) return;
   const int per = (B + 1023) / 1024;
   const int b0 = min(B, tid * per), b1 = min(B, b0 + per);
   int32_t n = 0;
@@ -349,7 +353,10 @@ __global__ void __launch_bounds__(1024) k_batch_compact(const int32_t* itile, co
   for (int b = b0; b < b1; ++b)
     if (!idone[b])
       for (int32_t t = itile[b]; t < itile[b + 1]; ++t) alist[at++] = t;
-  if (tid == 1023) *acount = sh[1023];
+  if (tid == 1023) {
+    *acount = sh[1023];
+    *dirty = 0;   // every thread read the flag before the first barrier
+  }
 }
 
 template <class R>
@@ -450,7 +457,7 @@ finom_status launch_end(finom_plan_s* p, int maps, int err, int iter_end, cudaSt
   e.err = err;
   e.iter_end = iter_end;
   k_batch_end<R><<<nblk(p->B, 8), 256, 0, s>>>(e);
-  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)p->B, st.alist, st.ctrl + 3);
+  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)p->B, st.alist, st.ctrl + 3, st.ctrl + 6);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "k_batch_end launch");
   return FINOM_OK;
@@ -609,11 +616,11 @@ finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, doub
   fill_d(st.itol, B, tol, s);
   FINOM_CUDA(cudaMemsetAsync(st.ictl, 0, sizeof(int32_t) * 6 * B, s));
   FINOM_CUDA(cudaMemsetAsync(st.ierr, 0, sizeof(double) * B, s));
-  int32_t c0[8] = {0, 0, (int32_t)B, 0, 0, 0, 0, 0};
+  int32_t c0[8] = {0, 0, (int32_t)B, 0, 0, 0, 1, 0};
   FINOM_CUDA(cudaMemcpyAsync(st.ctrl, c0, sizeof(c0), cudaMemcpyHostToDevice, s));
   st.tol = tol;
   st.maxit = maxit;
-  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3);
+  k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3, st.ctrl + 6);
   // iteration 0: maps of the first K^T phi, then its half step with the
   // check at the first loop head, then the phi half step
   ApplyArgs<R> a0 = batch_args<R>(p, false, 0, true);
@@ -713,9 +720,9 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     k_bswap<Pot><<<nblk(N, 256), 256, 0, s>>>((Pot*)st.px[0], (const Pot*)st.px[1], p->ioffx, (int)B, dswap, N);
     k_bswap<Pot><<<nblk(M, 256), 256, 0, s>>>((Pot*)st.py[1], (const Pot*)st.py[0], p->ioffy, (int)B, dswap, M);
     cudaFreeAsync(dswap, s);
-    int32_t c1[8] = {0, 0, n_resume, 0, 0, 0, 0, 0};
+    int32_t c1[8] = {0, 0, n_resume, 0, 0, 0, 1, 0};
     FINOM_CUDA(cudaMemcpyAsync(st.ctrl, c1, sizeof(c1), cudaMemcpyHostToDevice, s));
-    k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3);
+    k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3, st.ctrl + 6);
     // the phi half step of the stop iterations, at parity 0
     rc = launch_apply<R>(batch_args<R>(p, true, 0, false), false, s);
     if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);

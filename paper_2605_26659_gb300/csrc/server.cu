@@ -58,6 +58,11 @@ struct finom_server_s {
   std::map<int64_t, Req*> finished;
   std::vector<cudaStream_t> streams;
   std::vector<int> free_slots;
+  // plans of retired requests, destroyed together: freeing device memory
+  // waits for the whole device, so it is done once per batch of plans (or
+  // when their memory is needed) rather than at every retirement
+  std::vector<finom_plan_t> graveyard;
+  int64_t dead_bytes = 0;
 };
 
 namespace {
@@ -80,9 +85,19 @@ int64_t npoints(const Req* r, int side) {   // points of the first (side 0) or s
   return r->kind == 1 ? (side == 0 ? r->N : r->M) : r->N * r->M;
 }
 
+constexpr size_t kGraveyard = 32;
+
+void flush_graveyard(finom_server_s* s) {
+  for (finom_plan_t p : s->graveyard) finom_plan_destroy(p);
+  s->graveyard.clear();
+  s->used -= s->dead_bytes;
+  s->dead_bytes = 0;
+}
+
 void release(finom_server_s* s, Req* r) {
-  if (r->plan) finom_plan_destroy(r->plan);
-  if (r->plan64) finom_plan_destroy(r->plan64);
+  if (r->plan) s->graveyard.push_back(r->plan);
+  if (r->plan64) s->graveyard.push_back(r->plan64);
+  s->dead_bytes += r->footprint;   // still counted in used until the plans are destroyed
   if (r->dev) cudaFreeAsync(r->dev, s->streams[r->slot]);
   if (r->ev) cudaEventDestroy(r->ev);
   r->plan = nullptr;
@@ -91,7 +106,6 @@ void release(finom_server_s* s, Req* r) {
   r->ev = nullptr;
   if (r->slot >= 0) s->free_slots.push_back(r->slot);
   r->slot = -1;
-  s->used -= r->footprint;
   for (auto& v : r->in) std::vector<double>().swap(v);
 }
 
@@ -281,6 +295,7 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   // admissions, first come first served: an empty server always admits
   while (!s->pending.empty() && !s->free_slots.empty()) {
     Req* r = s->pending.front();
+    if (s->used + r->footprint > s->budget && !s->graveyard.empty()) flush_graveyard(s);
     if (!s->active.empty() && s->used + r->footprint > s->budget) break;
     s->pending.pop_front();
     finom_status rc = admit(s, r);
@@ -320,6 +335,7 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
     s->finished[r->id] = r;
   }
   s->active.swap(still);
+  if (s->graveyard.size() >= kGraveyard || (s->active.empty() && !s->graveyard.empty())) flush_graveyard(s);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   if (n_pending) *n_pending = (int32_t)s->pending.size();
   if (n_active) *n_active = (int32_t)s->active.size();
@@ -391,6 +407,7 @@ finom_status finom_server_destroy(finom_server_t s) {
   }
   for (Req* r : s->pending) delete r;
   for (auto& kv : s->finished) delete kv.second;
+  flush_graveyard(s);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   delete s;
   return FINOM_OK;
