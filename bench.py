@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrent solves (streams)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
+    ap.add_argument("--eps-stages", type=int, default=0,
+                    help="serve: eps-scaling stages of the second run (0: no second run)")
     ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
     ap.add_argument("--e2e-count", type=int, default=512, help="batch: instances of the end-to-end solve")
     ap.add_argument("--plain-count", type=int, default=16,
@@ -548,6 +550,32 @@ def _request_points(pr):
     return len(pr.x) + len(pr.y) if hasattr(pr, "x") else 2 * pr.U.size
 
 
+def _serve_once(api, args, reqs, probs, stages):
+    """Submit the requests at their arrival times to a fresh server, step it
+    until every request has finished; returns (wall seconds, results in
+    request order, peak active solves)."""
+    srv = api.Server(int(args.budget_gb * 2**30), max_active=args.slots, precision="f32_log")
+    if stages:
+        srv.set_eps_scaling(stages, 0.5, 1e-4)
+    t0 = time.perf_counter()
+    nxt, ids, done, peak_active = 0, {}, {}, 0
+    while len(done) < len(probs):
+        now = time.perf_counter() - t0
+        while nxt < len(probs) and reqs[nxt].t_arrival <= now:
+            ids[_submit_request(srv, probs[nxt])] = nxt
+            nxt += 1
+        pend, act, fin = srv.step()
+        peak_active = max(peak_active, act)
+        if fin:
+            for rid in [r for r in ids if ids[r] not in done]:
+                got = srv.result(rid)
+                if got is not None:
+                    done[ids[rid]] = got[0]
+    wall = time.perf_counter() - t0
+    srv.close()
+    return wall, [done[k] for k in range(len(probs))], peak_active
+
+
 def run_finom_serve(args, ws, rank, local):
     """Served solves/s and latency of the serving loop on the arrival process."""
     import numpy as np
@@ -564,6 +592,7 @@ def run_finom_serve(args, ws, rank, local):
     srv = api.Server(int(args.budget_gb * 2**30), max_active=args.slots, precision="f32_log")
     warm = [q for q in probs if _request_points(q) < 200000][:max(args.warmup, 1)]
     srv.run([_submit_request(srv, q) for q in warm])
+    srv.close()
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -573,31 +602,27 @@ def run_finom_serve(args, ws, rank, local):
     sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nxt, ids, done, peak_active = 0, {}, {}, 0
-    while len(done) < len(probs):
-        now = time.perf_counter() - t0
-        while nxt < len(probs) and reqs[nxt].t_arrival <= now:
-            ids[_submit_request(srv, probs[nxt])] = nxt
-            nxt += 1
-        pend, act, fin = srv.step()
-        peak_active = max(peak_active, act)
-        if fin:
-            for rid in [r for r in ids if ids[r] not in done]:
-                got = srv.result(rid)
-                if got is not None:
-                    done[ids[rid]] = got[0]
-    wall = time.perf_counter() - t0
+    wall, res, peak_active = _serve_once(api, args, reqs, probs, 0)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = sampler.stop()
-    srv.close()
     wall = max_over_ranks(wall, ws)
-    res = [done[k] for k in range(len(probs))]
     lat = np.array([r["latency_s"] for r in res])
     que = np.array([r["queue_s"] for r in res])
     nconv = sum(r["converged"] for r in res)
     pts = sum(_request_points(q) * r["iters"] for q, r in zip(probs, res))
+    # the same arrivals with eps scaling in the server (same fixed points)
+    scaled = None
+    if args.eps_stages > 0:
+        wall2, res2, _ = _serve_once(api, args, reqs, probs, args.eps_stages)
+        lat2 = np.array([r["latency_s"] for r in res2])
+        w1d = [abs(a["w1"] - b["w1"]) / abs(a["w1"]) for a, b in zip(res, res2) if a["converged"] and b["converged"]]
+        scaled = {"solves_per_s": ws * len(probs) / wall2, "stages": args.eps_stages, "factor": 0.5,
+                  "tol_stage": 1e-4, "converged": int(sum(r["converged"] for r in res2)),
+                  "latency_s": {"p50": float(np.percentile(lat2, 50)), "p99": float(np.percentile(lat2, 99))},
+                  "iterations": int(sum(r["iters"] for r in res2)),
+                  "iterations_plain": int(sum(r["iters"] for r in res)),
+                  "w1_max_relerr_vs_plain_served": max(w1d) if w1d else None}
     solves_per_s = ws * len(probs) / wall
     h2d = sum(8 * (2 * (len(q.x) + len(q.y)) if hasattr(q, "x") else 2 * (q.U.size + len(q.x1) + len(q.y1)))
               for q in probs)
@@ -654,6 +679,7 @@ def run_finom_serve(args, ws, rank, local):
             "plain_fp64_one_at_a_time": {"solves_per_s": 1.0 / plain_per_solve, "sample": len(plain),
                                          "seconds_per_solve": plain_per_solve,
                                          "w1_max_relerr_served_vs_plain": max(w1_dev) if w1_dev else None},
+            "eps_scaling": scaled,
             "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)

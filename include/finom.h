@@ -273,6 +273,18 @@ finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, f
                                  finom_server_t* out);
 
 /*
+ * finom_server_set_eps_scaling -- requests admitted from now on first solve
+ * their problem at eps / factor^stages, eps / factor^(stages-1), ...,
+ * eps / factor, each to tol_stage (or tol if larger) on a plan of its own and
+ * warm-started from the previous stage, then at their own eps to tol (as
+ * finom_solve_eps_scaling).  The fixed point is unchanged; at small eps it
+ * takes fewer iterations.  `iters` of a result counts every stage.  stages = 0
+ * (the default) turns it off.  0 <= stages <= 30, 0 < factor < 1,
+ * tol_stage > 0.
+ */
+finom_status finom_server_set_eps_scaling(finom_server_t srv, int32_t stages, double factor, double tol_stage);
+
+/*
  * finom_server_submit_1d -- queue a 1D solve (arguments as finom_plan and
  * finom_solve; x, y, u, v are HOST arrays of N, M, N, M doubles, copied before
  * the call returns).  *id receives the request id.  Sorting and mass checks

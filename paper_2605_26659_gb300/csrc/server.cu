@@ -39,7 +39,8 @@ struct finom_server_s {
     int slot = -1;
     finom_plan_t plan = nullptr;
     finom_plan_t plan64 = nullptr;    // after a switch to float64: the float32 plan
-    int64_t iters_before = 0;         // iterations before that switch
+    int64_t iters_before = 0;         // iterations before that switch (or the current stage)
+    int stages_left = 0;              // eps-scaling stages still to come before the final eps
     double* dev = nullptr;            // device inputs, then f and g
     cudaEvent_t ev = nullptr;
     int64_t step = 1;
@@ -50,6 +51,10 @@ struct finom_server_s {
   };
   int64_t budget = 0, used = 0;
   int max_active = 8;
+  // eps scaling (finom_server_set_eps_scaling): stages at eps / factor^k,
+  // k = stages .. 1, each to tol_stage, before the request's own eps
+  int sc_stages = 0;
+  double sc_factor = 0.5, sc_tol = 1e-4;
   finom_precision prec = FINOM_F32_LOG;
   int device = 0;
   int64_t next_id = 1;
@@ -117,6 +122,15 @@ void fail(finom_server_s* s, Req* r, finom_status rc) {
   s->finished[r->id] = r;
 }
 
+// a plan of the request's meshes (device copies in r->dev) at eps e
+finom_status plan_at(finom_server_s* s, Req* r, double e, finom_precision prec, finom_plan_t* out) {
+  (void)s;
+  const double* d = r->dev;
+  cudaStream_t st = s->streams[r->slot];
+  if (r->kind == 1) return finom_plan(d, r->N, d + r->N, r->M, e, prec, st, out);
+  return finom_plan_2d(d, d + r->N, r->N, d + 2 * r->N, d + 2 * r->N + r->M, r->M, e, prec, st, out);
+}
+
 // admit: device copies of the inputs, the plan, the start of the solve
 finom_status admit(finom_server_s* s, Req* r) {
   r->slot = s->free_slots.back();
@@ -139,14 +153,13 @@ finom_status admit(finom_server_s* s, Req* r) {
                                  cudaMemcpyHostToDevice, st));
     off += (int64_t)r->in[k].size();
   }
-  finom_status rc;
-  if (r->kind == 1) {
-    rc = finom_plan(d[0], r->N, d[1], r->M, r->eps, s->prec, st, &r->plan);
-    if (rc == FINOM_OK) rc = finom_solve_begin(r->plan, d[2], d[3], r->tol, r->maxit, nullptr, nullptr, st);
-  } else {
-    rc = finom_plan_2d(d[0], d[1], r->N, d[2], d[3], r->M, r->eps, s->prec, st, &r->plan);
-    if (rc == FINOM_OK) rc = finom_solve_begin(r->plan, d[4], d[5], r->tol, r->maxit, nullptr, nullptr, st);
-  }
+  r->stages_left = s->sc_stages;
+  const double e0 = r->eps / std::pow(s->sc_factor, r->stages_left);
+  const double tol0 = r->stages_left > 0 ? std::max(r->tol, s->sc_tol) : r->tol;
+  finom_status rc = plan_at(s, r, e0, s->prec, &r->plan);
+  if (rc == FINOM_OK)
+    rc = finom_solve_begin(r->plan, d[r->kind == 1 ? 2 : 4], d[r->kind == 1 ? 3 : 5], tol0, r->maxit, nullptr,
+                           nullptr, st);
   if (rc != FINOM_OK) return rc;
   FINOM_CUDA(cudaEventRecord(r->ev, st));
   return FINOM_OK;
@@ -170,13 +183,28 @@ finom_status finish(finom_server_s* s, Req* r, bool* more) {
   finom_status rc = finom_solve_end(r->plan, f, g, &r->res, st);
   if (rc != FINOM_OK) return rc;
   r->res.iters += r->iters_before;
+  if (r->stages_left > 0) {
+    // eps scaling: the next stage (or the request's own eps) on a plan of its
+    // own, warm-started from this stage's potentials
+    --r->stages_left;
+    const double e = r->eps / std::pow(s->sc_factor, r->stages_left);
+    const double tol = r->stages_left > 0 ? std::max(r->tol, s->sc_tol) : r->tol;
+    s->graveyard.push_back(r->plan);   // an extra plan alive until the next flush
+    s->used += r->footprint;
+    s->dead_bytes += r->footprint;
+    r->plan = nullptr;
+    rc = plan_at(s, r, e, s->prec, &r->plan);
+    if (rc != FINOM_OK) return rc;
+    rc = finom_solve_begin(r->plan, u, v, tol, std::max<int64_t>(r->maxit - r->res.iters, 0), f, g, st);
+    if (rc != FINOM_OK) return rc;
+    r->iters_before = r->res.iters;
+    r->step = 1;
+    FINOM_CUDA(cudaEventRecord(r->ev, st));
+    *more = true;
+    return FINOM_OK;
+  }
   if (!r->res.converged && r->res.iters < r->maxit && !r->plan64 && s->prec != FINOM_F64) {
-    const double* d = r->dev;
-    if (r->kind == 1)
-      rc = finom_plan(d, r->N, d + r->N, r->M, r->eps, FINOM_F64, st, &r->plan64);
-    else
-      rc = finom_plan_2d(d, d + r->N, r->N, d + 2 * r->N, d + 2 * r->N + r->M, r->M, r->eps, FINOM_F64, st,
-                         &r->plan64);
+    rc = plan_at(s, r, r->eps, FINOM_F64, &r->plan64);
     if (rc != FINOM_OK) return rc;
     rc = finom_solve_begin(r->plan64, u, v, r->tol, r->maxit - r->res.iters, f, g, st);
     if (rc != FINOM_OK) return rc;
@@ -234,6 +262,17 @@ finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, f
     s->free_slots.push_back(max_active - 1 - k);
   }
   *out = s;
+  return FINOM_OK;
+}
+
+finom_status finom_server_set_eps_scaling(finom_server_t s, int32_t stages, double factor, double tol_stage) {
+  if (!s || stages < 0 || stages > 30 || !(factor > 0.0 && factor < 1.0) || !(tol_stage > 0.0)) {
+    finom::set_error("finom_server_set_eps_scaling: need 0 <= stages <= 30, 0 < factor < 1, tol_stage > 0");
+    return FINOM_EINVAL;
+  }
+  s->sc_stages = stages;
+  s->sc_factor = factor;
+  s->sc_tol = tol_stage;
   return FINOM_OK;
 }
 

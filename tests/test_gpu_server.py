@@ -183,3 +183,35 @@ def test_cancel_queued_and_active(lib):
     assert out[a][0]["status"] == lib.FINOM_ECANCELED
     assert out[b][0]["status"] == lib.FINOM_ECANCELED
     assert out[c][0]["status"] == 0 and out[c][0]["converged"] == 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_eps_scaling_in_the_server(lib, prec):
+    """With eps scaling on, served solves reach the same fixed point (the
+    oracle's float64 error of the returned potentials within tol, W1 equal to
+    the plain served W1) and results stay the same alone and in the mix."""
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.config2(1 << 12)
+    reqs = [("1d", (pr.x, pr.y, pr.u, pr.v), pr.eps, 1e-6, 50000)] + _requests()[:2] + _requests()[5:6]
+    plain = lib.Server(1 << 32, max_active=4, precision=prec)
+    ids = [_submit(plain, r) for r in reqs]
+    base = plain.run(ids)
+    plain.close()
+    mixed = lib.Server(1 << 32, max_active=4, precision=prec)
+    mixed.set_eps_scaling(3, 0.5, 1e-4)
+    ids2 = [_submit(mixed, r) for r in reqs]
+    got = mixed.run(ids2)
+    mixed.close()
+    for r, i0, i1 in zip(reqs, ids, ids2):
+        d0, d1 = base[i0][0], got[i1][0]
+        assert d1["status"] == 0 and d1["converged"] == 1, (r[0], d1)
+        assert d1["w1"] == pytest.approx(d0["w1"], rel=1e-6 if prec == "f64" else 1e-4)
+        assert _oracle_err(r, got[i1][1], got[i1][2]) <= r[3] * (1 + 1e-6) + 1e-15
+    # graded mesh at eps = 1e-3: fewer iterations in total with the stages
+    assert got[ids2[0]][0]["iters"] < base[ids[0]][0]["iters"]
+    alone = lib.Server(1 << 32, max_active=1, precision=prec)
+    alone.set_eps_scaling(3, 0.5, 1e-4)
+    rid = _submit(alone, reqs[0])
+    a = alone.run([rid])[rid]
+    alone.close()
+    assert np.array_equal(a[1], got[ids2[0]][1]) and a[0]["iters"] == got[ids2[0]][0]["iters"]
