@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
-    ap.add_argument("--n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
+    ap.add_argument("--n", "--mesh-points", dest="n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", choices=["1d", "2d", "batch", "serve"], default="1d")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
@@ -159,21 +159,26 @@ class ClockSampler:
 
 
 def dist_init():
+    """One process per GPU under torchrun: NCCL on GPUs; gloo where no GPU is
+    visible (the host-side logic of the multi-rank path, tested on CPU)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return ws, rank, local
 
 
 def max_over_ranks(v, ws):
+    """The maximum of v over the ranks (every rank gets it)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
