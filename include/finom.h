@@ -391,6 +391,23 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
                          void* stream);
 
 /*
+ * finom_solve_trace -- the marginal error against time (the measurement
+ * behind the time-to-error curves of Sec. 4): runs the loop of finom_solve
+ * without a stopping tolerance for maxit iterations, started from
+ * phi = 1/N, psi = 1/M, and after every `every` iterations records, without
+ * synchronising, the loop-head error || diag(psi) K^T phi - v ||_1 (plan
+ * precision) and a CUDA event.
+ *   err, ms: HOST arrays of ceil(maxit / every) doubles; entry i holds the
+ *            error at the head of iteration min((i + 1) * every, maxit - 1)
+ *            and the GPU time in ms since iteration 0 was launched.
+ *   *n:      number of entries written.
+ * The solve state is left ended (use finom_solve for potentials).  1D and
+ * 2D plans; synchronous.
+ */
+finom_status finom_solve_trace(finom_plan_t plan, const double* u, const double* v, int64_t maxit, int64_t every,
+                               double* err, double* ms, int64_t* n, void* stream);
+
+/*
  * finom_solve_eps_scaling -- finom_solve preceded by solves of the same
  * problem at eps0, eps0 * factor, eps0 * factor^2, ... (while above the
  * plan's eps), each to tol_stage on a plan of its own and warm-started from

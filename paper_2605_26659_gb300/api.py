@@ -75,6 +75,7 @@ _SIGS = {
     "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
     "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
     "finom_solve_batch_end": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "finom_solve_trace": ([_P, _P, _P, _I64, _I64, _P, _P, ctypes.POINTER(_I64), _P], ctypes.c_int),
     "finom_solve_eps_scaling": ([_P, _P, _P, _D, _I64, _D, _D, _D, _P, _P, ctypes.POINTER(FinomResult), _P],
                                 ctypes.c_int),
     "finom_transport_row": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
@@ -266,6 +267,23 @@ def finom_solve_batch_end(plan: Plan, f=None, g=None, stream=None):
     _check(_lib.finom_solve_batch_end(plan.handle, _dev(f, plan.N), _dev(g, plan.M),
                                       ctypes.cast(res, ctypes.c_void_p), _stream(stream)))
     return f, g, [r.as_dict() for r in res]
+
+
+def finom_solve_trace(plan: Plan, u, v, maxit, every=10, stream=None):
+    """Loop-head marginal error against GPU time: returns (iterations, err, ms)
+    as numpy arrays, one entry per `every` iterations."""
+    import numpy as np
+    import torch
+    K = (int(maxit) + int(every) - 1) // int(every)
+    err = np.zeros(K)
+    ms = np.zeros(K)
+    n = _I64()
+    _check(_lib.finom_solve_trace(plan.handle, _dev(u, plan.N, torch.float64, "u"), _dev(v, plan.M, torch.float64, "v"),
+                                  int(maxit), int(every), err.ctypes.data, ms.ctypes.data, ctypes.byref(n),
+                                  _stream(stream)))
+    k = n.value
+    its = np.minimum((np.arange(k) + 1) * int(every), int(maxit) - 1)
+    return its, err[:k], ms[:k]
 
 
 def finom_solve_eps_scaling(plan: Plan, u, v, tol, maxit, eps0, factor=0.5, tol_stage=1e-4, stream=None):

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -780,6 +781,57 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
                         ? solve_blocking<float>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream)
                         : solve_blocking<double>(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
   if (res && rc != FINOM_OK) res->status = rc;
+  return rc;
+}
+
+finom_status finom_solve_trace(finom_plan_t plan, const double* u, const double* v, int64_t maxit, int64_t every,
+                               double* err, double* ms, int64_t* n, void* stream) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (batch_plan(plan, "finom_solve_trace")) return FINOM_ENOTSUP;
+  if (!u || !v || !err || !ms || !n || maxit < 1 || every < 1) {
+    set_error("finom_solve_trace: need u, v, err, ms, n non-null, maxit >= 1, every >= 1");
+    return FINOM_EINVAL;
+  }
+  DeviceGuard dg(plan->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t K = (maxit + every - 1) / every;
+  double* dtrace = nullptr;
+  FINOM_CUDA(cudaMallocAsync(&dtrace, sizeof(double) * K, s));
+  std::vector<cudaEvent_t> ev(K + 1, nullptr);
+  finom_status rc = FINOM_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  // the loop without a stopping tolerance: the loop-head error of every
+  // iteration is the one the kernels leave in the plan's control block
+  if (rc == FINOM_OK) rc = finom_solve_begin(plan, u, v, 0.0, maxit, nullptr, nullptr, stream);
+  if (rc == FINOM_OK) cudaEventRecord(ev[0], s);
+  int64_t k = 0, done = 1;   // iterations launched (begin launched iteration 0)
+  for (; rc == FINOM_OK && k < K; ++k) {
+    const int64_t chunk = std::min(every, maxit - done);
+    if (chunk > 0) rc = finom_solve_step(plan, chunk, stream);
+    done += std::max<int64_t>(chunk, 0);
+    if (rc != FINOM_OK) break;
+    if (cudaMemcpyAsync(dtrace + k, plan->st.scal, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "trace copy");
+    cudaEventRecord(ev[k + 1], s);
+  }
+  if (rc == FINOM_OK) {
+    std::vector<double> h(k);
+    if (k > 0 && cudaMemcpyAsync(h.data(), dtrace, sizeof(double) * k, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "trace read");
+    if (rc == FINOM_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "trace sync");
+    for (int64_t i = 0; rc == FINOM_OK && i < k; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[0], ev[i + 1]);
+      err[i] = h[i];
+      ms[i] = t;
+    }
+    *n = k;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaFreeAsync(dtrace, s);
+  plan->st.active = false;
   return rc;
 }
 

@@ -52,3 +52,19 @@ def test_eps_scaling_argument_errors(lib):
         with pytest.raises(lib.FinomError) as e:
             lib.finom_solve_eps_scaling(p, T(pr.u), T(pr.v), 1e-6, 1000, **args)
         assert e.value.status == lib.FINOM_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_time_to_error_trace(lib, prec):
+    """The traced loop-head errors are the oracle's at the same iterations (to
+    the precision of the loop's own check: its S - 1 uses a truncated series
+    near S = 1, ~1e-9 relative in float64), and the GPU times increase."""
+    from paper_2605_26659_gb300 import inputs
+    pr = inputs.chebyshev(2000)
+    p = lib.finom_plan(T(pr.x), T(pr.y), pr.eps, prec)
+    its, err, ms = lib.finom_solve_trace(p, T(pr.u), T(pr.v), 200, every=25)
+    assert list(its) == [25, 50, 75, 100, 125, 150, 175, 199]
+    assert np.all(np.diff(ms) > 0)
+    for l, e in zip(its, err):
+        _, _, it, eo = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, int(l))
+        assert e == pytest.approx(eo, rel=1e-7 if prec == "f64" else 2e-3, abs=1e-13 if prec == "f64" else 2e-6)
