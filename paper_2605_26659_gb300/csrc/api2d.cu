@@ -139,7 +139,8 @@ finom_status run_pass(ApplyArgs<R> a, cudaStream_t s) {
 }
 
 // K'^T phi, first pass: rows k of grid 1 along y (W = y1 with phi, O = y2),
-// log2 Q'(k, j) written column-major (k + N j)
+// log2 Q'(k, j) written along the line (k M + j): contiguous stores; the
+// second pass reads it across lines
 template <class R>
 ApplyArgs<R> pass_t1(finom_plan_s* p, int q) {
   SolveState& st = p->st;
@@ -149,8 +150,8 @@ ApplyArgs<R> pass_t1(finom_plan_s* p, int q) {
   a.mW = (const MassT<R>*)st.mu;
   a.w_ls = M;
   a.q_out = (PotT<R>*)st.q2;
-  a.q_ls = 1;
-  a.q_es = N;
+  a.q_ls = M;
+  a.q_es = 1;
   a.flags = kMode2Inner;
   return a;
 }
@@ -167,13 +168,14 @@ ApplyArgs<R> pass_t2(finom_plan_s* p, int q) {
   a.o_ls = N;
   a.pO_out = (PotT<R>*)st.py[1 - q];
   a.pW = (const PotT<R>*)st.q2;
-  a.w_ls = N;
+  a.w_ls = 1;
+  a.w_es = M;
   a.flags = kMode2HalfB;
   return a;
 }
 
 // K' psi, first pass: columns j of grid 2 along x (W = x2 with psi, O = x1),
-// log2 Q(k, j) written row-major (j + M k)
+// log2 Q(k, j) written along the line (j N + k)
 template <class R>
 ApplyArgs<R> pass_a1(finom_plan_s* p, int q) {
   SolveState& st = p->st;
@@ -183,8 +185,8 @@ ApplyArgs<R> pass_a1(finom_plan_s* p, int q) {
   a.mW = (const MassT<R>*)st.nu;
   a.w_ls = N;
   a.q_out = (PotT<R>*)st.q2;
-  a.q_ls = 1;
-  a.q_es = M;
+  a.q_ls = N;
+  a.q_es = 1;
   a.flags = kMode2Inner;
   return a;
 }
@@ -201,7 +203,8 @@ ApplyArgs<R> pass_a2(finom_plan_s* p, int q) {
   a.o_ls = M;
   a.pO_out = (PotT<R>*)st.px[1 - q];
   a.pW = (const PotT<R>*)st.q2;
-  a.w_ls = M;
+  a.w_ls = 1;
+  a.w_es = N;
   a.flags = kMode2HalfA;
   return a;
 }

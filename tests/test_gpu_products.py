@@ -156,3 +156,25 @@ def test_invalid_inputs_are_rejected(lib):
         lib.finom_plan(T([0.1, float("nan")]), y, 0.1, "f64")
     with pytest.raises(lib.FinomError):
         lib.finom_plan(T([0.1, 0.2]), y, 0.0, "f64")
+
+
+def test_large_graded_mesh_sampled_rows(lib):
+    """N = M = 2^27 graded meshes (268 M merged points, 131,072 tiles: the
+    block-wide launch tail with many chunks, 64-bit offsets): sampled rows of
+    K v and K^T u (float32 log-domain plan) against exact dense row sums."""
+    import torch
+    from paper_2605_26659_gb300 import inputs
+    if torch.cuda.get_device_properties(0).total_memory < (120 << 30):
+        pytest.skip("needs a GPU with > 120 GB")
+    prob = inputs.config2(1 << 27)
+    p = lib.finom_plan(T(prob.x), T(prob.y), prob.eps, "f32_log")
+    assert lib.finom_plan_elems(p) == (8, (1 << 28) // 2048)
+    kv = H(lib.finom_kv(p, T(prob.v)))
+    ktu = H(lib.finom_ktu(p, T(prob.u)))
+    del p
+    g = np.random.default_rng(27)
+    rows = np.concatenate([[0, len(prob.x) - 1], g.integers(0, len(prob.x), 6)])
+    want = np.array([np.dot(np.exp(-np.abs(prob.x[i] - prob.y) / prob.eps), prob.v) for i in rows])
+    want_t = np.array([np.dot(np.exp(-np.abs(prob.y[j] - prob.x) / prob.eps), prob.u) for j in rows])
+    assert relerr(kv[rows], want, floor=1e-30) <= TOL["f32_log"]
+    assert relerr(ktu[rows], want_t, floor=1e-30) <= TOL["f32_log"]
