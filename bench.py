@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrent solves (streams)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
+    ap.add_argument("--rates", type=str, default="",
+                    help="serve: extra arrival rates (req/s, comma-separated) for a latency-vs-load sweep")
     ap.add_argument("--eps-stages", type=int, default=0,
                     help="serve: eps-scaling stages of the second run (0: no second run)")
     ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
@@ -616,6 +618,18 @@ def run_finom_serve(args, ws, rank, local):
     que = np.array([r["queue_s"] for r in res])
     nconv = sum(r["converged"] for r in res)
     pts = sum(_request_points(q) * r["iters"] for q, r in zip(probs, res))
+    # latency against load: the same kinds of requests at other arrival rates
+    sweep = None
+    if args.rates:
+        sweep = {}
+        for rate in [float(r) for r in args.rates.split(",") if r]:
+            rq = inputs.serving_requests(rate=rate, duration=2.0 * args.requests / rate + 1.0)[:args.requests]
+            pb = [inputs.request_problem(r) for r in rq]
+            w, rs, pk = _serve_once(api, args, rq, pb, 0)
+            lt = np.array([r["latency_s"] for r in rs])
+            sweep[str(rate)] = {"solves_per_s": len(pb) / w, "p50_s": float(np.percentile(lt, 50)),
+                                "p99_s": float(np.percentile(lt, 99)), "arrival_span_s": rq[-1].t_arrival,
+                                "peak_active": pk, "converged": int(sum(r["converged"] for r in rs))}
     # the same arrivals with eps scaling in the server (same fixed points)
     scaled = None
     if args.eps_stages > 0:
@@ -685,6 +699,7 @@ def run_finom_serve(args, ws, rank, local):
                                          "seconds_per_solve": plain_per_solve,
                                          "w1_max_relerr_served_vs_plain": max(w1_dev) if w1_dev else None},
             "eps_scaling": scaled,
+            "rate_sweep": sweep,
             "cpu_baseline": None,
         }
         print(json.dumps(line), flush=True)
