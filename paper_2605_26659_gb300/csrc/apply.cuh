@@ -816,6 +816,8 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   constexpr bool kBatch = (kFlags & F_BATCH) != 0;
   // the launches of 1D plans: one line, unit strides, no offsets
   constexpr bool kUnit = (kFlags & (F_FRAME_W | F_WVALID | F_QOUT | F_BATCH)) == 0;
+  // batches: unit strides, an offset per instance
+  constexpr bool kStride1 = (kFlags & (F_FRAME_W | F_WVALID | F_QOUT)) == 0;
   const int tid = threadIdx.x;
   const int C = a.C;
   // geometry of the unit: its line (or instance), tile, sequence length, the
@@ -881,7 +883,9 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   // loop control come after the wait.
   if (!kFrameW) {
     for (int i = tid; i < n_o + 1; i += kThreads) {
-      const int64_t gi = kUnit ? (int64_t)max(o_start - 1 + i, 0) : ob + (int64_t)max(o_start - 1 + i, 0) * a.o_es;
+      const int64_t gi = kUnit      ? (int64_t)max(o_start - 1 + i, 0)
+                         : kStride1 ? ob + max(o_start - 1 + i, 0)
+                                    : ob + (int64_t)max(o_start - 1 + i, 0) * a.o_es;
       cp_async(&sm.pot[i], &a.pO[gi]);
       cp_async(&sm.mass[i], &a.mO[gi]);
     }
@@ -899,7 +903,9 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   }
   if (w_uniform <= R(0) || (kFlags & F_NEXT)) {
     for (int i = tid; i < n_w + 1; i += kThreads) {
-      const int64_t gi = kUnit ? (int64_t)max(w_start - 1 + i, 0) : wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
+      const int64_t gi = kUnit      ? (int64_t)max(w_start - 1 + i, 0)
+                         : kStride1 ? wb + max(w_start - 1 + i, 0)
+                                    : wb + (int64_t)max(w_start - 1 + i, 0) * a.w_es;
       cp_async(&sm.pot[wofs + i], &a.pW[gi]);
       if (!kWValid) cp_async(&sm.mass[wofs + i], &a.mW[gi]);
     }
@@ -1033,6 +1039,8 @@ __device__ __forceinline__ bool apply_unit(const ApplyArgs<R>& a, TileSmem<R>& s
   if constexpr ((kFlags & F_OUT_POT) != 0) {
     if constexpr (kUnit) {
       for (int i = tid; i < n_o; i += kThreads) a.pO_out[o_start + i] = sm.pot[1 + i];
+    } else if constexpr (kStride1) {
+      for (int i = tid; i < n_o; i += kThreads) a.pO_out[ob + o_start + i] = sm.pot[1 + i];
     } else {
       for (int i = tid; i < n_o; i += kThreads) a.pO_out[ob + (int64_t)(o_start + i) * a.o_es] = sm.pot[1 + i];
     }
