@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrent solves (streams)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
+    ap.add_argument("--policy", choices=["fifo", "smallest"], default="smallest",
+                    help="serve: admission order of queued requests")
     ap.add_argument("--rates", type=str, default="",
                     help="serve: extra arrival rates (req/s, comma-separated) for a latency-vs-load sweep")
     ap.add_argument("--eps-stages", type=int, default=0,
@@ -562,6 +564,7 @@ def _serve_once(api, args, reqs, probs, stages):
     until every request has finished; returns (wall seconds, results in
     request order, peak active solves)."""
     srv = api.Server(int(args.budget_gb * 2**30), max_active=args.slots, precision="f32_log")
+    srv.set_policy(args.policy)
     if stages:
         srv.set_eps_scaling(stages, 0.5, 1e-4)
     t0 = time.perf_counter()
@@ -681,6 +684,7 @@ def run_finom_serve(args, ws, rank, local):
                                    f"axes), eps in {{1e-3, 5e-3, 1e-2}}, tol 1e-6, maxit 10000, FP32 "
                                    f"log-domain with float64 verification; one step = one request",
                        "slots": args.slots, "budget_gb": args.budget_gb, "peak_active": peak_active,
+                       "policy": args.policy,
                        "l2": "inputs and potentials of the active solves exceed L2",
                        "parallelism": f"replicas x{ws}"},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

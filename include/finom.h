@@ -236,7 +236,8 @@ finom_status finom_solve_batch_end(finom_plan_t plan, double* f, double* g, fino
  * A server owns max_active CUDA streams (slots).  finom_server_submit_* copy a
  * request's HOST arrays and queue it.  finom_server_step runs one scheduling
  * round, without waiting for the GPU:
- *   - admission, first come first served: the queue head is admitted while a
+ *   - admission (first come first served by default; see
+ *     finom_server_set_policy): the queue head is admitted while a
  *     slot is free and the estimated device footprint of the active solves
  *     plus its own stays within mem_budget_bytes (a request larger than the
  *     budget is admitted alone); admission copies its inputs to the device,
@@ -271,6 +272,16 @@ typedef struct {
  */
 finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, finom_precision prec,
                                  finom_server_t* out);
+
+/*
+ * finom_server_set_policy -- admission order of queued requests:
+ * FINOM_SERVE_FIFO (default; arrival order) or FINOM_SERVE_SMALLEST_FIRST
+ * (the queued request with the smallest estimated footprint first, which
+ * keeps short solves from waiting behind long ones; a large request can wait
+ * as long as smaller ones keep arriving).
+ */
+enum { FINOM_SERVE_FIFO = 0, FINOM_SERVE_SMALLEST_FIRST = 1 };
+finom_status finom_server_set_policy(finom_server_t srv, int32_t policy);
 
 /*
  * finom_server_set_eps_scaling -- requests admitted from now on first solve

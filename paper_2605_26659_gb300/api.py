@@ -94,6 +94,7 @@ _SIGS = {
     "finom_server_result": ([_P, _I64, ctypes.POINTER(FinomServerDone), _P, _P], ctypes.c_int),
     "finom_server_cancel": ([_P, _I64], ctypes.c_int),
     "finom_server_set_eps_scaling": ([_P, _I32, _D, _D], ctypes.c_int),
+    "finom_server_set_policy": ([_P, _I32], ctypes.c_int),
     "finom_server_destroy": ([_P], ctypes.c_int),
 }
 
@@ -560,6 +561,10 @@ class Server:
             f = f.reshape(shp[2], order="F")
             g = g.reshape(shp[2], order="F")
         return out, f, g
+
+    def set_policy(self, policy):
+        """'fifo' (arrival order) or 'smallest' (smallest queued request first)."""
+        _check(_lib.finom_server_set_policy(self.handle, {"fifo": 0, "smallest": 1}[policy]))
 
     def set_eps_scaling(self, stages, factor=0.5, tol_stage=1e-4):
         _check(_lib.finom_server_set_eps_scaling(self.handle, int(stages), float(factor), float(tol_stage)))

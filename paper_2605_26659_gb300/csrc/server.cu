@@ -1,7 +1,7 @@
 // Serving loop: continuous batching of 1D and 2D solves of mixed sizes.
 //
 // Requests are queued on the host; a scheduling round (finom_server_step)
-// admits queued requests first come first served while their estimated
+// admits queued requests (first come first served, or smallest first) while their estimated
 // device footprint fits the memory budget and a stream slot is free, builds
 // their plans and starts their solves on their own stream; for every active
 // solve whose previous launches have completed it either launches more
@@ -55,6 +55,7 @@ struct finom_server_s {
   // k = stages .. 1, each to tol_stage, before the request's own eps
   int sc_stages = 0;
   double sc_factor = 0.5, sc_tol = 1e-4;
+  int policy = FINOM_SERVE_FIFO;        // admission order
   finom_precision prec = FINOM_F32_LOG;
   int device = 0;
   int64_t next_id = 1;
@@ -265,6 +266,15 @@ finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, f
   return FINOM_OK;
 }
 
+finom_status finom_server_set_policy(finom_server_t s, int32_t policy) {
+  if (!s || (policy != FINOM_SERVE_FIFO && policy != FINOM_SERVE_SMALLEST_FIRST)) {
+    finom::set_error("finom_server_set_policy: need a server and FINOM_SERVE_FIFO or FINOM_SERVE_SMALLEST_FIRST");
+    return FINOM_EINVAL;
+  }
+  s->policy = policy;
+  return FINOM_OK;
+}
+
 finom_status finom_server_set_eps_scaling(finom_server_t s, int32_t stages, double factor, double tol_stage) {
   if (!s || stages < 0 || stages > 30 || !(factor > 0.0 && factor < 1.0) || !(tol_stage > 0.0)) {
     finom::set_error("finom_server_set_eps_scaling: need 0 <= stages <= 30, 0 < factor < 1, tol_stage > 0");
@@ -333,10 +343,15 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   if (prev != s->device) cudaSetDevice(s->device);
   // admissions, first come first served: an empty server always admits
   while (!s->pending.empty() && !s->free_slots.empty()) {
-    Req* r = s->pending.front();
+    // the next request: the queue head, or the smallest queued one
+    auto pick = s->pending.begin();
+    if (s->policy == FINOM_SERVE_SMALLEST_FIRST)
+      for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+        if ((*it)->footprint < (*pick)->footprint) pick = it;
+    Req* r = *pick;
     if (s->used + r->footprint > s->budget && !s->graveyard.empty()) flush_graveyard(s);
     if (!s->active.empty() && s->used + r->footprint > s->budget) break;
-    s->pending.pop_front();
+    s->pending.erase(pick);
     finom_status rc = admit(s, r);
     if (rc != FINOM_OK) fail(s, r, rc);
     else s->active.push_back(r);

@@ -215,3 +215,26 @@ def test_eps_scaling_in_the_server(lib, prec):
     a = alone.run([rid])[rid]
     alone.close()
     assert np.array_equal(a[1], got[ids2[0]][1]) and a[0]["iters"] == got[ids2[0]][0]["iters"]
+
+
+def test_smallest_first_admission(lib):
+    """One solve at a time: smallest first admits the queued requests by size,
+    first come first served by arrival; results are the same either way."""
+    reqs = [_requests()[k] for k in (1, 0, 3)]      # 8100, 557, 4096 merged points
+    out = {}
+    for policy in ("fifo", "smallest"):
+        srv = lib.Server(1, max_active=1, precision="f32_log")
+        srv.set_policy(policy)
+        ids = [_submit(srv, r) for r in reqs]
+        res = srv.run(ids)
+        out[policy] = [res[i] for i in ids]
+        srv.close()
+    q = {p: [d[0]["queue_s"] for d in out[p]] for p in out}
+    assert q["fifo"][0] < q["fifo"][1] < q["fifo"][2]
+    assert q["smallest"][1] < q["smallest"][2] < q["smallest"][0]
+    for a, b in zip(out["fifo"], out["smallest"]):
+        assert np.array_equal(a[1], b[1]) and a[0]["iters"] == b[0]["iters"]
+    srv = lib.Server(1, max_active=1)
+    rc = lib._lib.finom_server_set_policy(srv.handle, 7)
+    assert rc == lib.FINOM_EINVAL
+    srv.close()
