@@ -129,7 +129,8 @@ finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64
  *      every instance with N_b >= 1 and M_b >= 1.
  *   eps: B doubles (HOST array), each > 0 and finite.
  *   1 <= B <= 2^24; the padded merged length (each instance rounded up to
- *   2048 points) and each of sum N_b, sum M_b must stay below 2^31.
+ *   whole tiles of 2048 points, or 256 * elems with finom_plan_batch_elems)
+ *   and each of sum N_b, sum M_b must stay below 2^31.
  * Only finom_solve_batch, finom_plan_info / finom_plan_shape (totals),
  * finom_plan_instances and finom_plan_destroy take a batch plan; the other
  * calls return FINOM_ENOTSUP.  Synchronous.  Errors as finom_plan.
@@ -189,6 +190,21 @@ finom_status finom_tune_set(finom_precision prec, int32_t log2_bucket, int32_t e
 finom_status finom_tune_get(finom_precision prec, int32_t log2_bucket, int32_t* elems);
 finom_status finom_autotune(finom_precision prec, int32_t log2_bucket, int32_t iters, int32_t* best,
                             double* us_per_iter, void* stream);
+
+/*
+ * finom_plan_batch_elems -- finom_plan_batch with the kernel's points per
+ * thread chosen: each instance is packed into tiles of 256 * elems points
+ * (elems in {1, 2, 4, 8}; 0 takes the process-wide batch entry of the tuning
+ * table, 8 unless finom_tune_set_batch changed it).  Smaller tiles waste less
+ * padding on small instances; results agree to rounding across elems.
+ * finom_tune_set_batch / finom_tune_get_batch set and read that entry
+ * (paper_2605_26659_gb300/autotune.py times the candidates on a batch).
+ */
+finom_status finom_plan_batch_elems(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
+                                    int64_t B, const double* eps, finom_precision prec, int32_t elems,
+                                    void* stream, finom_plan_t* out);
+finom_status finom_tune_set_batch(finom_precision prec, int32_t elems);
+finom_status finom_tune_get_batch(finom_precision prec, int32_t* elems);
 
 /* Number of instances of a batch plan (0 for other plans). */
 finom_status finom_plan_instances(finom_plan_t plan, int64_t* B);

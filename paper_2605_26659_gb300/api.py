@@ -71,6 +71,10 @@ _SIGS = {
     "finom_plan_shape": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
     "finom_plan_batch": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_plan_instances": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_plan_batch_elems": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _I32, _P, ctypes.POINTER(_P)],
+                               ctypes.c_int),
+    "finom_tune_set_batch": ([ctypes.c_int, _I32], ctypes.c_int),
+    "finom_tune_get_batch": ([ctypes.c_int, ctypes.POINTER(_I32)], ctypes.c_int),
     "finom_solve_batch": ([_P, _P, _P, _D, _I64, _P, _P, _P, _P], ctypes.c_int),
     "finom_solve_batch_begin": ([_P, _P, _P, _D, _I64, _P], ctypes.c_int),
     "finom_solve_batch_step": ([_P, _I64, _P], ctypes.c_int),
@@ -205,9 +209,10 @@ def finom_plan_shape(plan: Plan):
     return d.value, n.value, m.value
 
 
-def finom_plan_batch(x, offx, y, offy, eps, precision="f32_log", stream=None) -> Plan:
+def finom_plan_batch(x, offx, y, offy, eps, precision="f32_log", stream=None, elems=0) -> Plan:
     """Batch of independent 1D problems: x, y concatenated (device float64),
-    offx, offy: B + 1 offsets (host sequences), eps: B values (host)."""
+    offx, offy: B + 1 offsets (host sequences), eps: B values (host); elems:
+    points per thread of the packing (0: the tuning table's batch entry)."""
     import numpy as np
     import torch
     load()
@@ -218,9 +223,10 @@ def finom_plan_batch(x, offx, y, offy, eps, precision="f32_log", stream=None) ->
     if len(ox) != B + 1 or len(oy) != B + 1:
         raise ValueError("offx and offy need B + 1 entries")
     h = ctypes.c_void_p()
-    _check(_lib.finom_plan_batch(_dev(x, int(ox[-1]), torch.float64, "x"), ox.ctypes.data,
-                                 _dev(y, int(oy[-1]), torch.float64, "y"), oy.ctypes.data, B, ep.ctypes.data,
-                                 _PREC[precision], _stream(stream), ctypes.byref(h)))
+    _check(_lib.finom_plan_batch_elems(_dev(x, int(ox[-1]), torch.float64, "x"), ox.ctypes.data,
+                                       _dev(y, int(oy[-1]), torch.float64, "y"), oy.ctypes.data, B,
+                                       ep.ctypes.data, _PREC[precision], int(elems), _stream(stream),
+                                       ctypes.byref(h)))
     return Plan(h, int(ox[-1]), int(oy[-1]), float(ep[0]), _PREC[precision], x.device.index or 0, batch=B)
 
 
@@ -351,6 +357,18 @@ def finom_tune_get(precision, log2_bucket):
     load()
     e = _I32()
     _check(_lib.finom_tune_get(_PREC[precision], int(log2_bucket), ctypes.byref(e)))
+    return e.value
+
+
+def finom_tune_set_batch(precision, elems):
+    load()
+    _check(_lib.finom_tune_set_batch(_PREC[precision], int(elems)))
+
+
+def finom_tune_get_batch(precision):
+    load()
+    e = _I32()
+    _check(_lib.finom_tune_get_batch(_PREC[precision], ctypes.byref(e)))
     return e.value
 
 

@@ -592,11 +592,22 @@ finom_status finom_plan_destroy(finom_plan_t plan) {
 finom_status finom_plan_batch(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
                               int64_t B, const double* eps, finom_precision prec, void* stream,
                               finom_plan_t* out) {
+  return finom_plan_batch_elems(x, offx, y, offy, B, eps, prec, 0, stream, out);
+}
+
+finom_status finom_plan_batch_elems(const double* x, const int64_t* offx, const double* y, const int64_t* offy,
+                                    int64_t B, const double* eps, finom_precision prec, int32_t elems,
+                                    void* stream, finom_plan_t* out) {
   if (!out) {
     set_error("finom_plan_batch: out is NULL");
     return FINOM_EINVAL;
   }
   *out = nullptr;
+  if (elems == 0) elems = tune_pick_batch(prec);
+  if (elems != 1 && elems != 2 && elems != 4 && elems != kElems) {
+    set_error("finom_plan_batch: points per thread must be 1, 2, 4 or 8");
+    return FINOM_EINVAL;
+  }
   if (!x || !y || !offx || !offy || !eps || B < 1 || B > (int64_t)1 << 24 ||
       (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
     set_error("finom_plan_batch: need x, y, offx, offy, eps non-null, 1 <= B <= 2^24, known precision");
@@ -622,6 +633,8 @@ finom_status finom_plan_batch(const double* x, const int64_t* offx, const double
   }
   finom_plan_s* p = new (std::nothrow) finom_plan_s();
   if (!p) return FINOM_ENOMEM;
+  p->btile = (int64_t)elems * kThreads;
+  p->elems = elems;
   p->eps = eps[0];
   p->prec = prec;
   cudaGetDevice(&p->device);

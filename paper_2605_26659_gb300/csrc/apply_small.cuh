@@ -1,6 +1,6 @@
 // Instantiations of the fused half-step kernel with smaller tiles (1, 2 or
-// 4 points per thread) for the launch modes of 1D plans: products, the
-// half steps of the loop, the loop-head check and the tile-map pass.
+// 4 points per thread) for the launch modes of 1D plans (products, the half
+// steps of the loop, the loop-head check, the tile-map pass) and of batches.
 #include "apply_launch.cuh"
 
 namespace finom {
@@ -15,6 +15,10 @@ static bool launch_e(cudaLaunchConfig_t& cfg, const ApplyArgs<R>& a, int mode, i
     case kModeCheck: *e = launch_mode<R, kModeCheck, E>(cfg, a, units, smem); return true;
     case kModeLin: *e = launch_mode<R, kModeLin, E>(cfg, a, units, smem); return true;
     case kModeLog: *e = launch_mode<R, kModeLog, E>(cfg, a, units, smem); return true;
+    case kModeBHalfY: *e = launch_mode<R, kModeBHalfY, E>(cfg, a, units, smem); return true;
+    case kModeBHalfX: *e = launch_mode<R, kModeBHalfX, E>(cfg, a, units, smem); return true;
+    case kModeBAgg: *e = launch_mode<R, kModeBAgg, E>(cfg, a, units, smem); return true;
+    case kModeBCheck: *e = launch_mode<R, kModeBCheck, E>(cfg, a, units, smem); return true;
     default: return false;
   }
 }

@@ -66,15 +66,15 @@ __global__ void k_bcheck(const double* a, const int64_t* off, int B, int64_t n, 
 // merged position of each point inside its instance (ties: y before x), and
 // the scatter of coordinates and types into the packed merged arrays
 __global__ void k_bpos(const double* a, int64_t n, const int64_t* offa, const double* o, const int64_t* offo,
-                       const int32_t* itile, int B, int strict, int64_t* pos, double* z, uint8_t* type,
-                       uint8_t t) {
+                       const int32_t* itile, int B, int64_t tile, int strict, int64_t* pos, double* z,
+                       uint8_t* type, uint8_t t) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = find_inst(offa, B, i);
   const double v = a[i];
   const int64_t loc = (i - offa[b]) + bcount(o + offo[b], offo[b + 1] - offo[b], v, strict != 0);
   pos[i] = loc;
-  const int64_t k = (int64_t)itile[b] * kTile + loc;
+  const int64_t k = (int64_t)itile[b] * tile + loc;
   z[k] = v;
   type[k] = t;
 }
@@ -82,15 +82,15 @@ __global__ void k_bpos(const double* a, int64_t n, const int64_t* offa, const do
 // gaps in bits (each instance's eps) and packed type bits; one thread per
 // packed position (the packed length is a whole number of tiles)
 __global__ void k_bgaps(const double* z, const uint8_t* type, const int32_t* tinst, const int32_t* itile,
-                        const int64_t* offx, const int64_t* offy, const double* ieps, int64_t total,
-                        double* gap64, float* gap32, uint32_t* bits) {
+                        const int64_t* offx, const int64_t* offy, const double* ieps, int64_t tile,
+                        int64_t total, double* gap64, float* gap32, uint32_t* bits) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < total;
   int ty = 0;
   double gv = 0.0;
   if (live) {
-    const int b = tinst[k / kTile];
-    const int64_t loc = k - (int64_t)itile[b] * kTile;
+    const int b = tinst[k / tile];
+    const int64_t loc = k - (int64_t)itile[b] * tile;
     const int64_t Lb = (offx[b + 1] - offx[b]) + (offy[b + 1] - offy[b]);
     if (loc < Lb) {
       ty = type[k];
@@ -105,9 +105,10 @@ __global__ void k_bgaps(const double* z, const uint8_t* type, const int32_t* tin
 }
 
 // tile_x0 of every instance: C_b + 1 entries from itile[b] + b, the number of
-// the instance's x points before each of its tile boundaries
-__global__ void k_btiles(const int64_t* posx, const int64_t* offx, const int32_t* itile, int B, int64_t n,
-                         int32_t* tx) {
+// the instance's x points before each of its tile boundaries (tiles of `tile`
+// points; itile holds the instances' first tiles in that tiling)
+__global__ void k_btiles(const int64_t* posx, const int64_t* offx, const int32_t* itile, int B, int64_t tile,
+                         int64_t n, int32_t* tx) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
   int lo = 0, hi = B;   // instance: the largest b with itile[b] + b <= e
@@ -117,7 +118,7 @@ __global__ void k_btiles(const int64_t* posx, const int64_t* offx, const int32_t
   }
   const int b = lo;
   const int64_t t = e - ((int64_t)itile[b] + b);
-  const int64_t bound = t * kTile;
+  const int64_t bound = t * tile;
   const int64_t* p = posx + offx[b];
   int64_t a = 0, c = offx[b + 1] - offx[b];
   while (a < c) {
@@ -403,6 +404,7 @@ ApplyArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q, bool start) {
   a.gap = (const R*)p->gap;
   a.tile_x0 = p->tile_x0;
   a.C = (int)p->C;   // units: all tiles of all instances
+  a.elems = (int)(p->btile / kThreads);
   a.lines = 1;
   a.o_es = 1;
   a.w_es = 1;
@@ -557,11 +559,14 @@ finom_status evaluate(finom_plan_s* p, double tol, int64_t maxit, double* f, dou
     view.N = p->hoffx[b + 1] - p->hoffx[b];
     view.M = p->hoffy[b + 1] - p->hoffy[b];
     view.L = view.N + view.M;
-    view.C = nt;
+    (void)nt;
+    // the float64 cost kernel works in 2048-point tiles from the instance's
+    // start: its own tile table, the packed arrays padded at the end
+    view.C = p->hitilec[b + 1] - p->hitilec[b];
     view.eps = p->heps[b];
-    view.tbits = p->tbits + t0 * (kTile / 32);
-    view.gap64 = p->gap64 + t0 * kTile;
-    view.tile_x0 = p->tile_x0 + t0 + b;
+    view.tbits = p->tbits + t0 * (p->btile / 32);
+    view.gap64 = p->gap64 + t0 * p->btile;
+    view.tile_x0 = p->tile_x0c + p->hitilec[b] + b;
     const int32_t its = stop_iter(b);
     const bool start = its == 0;
     const double* mx = start ? uni0 + p->hoffx[b] : st.mu64 + p->hoffx[b];
@@ -760,20 +765,26 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
   p->hoffx.assign(offx, offx + B + 1);
   p->hoffy.assign(offy, offy + B + 1);
   p->heps.assign(eps, eps + B);
+  const int64_t tile = p->btile;
   p->hitile.assign(B + 1, 0);
+  p->hitilec.assign(B + 1, 0);
   std::vector<int32_t> tinst;
   for (int64_t b = 0; b < B; ++b) {
     const int64_t Lb = (offx[b + 1] - offx[b]) + (offy[b + 1] - offy[b]);
-    const int64_t Cb = (Lb + kTile - 1) / kTile;
+    const int64_t Cb = (Lb + tile - 1) / tile;
     p->hitile[b + 1] = (int32_t)(p->hitile[b] + Cb);
+    p->hitilec[b + 1] = (int32_t)(p->hitilec[b] + (Lb + kTile - 1) / kTile);
     for (int64_t t = 0; t < Cb; ++t) tinst.push_back((int32_t)b);
   }
-  const int64_t T = p->hitile[B], N = offx[B], M = offy[B];
+  const int64_t T = p->hitile[B], Tc = p->hitilec[B], N = offx[B], M = offy[B];
   p->N = N;
   p->M = M;
   p->C = T;
-  p->L = T * kTile;
-  const int64_t total = T * kTile;
+  p->L = T * tile;
+  const int64_t total = T * tile;
+  // packed arrays: whole tiles, plus one 2048-point tile of padding so that the
+  // cost kernel's 2048-point tiles of the last instance stay inside them
+  const int64_t alloc = total + kTile;
   FINOM_CUDA(cudaMalloc(&p->x, sizeof(double) * N));
   FINOM_CUDA(cudaMalloc(&p->y, sizeof(double) * M));
   FINOM_CUDA(cudaMemcpyAsync(p->x, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -802,16 +813,23 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
     set_error("finom_plan_batch: every instance's x and y must be finite and sorted non-decreasing");
     return FINOM_EINVAL;
   }
-  FINOM_CUDA(cudaMalloc(&p->tbits, sizeof(uint32_t) * (total / 32)));
-  FINOM_CUDA(cudaMalloc(&p->gap64, sizeof(double) * total));
+  FINOM_CUDA(cudaMalloc(&p->tbits, sizeof(uint32_t) * (alloc / 32)));
+  FINOM_CUDA(cudaMemsetAsync(p->tbits, 0, sizeof(uint32_t) * (alloc / 32), s));
+  FINOM_CUDA(cudaMalloc(&p->gap64, sizeof(double) * alloc));
+  FINOM_CUDA(cudaMemsetAsync(p->gap64, 0, sizeof(double) * alloc, s));
   float* gap32 = nullptr;
   if (p->prec == FINOM_F32_LOG) {
-    FINOM_CUDA(cudaMalloc(&gap32, sizeof(float) * total));
+    FINOM_CUDA(cudaMalloc(&gap32, sizeof(float) * alloc));
+    FINOM_CUDA(cudaMemsetAsync(gap32, 0, sizeof(float) * alloc, s));
     p->gap = gap32;
   } else {
     p->gap = p->gap64;
   }
   FINOM_CUDA(cudaMalloc(&p->tile_x0, sizeof(int32_t) * (T + B)));
+  FINOM_CUDA(cudaMalloc(&p->tile_x0c, sizeof(int32_t) * (Tc + B)));
+  int32_t* itilec = nullptr;
+  FINOM_CUDA(cudaMalloc(&itilec, sizeof(int32_t) * (B + 1)));
+  FINOM_CUDA(cudaMemcpyAsync(itilec, p->hitilec.data(), sizeof(int32_t) * (B + 1), cudaMemcpyHostToDevice, s));
   int64_t *posx = nullptr, *posy = nullptr;
   double* z = nullptr;
   uint8_t* type = nullptr;
@@ -821,13 +839,17 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
   FINOM_CUDA(cudaMalloc(&type, total));
   FINOM_CUDA(cudaMemsetAsync(type, 0, total, s));
   FINOM_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * total, s));
-  k_bpos<<<nblk(N, 256), 256, 0, s>>>(p->x, N, p->ioffx, p->y, p->ioffy, p->itile, (int)B, 0, posx, z, type, 1);
-  k_bpos<<<nblk(M, 256), 256, 0, s>>>(p->y, M, p->ioffy, p->x, p->ioffx, p->itile, (int)B, 1, posy, z, type, 0);
-  k_bgaps<<<nblk(total, 256), 256, 0, s>>>(z, type, p->tinst, p->itile, p->ioffx, p->ioffy, p->ieps, total,
+  k_bpos<<<nblk(N, 256), 256, 0, s>>>(p->x, N, p->ioffx, p->y, p->ioffy, p->itile, (int)B, tile, 0, posx, z,
+                                       type, 1);
+  k_bpos<<<nblk(M, 256), 256, 0, s>>>(p->y, M, p->ioffy, p->x, p->ioffx, p->itile, (int)B, tile, 1, posy, z,
+                                       type, 0);
+  k_bgaps<<<nblk(total, 256), 256, 0, s>>>(z, type, p->tinst, p->itile, p->ioffx, p->ioffy, p->ieps, tile, total,
                                             p->gap64, gap32, p->tbits);
-  k_btiles<<<nblk(T + B, 256), 256, 0, s>>>(posx, p->ioffx, p->itile, (int)B, T + B, p->tile_x0);
+  k_btiles<<<nblk(T + B, 256), 256, 0, s>>>(posx, p->ioffx, p->itile, (int)B, tile, T + B, p->tile_x0);
+  k_btiles<<<nblk(Tc + B, 256), 256, 0, s>>>(posx, p->ioffx, itilec, (int)B, kTile, Tc + B, p->tile_x0c);
   FINOM_CUDA(cudaGetLastError());
   FINOM_CUDA(cudaStreamSynchronize(s));
+  cudaFree(itilec);
   cudaFree(posx);
   cudaFree(posy);
   cudaFree(z);
@@ -836,6 +858,8 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
 }
 
 void plan_batch_free(finom_plan_s* p) {
+  cudaFree(p->tile_x0c);
+  p->tile_x0c = nullptr;
   cudaFree(p->ioffx);
   cudaFree(p->ioffy);
   cudaFree(p->itile);

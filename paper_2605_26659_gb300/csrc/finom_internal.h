@@ -119,6 +119,9 @@ struct finom_plan_s {
   int64_t* ioffy = nullptr;
   int32_t* itile = nullptr;
   int32_t* tinst = nullptr;      // per tile: its instance
+  int64_t btile = finom::kTile;  // merged points per tile of the packing (256 x points per thread)
+  std::vector<int32_t> hitilec;  // per instance: first 2048-point tile of the float64 evaluation
+  int32_t* tile_x0c = nullptr;   // the evaluation's tile tables (as tile_x0, 2048-point tiles)
   double* ieps = nullptr;        // per instance
   finom::SolveState st;
 };
@@ -128,8 +131,10 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
 // tile table of a 1D plan for elems points per thread (plan.cu); the solve
 // state must be released by the caller when Ce changes
 finom_status build_tiles_e(finom_plan_s* p, int elems, cudaStream_t s);
-// points per thread that the tuning table gives a 1D plan of L merged points
+// points per thread that the tuning table gives a 1D plan of L merged points,
+// and batch plans
 int tune_pick(finom_precision prec, int64_t L);
+int tune_pick_batch(finom_precision prec);
 void free_plan(finom_plan_s* p);
 finom_status cost64(finom_plan_s* p, const double* px, const double* py, const double* u,
                     const double* v, double* err, double* w1, cudaStream_t s);

@@ -33,6 +33,7 @@ std::mutex g_tune_mu;
 // 2^20 on E = 8.
 struct Table {
   int e[2][kBuckets];
+  int batch[2] = {kElems, kElems};   // batch plans (finom_tune_set_batch)
   Table() {
     for (int b = 0; b < kBuckets; ++b) {
       e[FINOM_F64][b] = b <= 15 ? 1 : (b == 16 ? 2 : (b == 17 ? 4 : kElems));
@@ -57,9 +58,34 @@ int tune_pick(finom_precision prec, int64_t L) {
   return g_table.e[prec == FINOM_F64 ? FINOM_F64 : FINOM_F32_LOG][bucket_of(L)];
 }
 
+int tune_pick_batch(finom_precision prec) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_table.batch[prec == FINOM_F64 ? FINOM_F64 : FINOM_F32_LOG];
+}
+
 }  // namespace finom
 
 extern "C" {
+
+finom_status finom_tune_set_batch(finom_precision prec, int32_t elems) {
+  if ((prec != FINOM_F64 && prec != FINOM_F32_LOG) || !finom::valid_elems(elems)) {
+    finom::set_error("finom_tune_set_batch: need a known precision and elems in {1, 2, 4, 8}");
+    return FINOM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(finom::g_tune_mu);
+  finom::g_table.batch[prec] = elems;
+  return FINOM_OK;
+}
+
+finom_status finom_tune_get_batch(finom_precision prec, int32_t* elems) {
+  if ((prec != FINOM_F64 && prec != FINOM_F32_LOG) || !elems) {
+    finom::set_error("finom_tune_get_batch: need a known precision and elems non-null");
+    return FINOM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(finom::g_tune_mu);
+  *elems = finom::g_table.batch[prec];
+  return FINOM_OK;
+}
 
 finom_status finom_tune_set(finom_precision prec, int32_t log2_bucket, int32_t elems) {
   if ((prec != FINOM_F64 && prec != FINOM_F32_LOG) || log2_bucket < 0 || log2_bucket >= finom::kBuckets ||

@@ -186,3 +186,43 @@ def test_batch_stepwise_equals_blocking(lib, prec):
     f2, g2, r2 = lib.finom_solve_batch_end(p)
     assert np.array_equal(H(f1), H(f2)) and np.array_equal(H(g1), H(g2))
     assert [r["iters"] for r in r1] == [r["iters"] for r in r2]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+def test_batch_every_tile_size(lib, prec):
+    """The batch packed into tiles of 256, 512, 1024 and 2048 points: the
+    oracle's lock-step iterates for every tile size, and agreement across
+    tile sizes (the float64 evaluation keeps its own 2048-point tiles)."""
+    xs, ys, us, vs, eps, offx, offy = _batch(SHAPES, 150)
+    outs = {}
+    for E in (1, 2, 4, 8):
+        p = lib.finom_plan_batch(T(np.concatenate(xs)), offx, T(np.concatenate(ys)), offy, eps, prec, elems=E)
+        f, g, res = lib.finom_solve_batch(p, T(np.concatenate(us)), T(np.concatenate(vs)), 0.0, 7)
+        outs[E] = (H(f), H(g), res)
+    for b, (N, M, kind, e) in enumerate(SHAPES):
+        if min(N, M) == 1:
+            continue
+        fo, go, it, err = serial_c.sinkhorn(xs[b], ys[b], us[b], vs[b], e, 0.0, 7)
+        u = us[b]
+        for E, (f, g, res) in outs.items():
+            fb = _split(f, offx, b)
+            assert res[b]["iters"] == 7
+            assert np.max(np.abs(fb[u > 0] - fo[u > 0])) / e <= LOCK_TOL[prec], (b, E)
+            # (float32: errors near the float32 floor differ by a few 1e-7 across tilings)
+            assert res[b]["marginal_err"] == pytest.approx(outs[8][2][b]["marginal_err"],
+                                                           rel=1e-9 if prec == "f64" else 1e-3,
+                                                           abs=1e-12 if prec == "f64" else 2e-6)
+
+
+def test_batch_autotune_sets_the_batch_entry(lib):
+    from paper_2605_26659_gb300 import autotune
+    xs, ys, us, vs, eps, offx, offy = _batch(SHAPES[:5], 170, zeros=False)
+    old = lib.finom_tune_get_batch("f32_log")
+    best, times = autotune.batch(T(np.concatenate(xs)), offx, T(np.concatenate(ys)), offy, eps, "f32_log",
+                                 T(np.concatenate(us)), T(np.concatenate(vs)), iters=4)
+    assert best in (1, 2, 4, 8) and times[best] == min(times.values())
+    assert lib.finom_tune_get_batch("f32_log") == best
+    p = lib.finom_plan_batch(T(np.concatenate(xs)), offx, T(np.concatenate(ys)), offy, eps, "f32_log")
+    f, g, res = lib.finom_solve_batch(p, T(np.concatenate(us)), T(np.concatenate(vs)), 1e-6, 100000)
+    assert all(r["converged"] == 1 for r in res)
+    lib.finom_tune_set_batch("f32_log", old)
