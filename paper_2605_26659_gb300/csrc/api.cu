@@ -805,6 +805,7 @@ finom_status finom_solve_trace(finom_plan_t plan, const double* u, const double*
     set_error("finom_solve_trace: need u, v, err, ms, n non-null, maxit >= 1, every >= 1");
     return FINOM_EINVAL;
   }
+  *n = 0;
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t K = (maxit + every - 1) / every;
