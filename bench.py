@@ -539,7 +539,7 @@ def run_finom_batch(args, ws, rank, local):
                                    f"log-uniform in [1e-3, 1e-2], FP32 log-domain; 1 iteration of every "
                                    f"instance per step", "instances": len(probs), "merged_points": L,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 6 * args.steps,   # per iteration: 2 half steps, 2 instance ends, 2 compactions
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "finom::k_apply<float, BHalfY|BHalfX> + k_batch_end",
