@@ -507,7 +507,7 @@ finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const dou
 
 extern "C" {
 
-int finom_version(void) { return 100; }
+int finom_version(void) { return 200; }
 
 const char* finom_last_error(void) { return g_err.c_str(); }
 
