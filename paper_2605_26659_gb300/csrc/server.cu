@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -216,8 +218,13 @@ finom_status finish(finom_server_s* s, Req* r, bool* more) {
     *more = true;
     return FINOM_OK;
   }
-  r->f.resize(n1);
-  r->g.resize(n2);
+  try {
+    r->f.resize(n1);
+    r->g.resize(n2);
+  } catch (const std::bad_alloc&) {
+    finom::set_error("finom_server_step: out of host memory for a result");
+    return FINOM_ENOMEM;
+  }
   FINOM_CUDA(cudaMemcpyAsync(r->f.data(), f, sizeof(double) * n1, cudaMemcpyDeviceToHost, st));
   FINOM_CUDA(cudaMemcpyAsync(r->g.data(), g, sizeof(double) * n2, cudaMemcpyDeviceToHost, st));
   FINOM_CUDA(cudaStreamSynchronize(st));
@@ -289,7 +296,8 @@ finom_status finom_server_set_eps_scaling(finom_server_t s, int32_t stages, doub
 finom_status finom_server_submit_1d(finom_server_t s, const double* x, int64_t N, const double* y, int64_t M,
                                     const double* u, const double* v, double eps, double tol, int64_t maxit,
                                     int64_t* id) {
-  if (!s || !x || !y || !u || !v || N < 1 || M < 1 || !(eps > 0.0) || !(tol >= 0.0) || maxit < 0) {
+  if (!s || !x || !y || !u || !v || N < 1 || M < 1 || N > INT32_MAX || M > INT32_MAX - N || !(eps > 0.0) ||
+      !(tol >= 0.0) || maxit < 0) {
     finom::set_error("finom_server_submit_1d: bad argument");
     return FINOM_EINVAL;
   }
@@ -301,18 +309,24 @@ finom_status finom_server_submit_1d(finom_server_t s, const double* x, int64_t N
   r->eps = eps;
   r->tol = tol;
   r->maxit = maxit;
-  r->in[0].assign(x, x + N);
-  r->in[1].assign(y, y + M);
-  r->in[2].assign(u, u + N);
-  r->in[3].assign(v, v + M);
+  try {   // the host copies of the inputs (no C++ exception crosses the C ABI)
+    r->in[0].assign(x, x + N);
+    r->in[1].assign(y, y + M);
+    r->in[2].assign(u, u + N);
+    r->in[3].assign(v, v + M);
+  } catch (const std::bad_alloc&) {
+    delete r;
+    finom::set_error("finom_server_submit_1d: out of host memory");
+    return FINOM_ENOMEM;
+  }
   return submit(s, r, id);
 }
 
 finom_status finom_server_submit_2d(finom_server_t s, const double* x1, const double* x2, int64_t N,
                                     const double* y1, const double* y2, int64_t M, const double* U,
                                     const double* V, double eps, double tol, int64_t maxit, int64_t* id) {
-  if (!s || !x1 || !x2 || !y1 || !y2 || !U || !V || N < 1 || M < 1 || !(eps > 0.0) || !(tol >= 0.0) ||
-      maxit < 0) {
+  if (!s || !x1 || !x2 || !y1 || !y2 || !U || !V || N < 1 || M < 1 || N > ((int64_t)1 << 31) / M ||
+      !(eps > 0.0) || !(tol >= 0.0) || maxit < 0) {
     finom::set_error("finom_server_submit_2d: bad argument");
     return FINOM_EINVAL;
   }
@@ -324,12 +338,18 @@ finom_status finom_server_submit_2d(finom_server_t s, const double* x1, const do
   r->eps = eps;
   r->tol = tol;
   r->maxit = maxit;
-  r->in[0].assign(x1, x1 + N);
-  r->in[1].assign(x2, x2 + N);
-  r->in[2].assign(y1, y1 + M);
-  r->in[3].assign(y2, y2 + M);
-  r->in[4].assign(U, U + N * M);
-  r->in[5].assign(V, V + N * M);
+  try {   // the host copies of the inputs (no C++ exception crosses the C ABI)
+    r->in[0].assign(x1, x1 + N);
+    r->in[1].assign(x2, x2 + N);
+    r->in[2].assign(y1, y1 + M);
+    r->in[3].assign(y2, y2 + M);
+    r->in[4].assign(U, U + N * M);
+    r->in[5].assign(V, V + N * M);
+  } catch (const std::bad_alloc&) {
+    delete r;
+    finom::set_error("finom_server_submit_2d: out of host memory");
+    return FINOM_ENOMEM;
+  }
   return submit(s, r, id);
 }
 
