@@ -83,3 +83,26 @@ def test_tuning_table_round_trip_without_gpu(libpath):
     assert lib.finom_tune_get(1, -1, ctypes.byref(e)) == 1
     lib.finom_tune_get(1, 12, ctypes.byref(e))
     assert e.value == old.value
+
+
+def test_tuning_cache_applies_without_gpu(libpath, tmp_path):
+    """The autotuner's JSON cache round trip: apply() installs its entries in
+    the library's table (host-side; no GPU needed)."""
+    import json
+    from paper_2605_26659_gb300 import api, autotune
+    api.load()
+    before = {(p, b): api.finom_tune_get(p, b) for p in ("f64", "f32_log") for b in (11, 17)}
+    cache = {"buckets": {"f64": {"11": 2, "17": 8}, "f32_log": {"11": 4, "17": 1}}}
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps(cache))
+    autotune.apply(str(path))
+    try:
+        assert api.finom_tune_get("f64", 11) == 2 and api.finom_tune_get("f64", 17) == 8
+        assert api.finom_tune_get("f32_log", 11) == 4 and api.finom_tune_get("f32_log", 17) == 1
+    finally:
+        for (p, b), e in before.items():
+            api.finom_tune_set(p, b, e)
+    old = api.finom_tune_get_batch("f32_log")
+    api.finom_tune_set_batch("f32_log", 2)
+    assert api.finom_tune_get_batch("f32_log") == 2
+    api.finom_tune_set_batch("f32_log", old)
