@@ -490,11 +490,13 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
  * afford the allocator's locks and implicit synchronisation).  The paper has
  * no counterpart; this is a property of the library, not of the method.
  *   - Allocates nothing: no cudaMalloc/cudaFree and no allocating library
- *     call.  The working memory of the scan (tile maps, tile carries, the
- *     last-block ticket) is one static device array of 327,936 bytes that
- *     every GPU loading the library keeps until the process exits.
- *   - Limit: N + M <= 8,388,608 merged points (4096 tiles); larger plans
- *     return FINOM_EINVAL with a message, and nothing is launched.
+ *     call.  The working memory of the scan (tile aggregates, tile carries,
+ *     the last-block ticket) is one static device array of 262,400 bytes
+ *     that every GPU loading the library keeps until the process exits.
+ *   - Limit: at most 4096 tiles of the plan, i.e. N + M <= 8,388,608 merged
+ *     points at the default 8 points per thread (finom_plan_elems reports a
+ *     plan's tile count); larger plans return FINOM_EINVAL with a message,
+ *     and nothing is launched.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -502,8 +504,10 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
  *     is reset at the start of each call.  Calls that overlap on the GPU (on
  *     different streams, or from different host threads) race and must not
  *     be issued.
- *   - One pass with a as the frame: results agree with finom_kv_log to the
- *     plan's precision when a varies smoothly between neighbouring points.
+ *   - The levels are formed inside the kernel from a, b and the plan's
+ *     positions, in one pass; the result is the one finom_kv_log computes,
+ *     with the same error bound (1e-5 relative in float32, 1e-12 in
+ *     float64), for any a and b.
  * Arguments as finom_kv_log (device pointers; out: N doubles, natural log).
  */
 finom_status finom_kv_log_noalloc(finom_plan_t plan, const double* a, const double* b, double* out,

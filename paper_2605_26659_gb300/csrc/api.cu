@@ -10,6 +10,7 @@
 
 #include "apply.cuh"
 #include "finom_internal.h"
+#include "half.cuh"
 
 namespace finom {
 
@@ -46,6 +47,17 @@ template <class R>
 void frame_from_log(const double*, int64_t, void*, cudaStream_t);
 void combine_passes(const double*, const double*, double, int64_t, int, double*, cudaStream_t);
 void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
+template <class R>
+finom_status half_launch(const HalfArgs<R>&, int, int, cudaStream_t);
+template <class R>
+void beta_set(void*, const double*, int64_t, double, const double*, double, double, cudaStream_t);
+template <class R>
+void beta_lin(void*, const double*, int64_t, double, const double*, cudaStream_t);
+template <class R>
+void log_mass(const double*, int64_t, void*, cudaStream_t);
+template <class R>
+void f_from_beta(const void*, const double*, int64_t, double, double*, double*, cudaStream_t);
+void add_scaled(double*, const double*, double, int64_t, cudaStream_t);
 
 namespace {
 
@@ -64,40 +76,45 @@ struct DeviceGuard {
 };
 
 template <class R>
-constexpr size_t pot_size() { return sizeof(typename Tr<R>::Pot); }
+constexpr size_t beta_size() { return sizeof(typename HT<R>::Beta); }
+template <class R>
+constexpr size_t level_size() { return sizeof(typename HT<R>::Lv); }
 template <class R>
 constexpr size_t mass_size() { return sizeof(typename Tr<R>::Mass); }
 
+// Device state of the loop of a 1D plan: per point its two levels
+// (beta+, beta-) of the half-step kernel (half.cuh), ping-pong; log2 masses;
+// float64 masses; tile aggregates and carries (two log-sum states per tile).
 template <class R>
 finom_status ensure_state(finom_plan_s* p) {
   SolveState& st = p->st;
   if (st.ready) return FINOM_OK;
   const int64_t N = p->N, M = p->M, C = p->Ce, NM = std::max(N, M);
+  const int64_t per_tile = 2 * HT<R>::kSt;
   for (int q = 0; q < 2; ++q) {
-    FINOM_CUDA(cudaMalloc(&st.px[q], pot_size<R>() * N));
-    FINOM_CUDA(cudaMalloc(&st.py[q], pot_size<R>() * M));
+    FINOM_CUDA(cudaMalloc(&st.px[q], beta_size<R>() * N));
+    FINOM_CUDA(cudaMalloc(&st.py[q], beta_size<R>() * M));
   }
   FINOM_CUDA(cudaMalloc(&st.mu, mass_size<R>() * N));
   FINOM_CUDA(cudaMalloc(&st.nu, mass_size<R>() * M));
+  FINOM_CUDA(cudaMalloc(&st.qom, level_size<R>() * N));   // log2 masses of x
+  FINOM_CUDA(cudaMalloc(&st.qwm, level_size<R>() * M));   // log2 masses of y
   FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * N));
   FINOM_CUDA(cudaMalloc(&st.nu64, sizeof(double) * M));
   // (also the scratch of normalise_masses: at least 257 entries)
   FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * std::max<int64_t>(N, 512)));
   FINOM_CUDA(cudaMalloc(&st.ty, sizeof(double) * std::max<int64_t>(M, 512)));
-  FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * 6 * C));
-  FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * 4 * C));
+  FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * per_tile * C));
+  FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * per_tile * C));
   FINOM_CUDA(cudaMalloc(&st.part, sizeof(double) * C));
   FINOM_CUDA(cudaMalloc(&st.scal, sizeof(double) * 520));
   FINOM_CUDA(cudaMalloc(&st.ctrl, sizeof(int32_t) * 8));
   FINOM_CUDA(cudaMalloc(&st.bad, sizeof(int)));
-  FINOM_CUDA(cudaMalloc(&st.qo, pot_size<R>() * NM));
-  FINOM_CUDA(cudaMalloc(&st.qom, mass_size<R>() * NM));
-  FINOM_CUDA(cudaMalloc(&st.qw, pot_size<R>() * NM));
-  FINOM_CUDA(cudaMalloc(&st.qwm, mass_size<R>() * NM));
+  FINOM_CUDA(cudaMalloc(&st.qo, beta_size<R>() * NM));
+  FINOM_CUDA(cudaMalloc(&st.qw, beta_size<R>() * NM));
   FINOM_CUDA(cudaMemset(st.ctrl, 0, sizeof(int32_t) * 8));
   FINOM_CUDA(cudaMemset(st.scal, 0, sizeof(double) * 520));
-  FINOM_CUDA(cudaMemset(st.carries, 0, sizeof(R) * 4 * C));
-  FINOM_CUDA(cudaMemset(st.qom, 0, mass_size<R>() * NM));
+  FINOM_CUDA(cudaMemset(st.carries, 0, sizeof(R) * per_tile * C));
   FINOM_CUDA(cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking));
   st.ready = true;
   return FINOM_OK;
@@ -120,17 +137,12 @@ void free_state(finom_plan_s* p) {
 }
 
 template <class R>
-ApplyArgs<R> base_args(finom_plan_s* p) {
-  ApplyArgs<R> a{};
+HalfArgs<R> base_args(finom_plan_s* p) {
+  HalfArgs<R> a{};
   a.tbits = p->tbits;
-  a.gap = (const R*)p->gap;
   a.tile_x0 = p->tile_x0e;
   a.L = p->L;
   a.C = (int)p->Ce;
-  a.elems = p->elems;
-  a.lines = 1;
-  a.o_es = 1;
-  a.w_es = 1;
   a.agg_out = (R*)p->st.aggs;
   a.carry_in = (const R*)p->st.carries;
   a.carry_out = (R*)p->st.carries;
@@ -140,51 +152,50 @@ ApplyArgs<R> base_args(finom_plan_s* p) {
   return a;
 }
 
-// One kernel product: frames qo on the O side, weights (qw, qwm) on the W side.
 template <class R>
-finom_status product(finom_plan_s* p, int o_is_x, double* out, int outflag, cudaStream_t s) {
-  using Pot = typename Tr<R>::Pot;
-  using Mass = typename Tr<R>::Mass;
+finom_status launch_half(const HalfArgs<R>& a, int mode, finom_plan_s* p, cudaStream_t s) {
+  return half_launch<R>(a, mode, p->elems, s);
+}
+
+// One kernel product: O frames qo, W levels qw; the tile aggregates of the
+// W side first, then the product itself (outputs to out).
+template <class R>
+finom_status product(finom_plan_s* p, int o_is_x, double* out, int mode, cudaStream_t s) {
+  using Beta = typename HT<R>::Beta;
   SolveState& st = p->st;
   st.active = false;   // a product overwrites the loop's scan scratch
-  ApplyArgs<R> a = base_args<R>(p);
+  HalfArgs<R> a = base_args<R>(p);
   a.o_is_x = o_is_x;
-  a.pO = (const Pot*)st.qo;
-  a.mO = (const Mass*)st.qom;
-  a.pW = (const Pot*)st.qw;
-  a.mW = (const Mass*)st.qwm;
+  a.bO = (const Beta*)st.qo;
+  a.bW = (const Beta*)st.qw;
   a.out = out;
-  a.flags = 0;
-  finom_status rc = launch_apply<R>(a, true, s);
+  a.carry_in = nullptr;
+  finom_status rc = launch_half<R>(a, kHalfAgg, p, s);
   if (rc != FINOM_OK) return rc;
-  a.flags = outflag;
-  return launch_apply<R>(a, false, s);
+  a.carry_in = (const R*)st.carries;
+  return launch_half<R>(a, mode, p, s);
 }
 
 template <class R>
-ApplyArgs<R> half_args(finom_plan_s* p, bool o_is_x, int q) {
-  using Pot = typename Tr<R>::Pot;
-  using Mass = typename Tr<R>::Mass;
+HalfArgs<R> half_args(finom_plan_s* p, bool o_is_x, int q) {
+  using Beta = typename HT<R>::Beta;
+  using Lv = typename HT<R>::Lv;
   SolveState& st = p->st;
-  ApplyArgs<R> a = base_args<R>(p);
+  HalfArgs<R> a = base_args<R>(p);
   a.tol = st.tol;
   a.maxit = st.maxit;
-  if (!o_is_x) {   // psi <- v / (K^T phi): outputs on y, weights on x
+  if (!o_is_x) {   // psi <- nu / (K^T phi): outputs on y, weights on x
     a.o_is_x = 0;
-    a.pO = (const Pot*)st.py[q];
-    a.mO = (const Mass*)st.nu;
-    a.pO_out = (Pot*)st.py[1 - q];
-    a.pW = (const Pot*)st.px[q];
-    a.mW = (const Mass*)st.mu;
-    a.flags = F_OUT_POT | F_ERR | F_NEXT | F_CHECK_DONE;
-  } else {         // phi <- u / (K psi): outputs on x, weights on y
+    a.bO = (const Beta*)st.py[q];
+    a.lmO = (const Lv*)st.qwm;
+    a.bO_out = (Beta*)st.py[1 - q];
+    a.bW = (const Beta*)st.px[q];
+  } else {         // phi <- mu / (K psi): outputs on x, weights on y
     a.o_is_x = 1;
-    a.pO = (const Pot*)st.px[q];
-    a.mO = (const Mass*)st.mu;
-    a.pO_out = (Pot*)st.px[1 - q];
-    a.pW = (const Pot*)st.py[1 - q];
-    a.mW = (const Mass*)st.nu;
-    a.flags = F_OUT_POT | F_NEXT | F_ITER_END | F_CHECK_DONE;
+    a.bO = (const Beta*)st.px[q];
+    a.lmO = (const Lv*)st.qom;
+    a.bO_out = (Beta*)st.px[1 - q];
+    a.bW = (const Beta*)st.py[1 - q];
   }
   return a;
 }
@@ -192,9 +203,9 @@ ApplyArgs<R> half_args(finom_plan_s* p, bool o_is_x, int q) {
 // one Sinkhorn iteration with parity q (iteration l has q = l % 2)
 template <class R>
 finom_status launch_iteration(finom_plan_s* p, int q, cudaStream_t s) {
-  finom_status rc = launch_apply<R>(half_args<R>(p, false, q), false, s);
+  finom_status rc = launch_half<R>(half_args<R>(p, false, q), kHalfY, p, s);
   if (rc != FINOM_OK) return rc;
-  return launch_apply<R>(half_args<R>(p, true, q), false, s);
+  return launch_half<R>(half_args<R>(p, true, q), kHalfX, p, s);
 }
 
 // graph of 2 * pairs iterations starting at an odd iteration (q = 1, 0, 1, ...)
@@ -235,14 +246,17 @@ finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, doub
   if (rc != FINOM_OK) return rc;
   rc = normalise_masses<R>(v, M, st.nu, st.nu64, st.ty, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
+  log_mass<R>(st.mu64, N, st.qom, s);
+  log_mass<R>(st.nu64, M, st.qwm, s);
   const double scale = 1.0 / (p->eps * kLn2);
   st.warm = (f0 != nullptr && g0 != nullptr);
   if (st.warm) {
-    conv_pot_from_f<R>(f0, st.mu64, N, scale, st.px[0], s);
-    conv_pot_from_f<R>(g0, st.nu64, M, scale, st.py[0], s);
+    beta_set<R>(st.px[0], p->x, N, scale, f0, scale, 0.0, s);
+    beta_set<R>(st.py[0], p->y, M, scale, g0, scale, 0.0, s);
   } else {
-    fill_pot<R>(st.px[0], N, 0.0, s);
-    fill_pot<R>(st.py[0], M, 0.0, s);
+    // the paper's start phi = 1/N, psi = 1/M at every point
+    beta_set<R>(st.px[0], p->x, N, scale, nullptr, 0.0, std::log2(1.0 / (double)N), s);
+    beta_set<R>(st.py[0], p->y, M, scale, nullptr, 0.0, std::log2(1.0 / (double)M), s);
   }
   FINOM_CUDA(cudaMemsetAsync(st.ctrl, 0, sizeof(int32_t) * 8, s));
   FINOM_CUDA(cudaMemsetAsync(st.scal, 0, sizeof(double) * 8, s));
@@ -250,23 +264,17 @@ finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, doub
   st.maxit = maxit;
   st.launched = 0;
   st.active = true;
-  // iteration 0: the first K^T phi uses phi = 1/N and checks against psi = 1/M
-  ApplyArgs<R> a0 = half_args<R>(p, false, 0);
-  if (!st.warm) {
-    a0.w_uniform = (R)(1.0 / (double)N);
-    a0.o_scale = (R)(1.0 / (double)M);
-  }
-  ApplyArgs<R> agg = a0;
-  agg.flags = 0;
-  rc = launch_apply<R>(agg, true, s);
+  // iteration 0: the tile aggregates of phi, then psi <- nu / K^T phi (its
+  // loop-head check against the starting psi), then phi <- mu / K psi
+  HalfArgs<R> a0 = half_args<R>(p, false, 0);
+  HalfArgs<R> agg = a0;
+  agg.carry_in = nullptr;
+  rc = launch_half<R>(agg, kHalfAgg, p, s);
   if (rc != FINOM_OK) return rc;
-  if (maxit == 0) {   // only the loop-head check of l = 0
-    a0.flags = F_ERR;
-    return launch_apply<R>(a0, false, s);
-  }
-  rc = launch_apply<R>(a0, false, s);
+  if (maxit == 0) return launch_half<R>(a0, kHalfCheck, p, s);   // only the loop-head check of l = 0
+  rc = launch_half<R>(a0, kHalfY, p, s);
   if (rc != FINOM_OK) return rc;
-  rc = launch_apply<R>(half_args<R>(p, true, 0), false, s);
+  rc = launch_half<R>(half_args<R>(p, true, 0), kHalfX, p, s);
   if (rc != FINOM_OK) return rc;
   st.launched = 1;
   return FINOM_OK;
@@ -339,8 +347,8 @@ finom_status solve_end(finom_plan_s* p, double* f, double* g, finom_result* res,
     err64 = loop_err;
   } else {
     const int q = (int)(iters & 1);
-    conv_f_from_pot<R>(st.px[q], st.mu64, N, eps_ln2, f, st.tx, s);
-    conv_f_from_pot<R>(st.py[q], st.nu64, M, eps_ln2, g, st.ty, s);
+    f_from_beta<R>(st.px[q], st.mu64, N, eps_ln2, f, st.tx, s);
+    f_from_beta<R>(st.py[q], st.nu64, M, eps_ln2, g, st.ty, s);
     finom_status rc = cost64(p, st.tx, st.ty, st.mu64, st.nu64, &err64, &w1, s);
     if (rc != FINOM_OK) return rc;
   }
@@ -410,18 +418,18 @@ finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, d
       const int q = (int)(l & 1);
       const double eps_ln2 = p->eps * kLn2;
       // float64 smooth potentials into tx, ty (f, g receive the full ones)
-      conv_f_from_pot<R>(st.px[q], st.mu64, p->N, eps_ln2, f, st.tx, s);
-      conv_f_from_pot<R>(st.py[q], st.nu64, p->M, eps_ln2, g, st.ty, s);
+      f_from_beta<R>(st.px[q], st.mu64, p->N, eps_ln2, f, st.tx, s);
+      f_from_beta<R>(st.py[q], st.nu64, p->M, eps_ln2, g, st.ty, s);
       rc = cost64(p, st.tx, st.ty, st.mu64, st.nu64, &err64, &w1, s);
       if (rc != FINOM_OK) return rc;
       if (err64 <= tol) break;
       // resume: clear the stop, continue with the phi half step of iteration l
-      const double f = std::max(0.1, std::min(0.8, 0.8 * tol / err64));
+      const double f = std::max(0.1, std::min(0.97, 0.97 * tol / err64));
       st.tol = std::max(loop_err * f, 0.0);
       int32_t zero[2] = {0, 0};
       FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 1, &zero[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
       FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 4, &zero[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      rc = launch_apply<R>(half_args<R>(p, true, q), false, s);
+      rc = launch_half<R>(half_args<R>(p, true, q), kHalfX, p, s);
       if (rc != FINOM_OK) return rc;
       st.launched = l + 1;
     }
@@ -456,10 +464,10 @@ using namespace finom;
 
 namespace {
 
-// Standalone products run two passes: the first with frame 0 gives ln S0;
-// the second uses the frame -ln S0 so that its sums are near 1, where the
-// float32 log-sum keeps full relative precision; the results are combined in
-// float64.  The O side's own absorption (log products) enters only there.
+// Standalone products: one pass of the half-step kernel with the O frames
+// at 0 (levels +-Z), which yields ln (K w) at every O point directly in
+// float64 (the levels are exact pairs; see half.cuh).  The O side's own
+// absorption of a log product is added afterwards.
 template <class R>
 finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double* a, const double* b,
                      double* out, cudaStream_t s) {
@@ -468,22 +476,20 @@ finom_status kv_impl(finom_plan_t p, bool transpose, bool logmode, const double*
   SolveState& st = p->st;
   const int64_t N = p->N, M = p->M;
   const int64_t nO = transpose ? M : N, nW = transpose ? N : M;
+  const double* posO = transpose ? p->y : p->x;
+  const double* posW = transpose ? p->x : p->y;
   const double scale = 1.0 / (p->eps * kLn2);
-  // log products: the O side's absorption (frames) and the W side's absorption;
-  // linear products: no O-side absorption, the weights are the input vector b
+  // log products: the O side's absorption (added at the end) and the W
+  // side's absorption (the weights); linear products: the weights are b
   const double* ao = logmode ? (transpose ? b : a) : nullptr;
   const double* bw = logmode ? (transpose ? a : b) : b;
-  double* t0 = transpose ? st.ty : st.tx;
-  if (logmode) conv_weights_log<R>(bw, nW, scale, st.qw, st.qwm, s);
-  else conv_weights_lin<R>(bw, nW, st.qw, st.qwm, s);
-  fill_pot<R>(st.qo, nO, 0.0, s);
+  if (logmode) beta_set<R>(st.qw, posW, nW, scale, bw, scale, 0.0, s);
+  else beta_lin<R>(st.qw, posW, nW, scale, bw, s);
+  beta_set<R>(st.qo, posO, nO, scale, nullptr, 0.0, 0.0, s);
   const int o_is_x = transpose ? 0 : 1;
-  rc = product<R>(p, o_is_x, t0, F_OUT_LOG, s);
+  rc = product<R>(p, o_is_x, out, logmode ? kHalfLog : kHalfLin, s);
   if (rc != FINOM_OK) return rc;
-  frame_from_log<R>(t0, nO, st.qo, s);
-  rc = product<R>(p, o_is_x, out, logmode ? F_OUT_LOG : F_OUT_LIN, s);
-  if (rc != FINOM_OK) return rc;
-  combine_passes(t0, ao, 1.0 / p->eps, nO, logmode ? 0 : 1, out, s);
+  if (logmode) add_scaled(out, ao, 1.0 / p->eps, nO, s);
   FINOM_CUDA(cudaGetLastError());
   return FINOM_OK;
 }

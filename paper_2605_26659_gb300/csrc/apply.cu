@@ -215,6 +215,12 @@ __global__ void k_combine(const double* t0, const double* a, double inv_eps, int
   else out[i] = (t > -INFINITY) ? a[i] * inv_eps + t + l2 : -INFINITY;
 }
 
+// out += a * sc (ln of a product plus the O side's absorption a / eps)
+__global__ void k_add_scaled(double* out, const double* a, double sc, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = out[i] + a[i] * sc;
+}
+
 __global__ void k_fill_d(double* f, int64_t n, double v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) f[i] = v;
@@ -320,6 +326,9 @@ FINOM_INST(double)
 #undef FINOM_INST
 
 void fill_d(double* f, int64_t n, double v, cudaStream_t s) { k_fill_d<<<nb(n), 256, 0, s>>>(f, n, v); }
+void add_scaled(double* out, const double* a, double sc, int64_t n, cudaStream_t s) {
+  k_add_scaled<<<nb(n), 256, 0, s>>>(out, a, sc, n);
+}
 void dot_pos(const double* m, const double* f, int64_t n, double* out, cudaStream_t s) {
   k_dot_pos<<<1, 256, 0, s>>>(m, f, n, out);
 }

@@ -1,0 +1,799 @@
+// FINOM half step on absolute levels: one launch applies K (or K^T) to the
+// weights of one mesh and performs the Sinkhorn division at the other.
+//
+// Every point k of either mesh carries its log-weight b_k in bits (b = f /
+// (eps ln 2) for a potential f in cost units; it includes log2 of the mass)
+// and its position Z_k = z_k / (eps ln 2) in bits, stored as the two levels
+//     beta+_k = b_k + Z_k,      beta-_k = b_k - Z_k.
+// With the merged order of both meshes (y before x on ties), the dividing
+// index zeta(k) of an output point k (Definition, Sec. 2.2) counts the
+// weight points before it, and the two blocks of eq. decompose to p+q are
+//     p_k = sum_{m < zeta(k)} 2^{b_m - (Z_k - Z_m)} = 2^{-Z_k} sum_{m < zeta(k)} 2^{beta+_m}
+//     q_k = sum_{m >= zeta(k)} 2^{b_m - (Z_m - Z_k)} = 2^{Z_k}  sum_{m >= zeta(k)} 2^{beta-_m}
+// i.e. the first-order recurrences of eqs. p/q by dynamic programming, with
+// their decay factors folded into the levels, become a prefix and a suffix
+// log-sum over the weight points.  The log-sum is associative and
+// commutative, so tile maps and carries are plain log-sum states (M, s):
+// value s * 2^M, M a level of the weight points (exact: a float-float pair in
+// the float32 path), s in [1, n] a float sum of mantissas.  Levels are large
+// numbers; only differences of levels that are moderate wherever they matter
+// are rounded to float32, so the float32 path keeps its precision on any
+// mesh (large gaps, disjoint supports).
+//
+// At an output (O) point with the old log-weight b_k as frame, the stabilised
+// sum of the Remark on log-domain stabilisation is
+//     S_k = 2^{b_k} (p_k + q_k) = 2^{beta-_k} P_k + 2^{beta+_k} Q_k,
+// P_k, Q_k the prefix / suffix sums; the division of eq. iteration sets
+//     b_k <- log2 mu_k - log2 (p_k + q_k) = b_k - delta_k,
+//     delta_k = log2 S_k - log2 mu_k,
+// and the marginal error of Algorithm 1's loop head (Sec. 4) is
+//     sum_k |S_k - mu_k| = sum_k mu_k |2^{delta_k} - 1|.
+//
+// One CTA owns one tile of the merged order (E * kThreads points).  Its weight
+// (W) points and output (O) points are handled separately, each as contiguous
+// runs of about equal length per thread (no per-point predication):
+//   1. every thread records, for each O point of its merged points, the
+//      number of W points of the tile before it (its local dividing index);
+//   2. W phase: each thread forms the running prefix log-sum of beta+ and the
+//      running suffix log-sum of beta- over its W run, in shared memory; two
+//      warps scan the 256 run totals, seeded with the tile's carries;
+//   3. O phase: each O point combines the entry state of the thread that owns
+//      the W point at its dividing index with that thread's local state,
+//      forms S_k, divides, adds its marginal-error term and, for the next
+//      application (roles swapped), accumulates its new levels into the
+//      tile's aggregate;
+//   4. the last CTA to finish scans the tile aggregates into the carries of
+//      the next launch, reduces the error in float64 and updates the loop
+//      control.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "dev_common.cuh"
+#include "finom_internal.h"
+
+namespace finom {
+
+enum : int {
+  H_POT = 1,          // division: write the new O levels
+  H_ERR = 2,          // marginal error at the O points + convergence flag
+  H_NEXT = 4,         // tile aggregates of the next application (new O levels)
+  H_ITER_END = 8,     // this launch ends a Sinkhorn iteration
+  H_CHECK_DONE = 16,  // exit at once when the loop is done
+  H_AGG = 32,         // only the tile aggregates of this application's W side
+  H_LOG = 64,         // products: ln of the sum at the O points (float64)
+  H_LIN = 128,        // products: the sum at the O points (float64)
+  H_RAW = 256,        // products: levels formed from the caller's float64 vectors and the
+                      // plan's positions inside the kernel (no converted copies)
+};
+
+constexpr int kHalfY = H_POT | H_ERR | H_NEXT | H_CHECK_DONE;       // psi <- nu / K^T phi
+constexpr int kHalfX = H_POT | H_NEXT | H_ITER_END | H_CHECK_DONE;  // phi <- mu / K psi
+constexpr int kHalfCheck = H_ERR;                                    // loop-head check only
+constexpr int kHalfAgg = H_AGG;
+constexpr int kHalfLog = H_LOG;
+constexpr int kHalfLin = H_LIN;
+constexpr int kHalfRawAgg = H_AGG | H_RAW;
+constexpr int kHalfRawLog = H_LOG | H_RAW;
+
+// Level arithmetic per precision.  Beta holds (beta+, beta-) of one point.
+template <class R>
+struct HT;
+
+template <>
+struct HT<float> {
+  using Lv = float2;    // unevaluated sum hi + lo
+  using Beta = float4;  // (beta+.hi, beta+.lo, beta-.hi, beta-.lo)
+  static constexpr int kSt = 3;   // values of a stored state: M.hi, M.lo, s
+  static constexpr float kNone = -1.0e30f;
+  __device__ __forceinline__ static Lv bp(const Beta& b) { return make_float2(b.x, b.y); }
+  __device__ __forceinline__ static Lv bm(const Beta& b) { return make_float2(b.z, b.w); }
+  __device__ __forceinline__ static Beta pack(Lv p, Lv m) { return make_float4(p.x, p.y, m.x, m.y); }
+  __device__ __forceinline__ static Lv none() { return make_float2(kNone, 0.f); }
+  __device__ __forceinline__ static bool valid(Lv a) { return a.x > 0.5f * kNone; }
+  __device__ __forceinline__ static float ex2(float x) { return ex2_approx(x); }
+  __device__ __forceinline__ static float lg2(float x) { return lg2_approx(x); }
+  // log2 with a relative error of about one ulp of the result: the division
+  // step takes log2 of a mantissa sum in [1, 4), where lg2.approx has an
+  // absolute error of ~2^-22 (not small against a result near 0)
+  __device__ __forceinline__ static float lg2_acc(float x) { return log2f(x); }
+  // a - b rounded once (exact where the hi parts are within a factor 2)
+  __device__ __forceinline__ static float diff(Lv a, Lv b) { return (a.x - b.x) + (a.y - b.y); }
+  // (a + b) + k - c for a small integer k: the hi parts are added with
+  // their rounding error kept (two-sum), and k and c enter before anything
+  // is rounded, so the result is accurate wherever it is moderate
+  __device__ __forceinline__ static float sum_minus(Lv a, Lv b, Lv c, float k) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    return (((s + k) - c.x) + e) + ((a.y + b.y) - c.y);
+  }
+  // s = m 2^k with m in [1, 2) (s = 0: m = 0, k = 0)
+  __device__ __forceinline__ static float mant_exp(float s, float& m) {
+    const uint32_t b = __float_as_uint(s);
+    const int ex = (int)((b >> 23) & 0xffu);
+    m = ex ? __uint_as_float((b & 0x007fffffu) | 0x3f800000u) : 0.f;
+    return ex ? (float)(ex - 127) : 0.f;
+  }
+  __device__ __forceinline__ static Lv zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static float hi(Lv a) { return a.x; }
+  // a - t as a renormalised pair
+  __device__ __forceinline__ static Lv sub(Lv a, float t) {
+    const float s = a.x - t;
+    const float bb = s - a.x;
+    const float err = (a.x - (s - bb)) + (-t - bb);
+    float lo = err + a.y;
+    const float hi = s + lo;
+    lo = lo - (hi - s);
+    return make_float2(hi, lo);
+  }
+  // a - t with the rounding error of the hi part moved to lo (exact when
+  // |a.x| >= |t|, the case of a division step near the fixed point); the pair
+  // is not renormalised
+  __device__ __forceinline__ static Lv sub_fast(Lv a, float t) {
+    const float s = a.x - t;
+    return make_float2(s, a.y + ((a.x - s) - t));
+  }
+  __device__ __forceinline__ static double to_double(Lv a) { return (double)a.x + (double)a.y; }
+  // the levels b + z, b - z of float64 values as pairs (b = -inf: none)
+  __device__ __forceinline__ static Beta make_beta(double b, double z) {
+    if (!(b > -INFINITY)) return make_float4(kNone, 0.f, kNone, 0.f);
+    const double p = b + z, m = b - z;
+    const float ph = (float)p, mh = (float)m;
+    return make_float4(ph, (float)(p - (double)ph), mh, (float)(m - (double)mh));
+  }
+  __device__ __forceinline__ static void put(float* p, Lv M, float s) { p[0] = M.x; p[1] = M.y; p[2] = s; }
+  // a state from global memory written by another CTA (L2, not L1)
+  __device__ __forceinline__ static void get(const float* p, Lv& M, float& s) {
+    M = make_float2(__ldcg(p), __ldcg(p + 1));
+    s = __ldcg(p + 2);
+  }
+  // a state from shared memory
+  __device__ __forceinline__ static void get_s(const float* p, Lv& M, float& s) {
+    M = make_float2(p[0], p[1]);
+    s = p[2];
+  }
+  __device__ __forceinline__ static Lv shfl_up(Lv a, int o) {
+    return make_float2(__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o));
+  }
+  __device__ __forceinline__ static Lv shfl_down(Lv a, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, a.x, o), __shfl_down_sync(0xffffffffu, a.y, o));
+  }
+};
+
+template <>
+struct HT<double> {
+  using Lv = double;
+  using Beta = double2;  // (beta+, beta-)
+  static constexpr int kSt = 2;
+  static constexpr double kNone = -1.0e300;
+  __device__ __forceinline__ static Lv bp(const Beta& b) { return b.x; }
+  __device__ __forceinline__ static Lv bm(const Beta& b) { return b.y; }
+  __device__ __forceinline__ static Beta pack(Lv p, Lv m) { return make_double2(p, m); }
+  __device__ __forceinline__ static Lv none() { return kNone; }
+  __device__ __forceinline__ static bool valid(Lv a) { return a > 0.5 * kNone; }
+  __device__ __forceinline__ static double ex2(double x) { return exp2(x); }
+  __device__ __forceinline__ static double lg2(double x) { return log2(x); }
+  __device__ __forceinline__ static double lg2_acc(double x) { return log2(x); }
+  __device__ __forceinline__ static double diff(Lv a, Lv b) { return a - b; }
+  __device__ __forceinline__ static double sum_minus(Lv a, Lv b, Lv c, double k) { return ((a + b) + k) - c; }
+  __device__ __forceinline__ static double mant_exp(double s, double& m) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const int ex = (int)((b >> 52) & 0x7ffull);
+    m = ex ? __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull)) : 0.0;
+    return ex ? (double)(ex - 1023) : 0.0;
+  }
+  __device__ __forceinline__ static Lv zero() { return 0.0; }
+  __device__ __forceinline__ static double hi(Lv a) { return a; }
+  __device__ __forceinline__ static Lv sub(Lv a, double t) { return a - t; }
+  __device__ __forceinline__ static Lv sub_fast(Lv a, double t) { return a - t; }
+  __device__ __forceinline__ static double to_double(Lv a) { return a; }
+  __device__ __forceinline__ static Beta make_beta(double b, double z) {
+    if (!(b > -INFINITY)) return make_double2(kNone, kNone);
+    return make_double2(b + z, b - z);
+  }
+  __device__ __forceinline__ static void put(double* p, Lv M, double s) { p[0] = M; p[1] = s; }
+  __device__ __forceinline__ static void get(const double* p, Lv& M, double& s) {
+    M = __ldcg(p);
+    s = __ldcg(p + 1);
+  }
+  __device__ __forceinline__ static void get_s(const double* p, Lv& M, double& s) {
+    M = p[0];
+    s = p[1];
+  }
+  __device__ __forceinline__ static Lv shfl_up(Lv a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
+  __device__ __forceinline__ static Lv shfl_down(Lv a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+};
+
+// log-sum state: value s * 2^M (s = 0: empty)
+template <class R>
+struct St {
+  typename HT<R>::Lv M;
+  R s;
+};
+
+template <class R>
+__device__ __forceinline__ St<R> st_empty() {
+  return {HT<R>::none(), R(0)};
+}
+
+// a (+) b
+template <class R>
+__device__ __forceinline__ St<R> st_comb(const St<R>& a, const St<R>& b) {
+  using H = HT<R>;
+  const R d = H::diff(b.M, a.M);
+  const bool gt = d > R(0);
+  const R e = H::ex2(-fabs(d));
+  St<R> r;
+  r.s = gt ? fma(a.s, e, b.s) : fma(b.s, e, a.s);
+  r.M = gt ? b.M : a.M;
+  return r;
+}
+
+// a (+) 2^lv (lv = none adds nothing)
+template <class R>
+__device__ __forceinline__ void st_term(St<R>& a, typename HT<R>::Lv lv) {
+  using H = HT<R>;
+  const R d = H::diff(lv, a.M);
+  const bool gt = d > R(0);
+  const R e = H::ex2(-fabs(d));
+  a.s = gt ? fma(a.s, e, R(1)) : a.s + e;
+  a.M = gt ? lv : a.M;
+}
+
+template <class R>
+__device__ __forceinline__ St<R> st_shfl_up(const St<R>& a, int o) {
+  return {HT<R>::shfl_up(a.M, o), __shfl_up_sync(0xffffffffu, a.s, o)};
+}
+template <class R>
+__device__ __forceinline__ St<R> st_shfl_down(const St<R>& a, int o) {
+  return {HT<R>::shfl_down(a.M, o), __shfl_down_sync(0xffffffffu, a.s, o)};
+}
+
+template <class R>
+struct HalfArgs {
+  using Beta = typename HT<R>::Beta;
+  const uint32_t* tbits;   // merged type bits (bit set = x point)
+  const int32_t* tile_x0;  // C + 1: x points before each tile
+  int64_t L;               // merged points
+  int C;                   // tiles
+  int o_is_x;              // 1: outputs at x (K psi), 0: outputs at y (K^T phi)
+  const Beta* bO;          // O levels (frames)
+  const typename HT<R>::Lv* lmO;   // O log2 masses (none for a zero mass); H_POT / H_ERR
+  Beta* bO_out;            // new O levels (H_POT)
+  const Beta* bW;          // W levels
+  double* out;             // H_LOG / H_LIN: per O point
+  const R* carry_in;       // 2 kSt per tile: forward state entering it | backward state entering it
+  R* agg_out;              // 2 kSt per tile: tile aggregates (forward beta+ | backward beta-)
+  R* carry_out;            // 2 kSt per tile: carries of the target application (last CTA)
+  double* part;            // per tile: partial error sum
+  double* scal;            // [0] error of the last check
+  int32_t* ctrl;           // [0] ticket [1] done [2] iteration [3] iterations at exit [4] converged
+  double tol;
+  int64_t maxit;
+  // H_RAW: W levels from rawW (cost units) at positions posW, O frames 0 at
+  // posO, and the output ln of the product plus rawO / eps
+  const double* rawW;
+  const double* rawO;
+  const double* posW;
+  const double* posO;
+  double scale;       // 1 / (eps ln 2)
+  double inv_eps;
+};
+
+constexpr int kHSlots = kThreads + kThreads / 32;
+__device__ __forceinline__ int hslot(int t) { return t + (t >> 5); }
+
+template <class R, int E>
+struct HalfSmem {
+  using Lv = typename HT<R>::Lv;
+  static constexpr int T = E * kThreads;
+  Lv pfM[T];      // W phase: running prefix states of the owning thread (levels ...
+  R pfs[T];       //   ... and mantissas)
+  Lv sfM[T];      // running suffix states
+  R sfs[T];
+  Lv slM[2][kHSlots];   // per thread: run totals, then entry states ([0] forward, [1] backward)
+  R sls[2][kHSlots];
+  int16_t zl[T];        // per O point of the tile: W points of the tile before it
+  uint8_t own[T];       // per W point of the tile: the thread whose run holds it
+  double red[kThreads / 32];
+  int iscan[kThreads / 32];
+  int last;
+  typename HT<R>::Lv totM;   // launch tail: the running carry of a chunk of tiles
+  R tots;
+};
+
+
+template <class R, int E>
+__device__ __forceinline__ void hslot_put(HalfSmem<R, E>& sm, int dir, int t, const St<R>& a) {
+  sm.slM[dir][hslot(t)] = a.M;
+  sm.sls[dir][hslot(t)] = a.s;
+}
+template <class R, int E>
+__device__ __forceinline__ St<R> hslot_get(const HalfSmem<R, E>& sm, int dir, int t) {
+  return {sm.slM[dir][hslot(t)], sm.sls[dir][hslot(t)]};
+}
+
+constexpr int kHPer = kThreads / 32;   // slots raked per lane
+
+// Warps 0 (forward) and 1 (backward): turn the kThreads run totals in the
+// slots into entry states: forward, the carry cf and the totals of threads
+// 0 .. t-1; backward, the carry cb and the totals of threads t+1 .. end.
+template <class R, int E>
+__device__ __forceinline__ void hrake_scan(HalfSmem<R, E>& sm, const St<R>& cf, const St<R>& cb) {
+  const int lane = threadIdx.x & 31;
+  const int dir = threadIdx.x >> 5;   // 0 or 1
+  St<R> f = st_empty<R>();
+#pragma unroll
+  for (int k = 0; k < kHPer; ++k) f = st_comb(f, hslot_get(sm, dir, lane * kHPer + k));
+  if (dir == 0) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const St<R> u = st_shfl_up(f, o);
+      if (lane >= o) f = st_comb(u, f);
+    }
+    St<R> ex = st_shfl_up(f, 1);
+    if (lane == 0) ex = st_empty<R>();
+    St<R> st = st_comb(cf, ex);
+#pragma unroll
+    for (int k = 0; k < kHPer; ++k) {
+      const St<R> a = hslot_get(sm, 0, lane * kHPer + k);
+      hslot_put(sm, 0, lane * kHPer + k, st);
+      st = st_comb(st, a);
+    }
+  } else {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const St<R> u = st_shfl_down(f, o);
+      if (lane + o < 32) f = st_comb(u, f);
+    }
+    St<R> ex = st_shfl_down(f, 1);
+    if (lane == 31) ex = st_empty<R>();
+    St<R> st = st_comb(cb, ex);
+#pragma unroll
+    for (int k = kHPer - 1; k >= 0; --k) {
+      const St<R> a = hslot_get(sm, 1, lane * kHPer + k);
+      hslot_put(sm, 1, lane * kHPer + k, st);
+      st = st_comb(st, a);
+    }
+  }
+}
+
+// Warps 0 and 1: log-sum of the kThreads partial states of slot direction 0
+// (warp 0) and 1 (warp 1); lane 0 stores it at out + dir * kSt.
+template <class R, int E>
+__device__ __forceinline__ void hrake_reduce(HalfSmem<R, E>& sm, R* out) {
+  const int lane = threadIdx.x & 31;
+  const int dir = threadIdx.x >> 5;
+  St<R> f = st_empty<R>();
+#pragma unroll
+  for (int k = 0; k < kHPer; ++k) f = st_comb(f, hslot_get(sm, dir, lane * kHPer + k));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f = st_comb(f, st_shfl_down(f, o));
+  if (lane == 0) HT<R>::put(out + dir * HT<R>::kSt, f.M, f.s);
+}
+
+
+// Warp dir (0: forward, 1: backward) alone: exclusive scan of the run
+// totals in slot direction dir, seeded with seed; the slots receive the entry
+// states and (totM, tots) the log-sum of seed and every slot.
+template <class R, int E, int dir>
+__device__ __forceinline__ void hrake_one(HalfSmem<R, E>& sm, const St<R>& seed) {
+  const int lane = threadIdx.x & 31;
+  St<R> f = st_empty<R>();
+#pragma unroll
+  for (int k = 0; k < kHPer; ++k) f = st_comb(f, hslot_get(sm, dir, lane * kHPer + k));
+  if (dir == 0) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const St<R> u = st_shfl_up(f, o);
+      if (lane >= o) f = st_comb(u, f);
+    }
+  } else {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const St<R> u = st_shfl_down(f, o);
+      if (lane + o < 32) f = st_comb(u, f);
+    }
+  }
+  St<R> ex = dir == 0 ? st_shfl_up(f, 1) : st_shfl_down(f, 1);
+  if (lane == (dir == 0 ? 0 : 31)) ex = st_empty<R>();
+  if (lane == (dir == 0 ? 31 : 0)) {
+    const St<R> t = st_comb(seed, f);
+    sm.totM = t.M;
+    sm.tots = t.s;
+  }
+  St<R> st = st_comb(seed, ex);
+#pragma unroll
+  for (int kk = 0; kk < kHPer; ++kk) {
+    const int k = dir == 0 ? kk : kHPer - 1 - kk;
+    const St<R> a = hslot_get(sm, dir, lane * kHPer + k);
+    hslot_put(sm, dir, lane * kHPer + k, st);
+    st = st_comb(st, a);
+  }
+}
+
+// S - 1 for S = 2^x without the cancellation near x = 0 (branch-free)
+template <class R>
+__device__ __forceinline__ R pow2m1(R x) {
+  const R t = x * R(0.69314718055994530942);
+  const R p = t * (R(1) + t * (R(0.5) + t * (R(1.0 / 6) + t * R(1.0 / 24))));
+  const R q = HT<R>::ex2(x) - R(1);
+  return (fabs(t) < R(0.03)) ? p : q;
+}
+
+// One tile of a launch: steps 1-3 of the header comment.  Returns false when
+// the loop is already done (the launch does nothing).  Per-thread runs have a
+// fixed trip count E; indices past a thread's run are clamped to a valid
+// point of the tile and its contributions masked, so the loops do not branch.
+template <class R, int kFlags, int E>
+__device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int unit, bool first) {
+  using H = HT<R>;
+  using Lv = typename H::Lv;
+  using Beta = typename H::Beta;
+  constexpr int kT = E * kThreads;
+  constexpr bool kAgg = (kFlags & H_AGG) != 0;
+  constexpr bool kProd = (kFlags & (H_LOG | H_LIN)) != 0;
+  constexpr bool kDiv = (kFlags & (H_POT | H_ERR)) != 0;
+  const int tid = threadIdx.x;
+
+  const int x0 = a.tile_x0[unit], x1 = a.tile_x0[unit + 1];
+  const int64_t k0 = (int64_t)unit * kT;
+  const int64_t kend = min(k0 + (int64_t)kT, a.L);
+  const int y0 = (int)(k0 - x0), y1 = (int)(kend - x1);
+  const int o_start = a.o_is_x ? x0 : y0;
+  const int n_o = a.o_is_x ? (x1 - x0) : (y1 - y0);
+  const int w_start = a.o_is_x ? y0 : x0;
+  const int n_w = a.o_is_x ? (y1 - y0) : (x1 - x0);
+  const Beta* bO = a.bO + o_start;
+  const Beta* bW = a.bW + w_start;
+
+  // 1. local dividing index of the O points of this thread's merged points
+  if (!kAgg) {
+    const int64_t seg = k0 + (int64_t)tid * E;
+    uint32_t omask = 0;
+    if (seg < a.L) {
+      const int64_t nv = a.L - seg;
+      const uint32_t vmask = nv >= E ? ((1u << E) - 1u) : ((1u << nv) - 1u);
+      const uint32_t bits = (a.tbits[seg >> 5] >> (seg & 31)) & ((1u << E) - 1u);
+      omask = (a.o_is_x ? bits : ~bits) & vmask;
+    }
+    int r = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((omask >> e) & 1u) sm.zl[r] = (int16_t)(tid * E + e - r);
+      r += (omask >> e) & 1u;
+    }
+  }
+  if (first) {
+    griddep_wait();
+    if ((kFlags & H_CHECK_DONE) && *(volatile int32_t*)(a.ctrl + 1)) return false;
+    griddep_launch_dependents();
+  }
+
+  // 2. W phase: running log-sums over this thread's W run
+  const int wlo = (int)(((int64_t)tid * n_w) / kThreads);
+  const int qw = (int)(((int64_t)(tid + 1) * n_w) / kThreads) - wlo;
+  const int wlast = max(n_w - 1, 0);
+  // longest run of the tile (block-uniform trip count)
+  const int qwm = (n_w + kThreads - 1) / kThreads;
+  St<R> tf = st_empty<R>(), tb = st_empty<R>();
+  if (n_w > 0) {
+    Beta bw[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (e < qwm) {
+        const int i = min(wlo + e, wlast);
+        if constexpr ((kFlags & H_RAW) != 0) {
+          bw[e] = H::make_beta(a.rawW[w_start + i] * a.scale, a.posW[w_start + i] * a.scale);
+        } else {
+          bw[e] = bW[i];
+        }
+      }
+    }
+    if constexpr (kAgg) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (e < qwm) {
+          const bool v = e < qw;
+          st_term(tf, v ? H::bp(bw[e]) : H::none());
+          st_term(tb, v ? H::bm(bw[e]) : H::none());
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (e < qwm) {
+          const bool v = e < qw;
+          st_term(tf, v ? H::bp(bw[e]) : H::none());
+          if (v) {
+            sm.pfM[wlo + e] = tf.M;
+            sm.pfs[wlo + e] = tf.s;
+            sm.own[wlo + e] = (uint8_t)tid;
+          }
+        }
+      }
+#pragma unroll
+      for (int e = E - 1; e >= 0; --e) {
+        if (e < qwm) {
+          const bool v = e < qw;
+          st_term(tb, v ? H::bm(bw[e]) : H::none());
+          if (v) {
+            sm.sfM[wlo + e] = tb.M;
+            sm.sfs[wlo + e] = tb.s;
+          }
+        }
+      }
+    }
+  }
+  if constexpr (kAgg) {
+    hslot_put(sm, 0, tid, tf);
+    hslot_put(sm, 1, tid, tb);
+    __syncthreads();
+    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * (int64_t)unit);
+    return true;
+  }
+  else {
+  // O run: levels and log masses, requested now so that their latency
+  // overlaps the scan of the run totals
+  const int olo = (int)(((int64_t)tid * n_o) / kThreads);
+  const int qo = (int)(((int64_t)(tid + 1) * n_o) / kThreads) - olo;
+  const int olast = max(n_o - 1, 0);
+  const int qom = (n_o + kThreads - 1) / kThreads;
+  Beta bo[E];
+  Lv lm[E];
+  if (n_o > 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (e < qom) {
+        const int j = min(olo + e, olast);
+        if constexpr ((kFlags & H_RAW) != 0) bo[e] = H::make_beta(0.0, a.posO[o_start + j] * a.scale);
+        else bo[e] = bO[j];
+        if constexpr (kDiv) lm[e] = a.lmO[o_start + j];
+      }
+    }
+  }
+  St<R> cf = st_empty<R>(), cb = st_empty<R>();
+  if (a.carry_in) {
+    const R* c = a.carry_in + 2 * H::kSt * (int64_t)unit;
+    H::get(c, cf.M, cf.s);
+    H::get(c + H::kSt, cb.M, cb.s);
+  }
+  hslot_put(sm, 0, tid, tf);
+  hslot_put(sm, 1, tid, tb);
+  __syncthreads();
+  if (tid < 64) hrake_scan(sm, cf, cb);
+  __syncthreads();
+
+  // 3. O phase
+  R err = R(0);
+  St<R> nf = st_empty<R>(), nb = st_empty<R>();
+  if (n_o > 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (e >= qom) break;
+      const bool v = e < qo;
+      const int j = min(olo + e, olast);
+      const int z = sm.zl[j];
+      // forward: the W points before z (entry of the owner of W point z-1
+      // and its local prefix); backward: the W points from z on
+      const int i1 = max(z - 1, 0), i2 = min(z, wlast);
+      const St<R> Fo = st_comb(hslot_get(sm, 0, sm.own[i1]), St<R>{sm.pfM[i1], sm.pfs[i1]});
+      const St<R> Bo = st_comb(hslot_get(sm, 1, sm.own[i2]), St<R>{sm.sfM[i2], sm.sfs[i2]});
+      const St<R> F = z > 0 ? Fo : cf;
+      const St<R> B = z < n_w ? Bo : cb;
+      const Lv op = H::bp(bo[e]), om = H::bm(bo[e]);
+      if constexpr (kProd) {
+        // ln of p + q with the O frame 0 (levels +-Z), in float64
+        const double a1 = H::to_double(F.M) + H::to_double(om);
+        const double a2 = H::to_double(B.M) + H::to_double(op);
+        const bool g1 = a1 >= a2;
+        const double big = g1 ? a1 : a2;
+        const R d = (R)(g1 ? a2 - a1 : a1 - a2);
+        const R sb = g1 ? F.s : B.s, so = g1 ? B.s : F.s;
+        const bool none = !(sb > R(0)) || big < 0.5 * (double)H::kNone;
+        const double l2 = big + (double)H::lg2_acc(fma(so, H::ex2(d), sb));
+        double val;
+        if constexpr ((kFlags & H_LOG) != 0) val = none ? -INFINITY : 0.69314718055994530942 * l2;
+        else val = none ? 0.0 : exp2(l2);
+        if constexpr ((kFlags & H_RAW) != 0) val += a.rawO[o_start + j] * a.inv_eps;
+        if (v) a.out[o_start + j] = val;
+      } else {
+        const bool has_mass = H::valid(lm[e]);
+        const Lv c = has_mass ? lm[e] : H::zero();
+        // delta = log2 S - c, S = 2^{beta-} P + 2^{beta+} Q; the binary
+        // exponents of the mantissa sums join the level sums before rounding,
+        // so the dominant part is near 0 and keeps full float precision
+        R m1, m2;
+        const R k1 = H::mant_exp(F.s, m1), k2 = H::mant_exp(B.s, m2);
+        const R a1 = H::sum_minus(F.M, om, c, k1);
+        const R a2 = H::sum_minus(B.M, op, c, k2);
+        const R dd = a1 - a2;
+        const bool g1 = dd > R(0);
+        const R ed = H::ex2(-fabs(dd));
+        const R big = g1 ? a1 : a2;
+        const R mb = g1 ? m1 : m2, mo = g1 ? m2 : m1;
+        const R delta = big + H::lg2_acc(fma(mo, ed, mb));
+        if constexpr ((kFlags & H_ERR) != 0) {
+          const R term = has_mass ? H::ex2(H::hi(lm[e])) * fabs(pow2m1(delta)) : H::ex2(delta);
+          err += v ? term : R(0);
+        }
+        if constexpr ((kFlags & H_POT) != 0) {
+          const bool ok = v && has_mass && delta > R(0.5) * H::kNone;
+          const Lv np = ok ? H::sub_fast(op, delta) : H::none();
+          const Lv nm = ok ? H::sub_fast(om, delta) : H::none();
+          if (v) a.bO_out[o_start + j] = H::pack(np, nm);
+          if constexpr ((kFlags & H_NEXT) != 0) {
+            // the tile aggregate of the next application (new levels)
+            st_term(nf, np);
+            st_term(nb, nm);
+          }
+        }
+      }
+    }
+  }
+
+  if constexpr ((kFlags & H_ERR) != 0) {
+    const double e64 = warp_sum((double)err);
+    if ((tid & 31) == 0) sm.red[tid >> 5] = e64;
+  }
+  __syncthreads();   // the entry states in the slots are no longer read
+  if constexpr ((kFlags & H_ERR) != 0) {
+    if (tid == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
+      a.part[unit] = tot;
+    }
+  }
+  if constexpr ((kFlags & H_NEXT) != 0) {
+    hslot_put(sm, 0, tid, nf);
+    hslot_put(sm, 1, tid, nb);
+    __syncthreads();
+    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * (int64_t)unit);
+  }
+  return true;
+  }
+}
+
+// Last CTA, one direction: carries of every tile from the tile aggregates
+// (forward: the log-sum of the tiles before it; backward: of the tiles after
+// it).  Chunks of E tiles per thread are staged in the (now free) prefix
+// arrays with coalesced loads; the state leaving a chunk enters the next.
+template <class R, int E, int dir>
+__device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
+  using H = HT<R>;
+  constexpr int kS = H::kSt;
+  constexpr int kQ = E;                     // tiles per thread per chunk
+  constexpr int K = kQ * kThreads;          // tiles per chunk
+  static_assert(sizeof(sm.pfM) + sizeof(sm.pfs) >= sizeof(R) * kS * K, "staging");
+  R* buf = reinterpret_cast<R*>(sm.pfM);    // pfM, pfs (adjacent): kS values per tile
+  const int tid = threadIdx.x;
+  const int C = a.C;
+  const int nch = (C + K - 1) / K;
+  St<R> run = st_empty<R>();
+#pragma unroll 1
+  for (int ci = 0; ci < nch; ++ci) {
+    const int ch = dir == 0 ? ci : nch - 1 - ci;
+    const int c0 = ch * K, nq = min(K, C - c0);
+    __syncthreads();
+#pragma unroll 1
+    for (int i = tid; i < kS * nq; i += kThreads) {
+      const int t = i / kS, d = i - t * kS;
+      buf[i] = __ldcg(a.agg_out + 2 * kS * (int64_t)(c0 + t) + dir * kS + d);
+    }
+    __syncthreads();
+    const int j0 = tid * kQ;
+    St<R> f = st_empty<R>();
+#pragma unroll 1
+    for (int k = 0; k < kQ; ++k) {
+      const int j = j0 + k;
+      if (j < nq) {
+        St<R> u;
+        H::get_s(buf + kS * j, u.M, u.s);
+        f = st_comb(f, u);
+      }
+    }
+    hslot_put(sm, dir, tid, f);
+    __syncthreads();
+    if ((tid >> 5) == dir) hrake_one<R, E, dir>(sm, run);
+    __syncthreads();
+    St<R> st = hslot_get(sm, dir, tid);
+#pragma unroll 1
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int k = dir == 0 ? kk : kQ - 1 - kk;
+      const int j = j0 + k;
+      if (j < nq) {
+        H::put(a.carry_out + 2 * kS * (int64_t)(c0 + j) + dir * kS, st.M, st.s);
+        St<R> u;
+        H::get_s(buf + kS * j, u.M, u.s);
+        st = st_comb(st, u);
+      }
+    }
+    run = {sm.totM, sm.tots};
+  }
+}
+
+// Last CTA: carries of the next launch, the float64 error sum, the loop
+// control.  Runs once per launch on one SM: loops stay rolled.
+template <class R, int kFlags, int E>
+__device__ void half_finish(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int units) {
+  const int tid = threadIdx.x;
+  double ep = 0.0;
+  if (kFlags & H_ERR) {
+#pragma unroll 1
+    for (int i = tid; i < units; i += kThreads) ep += __ldcg(a.part + i);
+  }
+  if (kFlags & (H_NEXT | H_AGG)) {
+    half_carries<R, E, 0>(a, sm);
+    half_carries<R, E, 1>(a, sm);
+  }
+  double errsum = 0.0;
+  if (kFlags & H_ERR) {
+    ep = warp_sum(ep);
+    __syncthreads();
+    if ((tid & 31) == 0) sm.red[tid >> 5] = ep;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) errsum += sm.red[w];
+  }
+  if (tid == 0) {
+    int32_t* c = a.ctrl;
+    if (kFlags & H_ERR) {
+      a.scal[0] = errsum;
+      if (errsum <= a.tol) {
+        c[1] = 1;
+        c[3] = c[2];
+        c[4] = 1;
+      }
+    }
+    if ((kFlags & H_ITER_END) && !c[1]) {
+      c[2] += 1;
+      if ((int64_t)c[2] >= a.maxit) {
+        c[1] = 1;
+        c[3] = c[2];
+      }
+    }
+    c[0] = 0;
+  }
+}
+
+template <class R, int E>
+__device__ __forceinline__ bool half_last_cta(int32_t* ticket, int G, HalfSmem<R, E>& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int t = atomicAdd(ticket, 1);
+    sm.last = (t == G - 1);
+  }
+  __syncthreads();
+  if (sm.last) __threadfence();
+  return sm.last != 0;
+}
+
+// resident CTAs per SM the registers are budgeted for (float32)
+#ifndef FINOM_HALF_MINB8
+#define FINOM_HALF_MINB8 2
+#endif
+template <class R, int E>
+constexpr int half_min_blocks() {
+  return sizeof(R) != 4 ? 1 : (E >= 8 ? FINOM_HALF_MINB8 : (E == 4 ? 3 : 4));
+}
+
+// Persistent CTAs: CTA b handles the tiles b, b + G, b + 2G, ... (G = grid
+// size); the last CTA to finish (ticket ctrl[0]) runs half_finish.
+template <class R, int kFlags, int E>
+__global__ void __launch_bounds__(kThreads, half_min_blocks<R, E>()) k_half(HalfArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  HalfSmem<R, E>& sm = *reinterpret_cast<HalfSmem<R, E>*>(smem_raw);
+  const int units = a.C;
+  for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    if (!half_unit<R, kFlags, E>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
+    __syncthreads();
+  }
+  griddep_wait();   // (a no-op after the first unit's wait)
+  if (half_last_cta<R, E>(a.ctrl, (int)gridDim.x, sm)) half_finish<R, kFlags, E>(a, sm, units);
+}
+
+}  // namespace finom

@@ -67,4 +67,7 @@ def test_time_to_error_trace(lib, prec):
     assert np.all(np.diff(ms) > 0)
     for l, e in zip(its, err):
         _, _, it, eo = serial_c.sinkhorn(pr.x, pr.y, pr.u, pr.v, pr.eps, 0.0, int(l))
-        assert e == pytest.approx(eo, rel=1e-7 if prec == "f64" else 2e-3, abs=1e-13 if prec == "f64" else 2e-6)
+        # float32: the loop's own check in float32 (mantissa sums of the scans,
+        # ~2e-4 relative) plus the float32 iterate's noise (ex2 relative error
+        # 2^-22.5, at most ~1.2e-7 of marginal error)
+        assert e == pytest.approx(eo, rel=1e-7 if prec == "f64" else 2e-4, abs=1e-13 if prec == "f64" else 2e-7)

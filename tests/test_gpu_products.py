@@ -20,15 +20,6 @@ pytestmark = pytest.mark.gpu
 TOL = {"f64": 1e-12, "f32_log": 1e-5}
 
 
-def f32_gap_bound(x, y, eps):
-    """FP32 plans keep gaps and the partial sums of the log-decays inside one
-    thread's points in float32; when one gap is G bits long those partial sums
-    reach G and carry a few ulps of it (4 ulp = 2.4e-7 G) into the log-sum.
-    The 1e-5 acceptance therefore applies while the largest gap stays below
-    ~40 bits; coarser meshes get this bound."""
-    z = np.sort(np.concatenate([x, y]))
-    gmax = float(np.max(np.diff(z))) / (eps * math.log(2.0)) if len(z) > 1 else 0.0
-    return max(TOL["f32_log"], 2.4e-7 * gmax)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (7, 3), (1000, 1048), (2047, 1), (2049, 2047), (3000, 2500),
@@ -81,7 +72,7 @@ def test_kv_ktu_linear(lib, prec, kind, N, M, eps):
     u = g.uniform(0, 1, N)
     p = lib.finom_plan(T(x), T(y), eps, prec)
     C = dense.cost_1d(x, y)
-    tol = TOL[prec] if prec == "f64" else f32_gap_bound(x, y, eps)
+    tol = TOL[prec]
     assert relerr(H(lib.finom_kv(p, T(v))), dense.kv_dense(C, v, eps)) <= tol
     assert relerr(H(lib.finom_ktu(p, T(u))), dense.ktu_dense(C, u, eps)) <= tol
 
@@ -106,7 +97,7 @@ def test_kv_log_stabilised(lib, prec, N, M, eps):
     C = dense.cost_1d(x, y)
     got = H(lib.finom_kv_log(p, T(a), T(b)))
     want = dense.log_apply_dense(C, a, b, eps)
-    tol = TOL[prec] if prec == "f64" else f32_gap_bound(x, y, eps)
+    tol = TOL[prec]
     # relative error of exp(out) = absolute error of out
     assert np.max(np.abs(got - want)) <= tol
     got_t = H(lib.finom_ktu_log(p, T(a), T(b)))

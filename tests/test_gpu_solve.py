@@ -32,6 +32,14 @@ def _pos(f, m):
 
 
 LOCK_TOL = {"f64": 1e-10, "f32_log": 2e-5}   # |f_gpu - f_oracle| / eps on points with mass
+# Float32 log-domain iterates: the mantissa sums of the scans take 2^d from
+# the float32 ex2 instruction, whose relative error is at most 2^-22.5
+# (1.7e-7); a point whose sum carries that error in full (one weight point,
+# N = 1) has its weight, and so the marginal error, off by up to ~1.2e-7.
+# Over many points the errors average out (a few 1e-9 measured at N = 500),
+# and 2e-4 of the error itself covers the float32 check of the loop.  The
+# bound stays at 0.2 tol for tol = 1e-6.
+F32_ERR_REL, F32_ERR_ABS = 2e-4, 2e-7
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
@@ -53,9 +61,12 @@ def test_lockstep_with_oracle(lib, prec, maxit, N, M, kind, eps):
     assert np.max(np.abs(_pos(H(f), u) - _pos(fo, u))) / eps <= LOCK_TOL[prec]
     assert np.max(np.abs(_pos(H(g), v) - _pos(go, v))) / eps <= LOCK_TOL[prec]
     assert np.all(np.isneginf(H(f)[u == 0])) and np.all(np.isneginf(H(g)[v == 0]))
-    # FP32 log-domain potentials carry a marginal-error floor of a few 1e-7
-    assert res["marginal_err"] == pytest.approx(err, rel=1e-6 if prec == "f64" else 1e-3,
-                                                abs=1e-9 if prec == "f64" else 2e-6)
+    # the float64 marginal error of the returned potentials against the
+    # oracle's at the same iteration; float32 potentials add at most F32_ERR_ABS
+    if prec == "f64":
+        assert res["marginal_err"] == pytest.approx(err, rel=1e-6, abs=1e-12)
+    else:
+        assert abs(res["marginal_err"] - err) <= F32_ERR_REL * err + F32_ERR_ABS
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
@@ -89,6 +100,10 @@ def test_converged_matches_oracle(lib, prec, tol, N, M, kind, eps):
     else:
         assert abs(res["iters"] - it) <= max(3, 0.02 * it)
         assert res["w1"] == pytest.approx(w1o, rel=1e-4)
+        # the float32 loop's own check at its stop (the loop head of iteration
+        # l) against the oracle's error at the same loop head: within 0.2 tol
+        _, _, _, err_l = serial_c.sinkhorn(x, y, u, v, eps, 0.0, res["iters"])
+        assert abs(res["marginal_err_loop"] - err_l) <= 0.2 * tol
     # float64 marginal error of the returned potentials, recomputed by the oracle
     e_or = serial_c.marginal_error(x, y, eps, H(f), H(g), v)
     assert e_or <= (tol if prec == "f64" else 3 * tol)
@@ -114,7 +129,7 @@ def test_config1_fp64_workload(lib, prec):
         assert np.max(np.abs(H(f) - fo)) / pr.eps <= 1e-9
     else:
         assert res["w1"] == pytest.approx(w1o, rel=1e-4)
-        assert res["marginal_err"] == pytest.approx(err, rel=2e-2)
+        assert abs(res["marginal_err"] - err) <= F32_ERR_REL * err + F32_ERR_ABS
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])

@@ -12,7 +12,6 @@ import numpy as np
 import pytest
 
 from oracle import dense, serial_c
-from tests.test_gpu_products import f32_gap_bound
 from tests.gpu_util import H, T, meshes, relerr
 
 pytestmark = pytest.mark.gpu
@@ -37,7 +36,7 @@ def test_products_every_tile_size(lib, prec, E, N, M, kind):
     v[g.random(M) < 0.05] = 0.0
     u = g.uniform(0, 1, N)
     C = dense.cost_1d(x, y)
-    tol = TOL[prec] if prec == "f64" else f32_gap_bound(x, y, eps)
+    tol = TOL[prec]
     assert relerr(H(lib.finom_kv(p, T(v))), dense.kv_dense(C, v, eps)) <= tol
     assert relerr(H(lib.finom_ktu(p, T(u))), dense.ktu_dense(C, u, eps)) <= tol
     a = 0.3 * eps * np.sin(7 * x)

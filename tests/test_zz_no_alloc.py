@@ -1,15 +1,18 @@
-"""The allocation-free product finom_kv_log_noalloc against finom_kv_log.
+"""The allocation-free product finom_kv_log_noalloc against finom_kv_log and
+against the CPU oracle.
 
 Some callers cannot allocate device memory while they run (memory owned by a
 fixed pool or another allocator, a hard budget, no tolerance for allocator
 locks).  finom_kv_log_noalloc serves them from a static device array; this
 file checks, through the C ABI, that two calls in a row give the product that
-finom_kv_log gives, and that plans beyond the array's limit are refused.
+finom_kv_log gives and the dense definition of the oracle, for smooth and for
+rough absorption vectors, and that plans beyond the array's limit are refused.
 Collected last on purpose (test_zz_*), so a failure here does not hide others.
 """
 import numpy as np
 import pytest
 
+from oracle import dense
 from tests.gpu_util import H, T, meshes
 
 pytestmark = pytest.mark.gpu
@@ -36,6 +39,26 @@ def test_noalloc_matches_kv_log_twice(lib, prec, N, M, eps):
     want = H(lib.finom_kv_log(p, ta, tb))
     for _ in range(2):   # the static scratch keeps the previous call's contents
         got = H(lib.finom_kv_log_noalloc(p, ta, tb))
+        assert np.max(np.abs(got - want)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32_log", "f64"])
+@pytest.mark.parametrize("rough", [False, True])
+@pytest.mark.parametrize("N,M,eps", [(3000, 2500, 0.01), (700, 2200, 0.003), (1, 7, 0.05)])
+def test_noalloc_matches_oracle(lib, prec, rough, N, M, eps):
+    """Against the dense definition (oracle), smooth absorption vectors and
+    rough ones whose neighbouring entries jump by several eps."""
+    x, y = meshes("uniform_random", N, M, 3 * N + M)
+    a, b = _potentials(x, y, eps, N + 7 * M)
+    if rough:
+        g = np.random.default_rng(N * M)
+        a = a + eps * g.uniform(-6, 6, N)
+        b = b + eps * g.uniform(-6, 6, M)
+    p = lib.finom_plan(T(x), T(y), eps, prec)
+    want = dense.log_apply_dense(dense.cost_1d(x, y), a, b, eps)
+    for _ in range(2):
+        got = H(lib.finom_kv_log_noalloc(p, T(a), T(b)))
+        # relative error of exp(out) = absolute error of out
         assert np.max(np.abs(got - want)) <= TOL[prec]
 
 
