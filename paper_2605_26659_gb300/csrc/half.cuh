@@ -118,6 +118,8 @@ struct HT<float> {
   }
   __device__ __forceinline__ static Lv zero() { return make_float2(0.f, 0.f); }
   __device__ __forceinline__ static float hi(Lv a) { return a.x; }
+  __device__ __forceinline__ static float lo(Lv a) { return a.y; }
+  __device__ __forceinline__ static Lv mk(float h, float l) { return make_float2(h, l); }
   // a - t as a renormalised pair
   __device__ __forceinline__ static Lv sub(Lv a, float t) {
     const float s = a.x - t;
@@ -186,6 +188,8 @@ struct HT<double> {
   }
   __device__ __forceinline__ static Lv zero() { return 0.0; }
   __device__ __forceinline__ static double hi(Lv a) { return a; }
+  __device__ __forceinline__ static double lo(Lv) { return 0.0; }
+  __device__ __forceinline__ static Lv mk(double h, double) { return h; }
   __device__ __forceinline__ static Lv sub(Lv a, double t) { return a - t; }
   __device__ __forceinline__ static Lv sub_fast(Lv a, double t) { return a - t; }
   __device__ __forceinline__ static double to_double(Lv a) { return a; }
@@ -293,7 +297,11 @@ struct HalfSmem {
   R pfs[T];       //   ... and mantissas)
   Lv sfM[T];      // running suffix states
   R sfs[T];
-  Lv slM[2][kHSlots];   // per thread: run totals, then entry states ([0] forward, [1] backward)
+  // per thread: run totals, then entry states ([0] forward, [1] backward);
+  // level hi / lo parts and mantissas as separate 4-byte arrays so that the
+  // raking lanes (8 consecutive slots each, padded) hit distinct banks
+  R slh[2][kHSlots];
+  R sll[2][kHSlots];
   R sls[2][kHSlots];
   int16_t zl[T];        // per O point of the tile: W points of the tile before it
   uint8_t own[T];       // per W point of the tile: the thread whose run holds it
@@ -307,12 +315,15 @@ struct HalfSmem {
 
 template <class R, int E>
 __device__ __forceinline__ void hslot_put(HalfSmem<R, E>& sm, int dir, int t, const St<R>& a) {
-  sm.slM[dir][hslot(t)] = a.M;
-  sm.sls[dir][hslot(t)] = a.s;
+  const int i = hslot(t);
+  sm.slh[dir][i] = HT<R>::hi(a.M);
+  if (sizeof(R) == 4) sm.sll[dir][i] = HT<R>::lo(a.M);
+  sm.sls[dir][i] = a.s;
 }
 template <class R, int E>
 __device__ __forceinline__ St<R> hslot_get(const HalfSmem<R, E>& sm, int dir, int t) {
-  return {sm.slM[dir][hslot(t)], sm.sls[dir][hslot(t)]};
+  const int i = hslot(t);
+  return {HT<R>::mk(sm.slh[dir][i], sizeof(R) == 4 ? sm.sll[dir][i] : R(0)), sm.sls[dir][i]};
 }
 
 constexpr int kHPer = kThreads / 32;   // slots raked per lane
@@ -475,85 +486,64 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   // 2. W phase: running log-sums over this thread's W run
   const int wlo = (int)(((int64_t)tid * n_w) / kThreads);
   const int qw = (int)(((int64_t)(tid + 1) * n_w) / kThreads) - wlo;
-  const int wlast = max(n_w - 1, 0);
-  // longest run of the tile (block-uniform trip count)
-  const int qwm = (n_w + kThreads - 1) / kThreads;
   St<R> tf = st_empty<R>(), tb = st_empty<R>();
-  if (n_w > 0) {
-    Beta bw[E];
+  auto wbeta = [&](int i) -> Beta {
+    if constexpr ((kFlags & H_RAW) != 0) {
+      return H::make_beta(a.rawW[w_start + i] * a.scale, a.posW[w_start + i] * a.scale);
+    } else {
+      return bW[i];
+    }
+  };
+  if constexpr (kAgg) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      if (e < qwm) {
-        const int i = min(wlo + e, wlast);
-        if constexpr ((kFlags & H_RAW) != 0) {
-          bw[e] = H::make_beta(a.rawW[w_start + i] * a.scale, a.posW[w_start + i] * a.scale);
-        } else {
-          bw[e] = bW[i];
-        }
+      if (e < qw) {
+        const Beta b = wbeta(wlo + e);
+        st_term(tf, H::bp(b));
+        st_term(tb, H::bm(b));
       }
     }
-    if constexpr (kAgg) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        if (e < qwm) {
-          const bool v = e < qw;
-          st_term(tf, v ? H::bp(bw[e]) : H::none());
-          st_term(tb, v ? H::bm(bw[e]) : H::none());
-        }
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        if (e < qwm) {
-          const bool v = e < qw;
-          st_term(tf, v ? H::bp(bw[e]) : H::none());
-          if (v) {
-            sm.pfM[wlo + e] = tf.M;
-            sm.pfs[wlo + e] = tf.s;
-            sm.own[wlo + e] = (uint8_t)tid;
-          }
-        }
-      }
-#pragma unroll
-      for (int e = E - 1; e >= 0; --e) {
-        if (e < qwm) {
-          const bool v = e < qw;
-          st_term(tb, v ? H::bm(bw[e]) : H::none());
-          if (v) {
-            sm.sfM[wlo + e] = tb.M;
-            sm.sfs[wlo + e] = tb.s;
-          }
-        }
-      }
-    }
-  }
-  if constexpr (kAgg) {
     hslot_put(sm, 0, tid, tf);
     hslot_put(sm, 1, tid, tb);
     __syncthreads();
     if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * (int64_t)unit);
     return true;
-  }
-  else {
-  // O run: levels and log masses, requested now so that their latency
-  // overlaps the scan of the run totals
-  const int olo = (int)(((int64_t)tid * n_o) / kThreads);
-  const int qo = (int)(((int64_t)(tid + 1) * n_o) / kThreads) - olo;
-  const int olast = max(n_o - 1, 0);
-  const int qom = (n_o + kThreads - 1) / kThreads;
-  Beta bo[E];
-  Lv lm[E];
-  if (n_o > 0) {
+  } else {
+  // longest run of the tile (block-uniform trip count); the loads of a run
+  // are all in flight before its chain starts
+  const int qwm = (n_w + kThreads - 1) / kThreads;
+  const int wl = max(n_w - 1, 0);
+  Beta bw[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if (e < qom) {
-        const int j = min(olo + e, olast);
-        if constexpr ((kFlags & H_RAW) != 0) bo[e] = H::make_beta(0.0, a.posO[o_start + j] * a.scale);
-        else bo[e] = bO[j];
-        if constexpr (kDiv) lm[e] = a.lmO[o_start + j];
+  for (int e = 0; e < E; ++e)
+    if (e < qwm) bw[e] = wbeta(min(wlo + e, wl));
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (e < qwm) {
+      const bool v = e < qw;
+      st_term(tf, v ? H::bp(bw[e]) : H::none());
+      if (v) {
+        sm.pfM[wlo + e] = tf.M;
+        sm.pfs[wlo + e] = tf.s;
+        sm.own[wlo + e] = (uint8_t)tid;
       }
     }
   }
+#pragma unroll
+  for (int e = E - 1; e >= 0; --e) {
+    if (e < qwm) {
+      const bool v = e < qw;
+      st_term(tb, v ? H::bm(bw[e]) : H::none());
+      if (v) {
+        sm.sfM[wlo + e] = tb.M;
+        sm.sfs[wlo + e] = tb.s;
+      }
+    }
+  }
+  const int wlast = max(n_w - 1, 0);
+  // O run of this thread
+  const int olo = (int)(((int64_t)tid * n_o) / kThreads);
+  const int qo = (int)(((int64_t)(tid + 1) * n_o) / kThreads) - olo;
   St<R> cf = st_empty<R>(), cb = st_empty<R>();
   if (a.carry_in) {
     const R* c = a.carry_in + 2 * H::kSt * (int64_t)unit;
@@ -566,24 +556,32 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   if (tid < 64) hrake_scan(sm, cf, cb);
   __syncthreads();
 
-  // 3. O phase
+  // 3. O phase (block-uniform trip count; a thread past its run repeats its
+  // last point with the results masked)
   R err = R(0);
   St<R> nf = st_empty<R>(), nb = st_empty<R>();
-  if (n_o > 0) {
+  const int qom = (n_o + kThreads - 1) / kThreads;
+  const int ol = max(n_o - 1, 0);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if (e >= qom) break;
-      const bool v = e < qo;
-      const int j = min(olo + e, olast);
-      const int z = sm.zl[j];
-      // forward: the W points before z (entry of the owner of W point z-1
-      // and its local prefix); backward: the W points from z on
-      const int i1 = max(z - 1, 0), i2 = min(z, wlast);
-      const St<R> Fo = st_comb(hslot_get(sm, 0, sm.own[i1]), St<R>{sm.pfM[i1], sm.pfs[i1]});
-      const St<R> Bo = st_comb(hslot_get(sm, 1, sm.own[i2]), St<R>{sm.sfM[i2], sm.sfs[i2]});
-      const St<R> F = z > 0 ? Fo : cf;
-      const St<R> B = z < n_w ? Bo : cb;
-      const Lv op = H::bp(bo[e]), om = H::bm(bo[e]);
+  for (int e = 0; e < E; ++e) {
+    if (e >= qom) break;
+    const bool v = e < qo;
+    const int j = min(olo + e, ol);
+    Beta bo;
+    Lv lm;
+    if constexpr ((kFlags & H_RAW) != 0) bo = H::make_beta(0.0, a.posO[o_start + j] * a.scale);
+    else bo = bO[j];
+    if constexpr (kDiv) lm = a.lmO[o_start + j];
+    const int z = sm.zl[j];
+    // forward: the W points before z (entry of the owner of W point z-1
+    // and its local prefix); backward: the W points from z on
+    const int i1 = max(z - 1, 0), i2 = min(z, wlast);
+    const St<R> Fo = st_comb(hslot_get(sm, 0, sm.own[i1]), St<R>{sm.pfM[i1], sm.pfs[i1]});
+    const St<R> Bo = st_comb(hslot_get(sm, 1, sm.own[i2]), St<R>{sm.sfM[i2], sm.sfs[i2]});
+    const St<R> F = z > 0 ? Fo : cf;
+    const St<R> B = z < n_w ? Bo : cb;
+    {
+      const Lv op = H::bp(bo), om = H::bm(bo);
       if constexpr (kProd) {
         // ln of p + q with the O frame 0 (levels +-Z), in float64
         const double a1 = H::to_double(F.M) + H::to_double(om);
@@ -600,8 +598,8 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
         if constexpr ((kFlags & H_RAW) != 0) val += a.rawO[o_start + j] * a.inv_eps;
         if (v) a.out[o_start + j] = val;
       } else {
-        const bool has_mass = H::valid(lm[e]);
-        const Lv c = has_mass ? lm[e] : H::zero();
+        const bool has_mass = H::valid(lm);
+        const Lv c = has_mass ? lm : H::zero();
         // delta = log2 S - c, S = 2^{beta-} P + 2^{beta+} Q; the binary
         // exponents of the mantissa sums join the level sums before rounding,
         // so the dominant part is near 0 and keeps full float precision
@@ -616,7 +614,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
         const R mb = g1 ? m1 : m2, mo = g1 ? m2 : m1;
         const R delta = big + H::lg2_acc(fma(mo, ed, mb));
         if constexpr ((kFlags & H_ERR) != 0) {
-          const R term = has_mass ? H::ex2(H::hi(lm[e])) * fabs(pow2m1(delta)) : H::ex2(delta);
+          const R term = has_mass ? H::ex2(H::hi(lm)) * fabs(pow2m1(delta)) : H::ex2(delta);
           err += v ? term : R(0);
         }
         if constexpr ((kFlags & H_POT) != 0) {
@@ -657,61 +655,96 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   }
 }
 
-// Last CTA, one direction: carries of every tile from the tile aggregates
-// (forward: the log-sum of the tiles before it; backward: of the tiles after
-// it).  Chunks of E tiles per thread are staged in the (now free) prefix
-// arrays with coalesced loads; the state leaving a chunk enters the next.
+// Last CTA: carries of every tile from the tile aggregates (forward: the
+// log-sum of the tiles before it; backward: of the tiles after it).  Chunks
+// of E tiles per thread are staged in the (now free) prefix / suffix arrays
+// with coalesced loads, eight in flight per thread; the state leaving a chunk
+// enters the next one in each direction.
+template <class R, int E>
+__device__ __forceinline__ void half_stage(const HalfArgs<R>& a, R* buf, int c0, int nq) {
+  constexpr int kS2 = 2 * HT<R>::kSt;
+  const R* src = a.agg_out + kS2 * (int64_t)c0;
+  const int nv = kS2 * nq;
+#pragma unroll 1
+  for (int r0 = threadIdx.x; r0 < nv; r0 += 8 * kThreads) {
+    R v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = r0 + k * kThreads;
+      v[k] = i < nv ? __ldcg(src + i) : R(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = r0 + k * kThreads;
+      if (i < nv) buf[i] = v[k];
+    }
+  }
+}
+
 template <class R, int E, int dir>
-__device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
+__device__ __forceinline__ void half_carry_chunk(const HalfArgs<R>& a, HalfSmem<R, E>& sm, const R* buf, int c0,
+                                                 int nq, St<R>& run) {
   using H = HT<R>;
   constexpr int kS = H::kSt;
-  constexpr int kQ = E;                     // tiles per thread per chunk
-  constexpr int K = kQ * kThreads;          // tiles per chunk
-  static_assert(sizeof(sm.pfM) + sizeof(sm.pfs) >= sizeof(R) * kS * K, "staging");
-  R* buf = reinterpret_cast<R*>(sm.pfM);    // pfM, pfs (adjacent): kS values per tile
+  constexpr int kQ = E;
   const int tid = threadIdx.x;
+  const int j0 = tid * kQ;
+  St<R> f = st_empty<R>();
+#pragma unroll 1
+  for (int k = 0; k < kQ; ++k) {
+    const int j = j0 + k;
+    if (j < nq) {
+      St<R> u;
+      H::get_s(buf + 2 * kS * j + dir * kS, u.M, u.s);
+      f = st_comb(f, u);
+    }
+  }
+  hslot_put(sm, dir, tid, f);
+  __syncthreads();
+  if ((tid >> 5) == dir) hrake_one<R, E, dir>(sm, run);
+  __syncthreads();
+  St<R> st = hslot_get(sm, dir, tid);
+#pragma unroll 1
+  for (int kk = 0; kk < kQ; ++kk) {
+    const int k = dir == 0 ? kk : kQ - 1 - kk;
+    const int j = j0 + k;
+    if (j < nq) {
+      H::put(a.carry_out + 2 * kS * (int64_t)(c0 + j) + dir * kS, st.M, st.s);
+      St<R> u;
+      H::get_s(buf + 2 * kS * j + dir * kS, u.M, u.s);
+      st = st_comb(st, u);
+    }
+  }
+  run = {sm.totM, sm.tots};
+}
+
+template <class R, int E>
+__device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
+  constexpr int K = E * kThreads;   // tiles per chunk
+  static_assert(sizeof(sm.pfM) + sizeof(sm.pfs) + sizeof(sm.sfM) + sizeof(sm.sfs) >=
+                    sizeof(R) * 2 * HT<R>::kSt * K, "staging");
+  R* buf = reinterpret_cast<R*>(sm.pfM);   // pfM, pfs, sfM, sfs are adjacent
   const int C = a.C;
   const int nch = (C + K - 1) / K;
-  St<R> run = st_empty<R>();
+  St<R> runF = st_empty<R>(), runB = st_empty<R>();
 #pragma unroll 1
-  for (int ci = 0; ci < nch; ++ci) {
-    const int ch = dir == 0 ? ci : nch - 1 - ci;
+  for (int ch = 0; ch < nch; ++ch) {
     const int c0 = ch * K, nq = min(K, C - c0);
     __syncthreads();
-#pragma unroll 1
-    for (int i = tid; i < kS * nq; i += kThreads) {
-      const int t = i / kS, d = i - t * kS;
-      buf[i] = __ldcg(a.agg_out + 2 * kS * (int64_t)(c0 + t) + dir * kS + d);
-    }
+    half_stage<R, E>(a, buf, c0, nq);
     __syncthreads();
-    const int j0 = tid * kQ;
-    St<R> f = st_empty<R>();
+    half_carry_chunk<R, E, 0>(a, sm, buf, c0, nq, runF);
+    if (nch == 1) half_carry_chunk<R, E, 1>(a, sm, buf, c0, nq, runB);
+  }
+  if (nch > 1) {
 #pragma unroll 1
-    for (int k = 0; k < kQ; ++k) {
-      const int j = j0 + k;
-      if (j < nq) {
-        St<R> u;
-        H::get_s(buf + kS * j, u.M, u.s);
-        f = st_comb(f, u);
-      }
+    for (int ch = nch - 1; ch >= 0; --ch) {
+      const int c0 = ch * K, nq = min(K, C - c0);
+      __syncthreads();
+      half_stage<R, E>(a, buf, c0, nq);
+      __syncthreads();
+      half_carry_chunk<R, E, 1>(a, sm, buf, c0, nq, runB);
     }
-    hslot_put(sm, dir, tid, f);
-    __syncthreads();
-    if ((tid >> 5) == dir) hrake_one<R, E, dir>(sm, run);
-    __syncthreads();
-    St<R> st = hslot_get(sm, dir, tid);
-#pragma unroll 1
-    for (int kk = 0; kk < kQ; ++kk) {
-      const int k = dir == 0 ? kk : kQ - 1 - kk;
-      const int j = j0 + k;
-      if (j < nq) {
-        H::put(a.carry_out + 2 * kS * (int64_t)(c0 + j) + dir * kS, st.M, st.s);
-        St<R> u;
-        H::get_s(buf + kS * j, u.M, u.s);
-        st = st_comb(st, u);
-      }
-    }
-    run = {sm.totM, sm.tots};
   }
 }
 
@@ -722,13 +755,10 @@ __device__ void half_finish(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int units)
   const int tid = threadIdx.x;
   double ep = 0.0;
   if (kFlags & H_ERR) {
-#pragma unroll 1
+#pragma unroll 4
     for (int i = tid; i < units; i += kThreads) ep += __ldcg(a.part + i);
   }
-  if (kFlags & (H_NEXT | H_AGG)) {
-    half_carries<R, E, 0>(a, sm);
-    half_carries<R, E, 1>(a, sm);
-  }
+  if (kFlags & (H_NEXT | H_AGG)) half_carries<R, E>(a, sm);
   double errsum = 0.0;
   if (kFlags & H_ERR) {
     ep = warp_sum(ep);
@@ -774,7 +804,7 @@ __device__ __forceinline__ bool half_last_cta(int32_t* ticket, int G, HalfSmem<R
 
 // resident CTAs per SM the registers are budgeted for (float32)
 #ifndef FINOM_HALF_MINB8
-#define FINOM_HALF_MINB8 2
+#define FINOM_HALF_MINB8 3
 #endif
 template <class R, int E>
 constexpr int half_min_blocks() {
