@@ -112,6 +112,37 @@ finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const 
                            void* stream, finom_plan_t* out);
 
 /*
+ * finom_plan_nd -- plan for two d-dimensional tensor-product grids (Sec. 3.2,
+ * the closing remark on higher dimensions: with the separable L1 cost
+ * sum_k |x^k - y^k| the kernel is K = K_d (x) ... (x) K_1, and a product
+ * with K is d batches of 1D products, one axis after the other):
+ *   mu's grid = { (x^1_{i1}, ..., x^d_{id}) }, nu's grid = { (y^1_{j1}, ...,
+ *   y^d_{jd}) }, i_k, j_k < n[k].
+ *   d: 1 .. 8; n: d sizes (HOST array), each >= 1, product < 2^31.
+ *   xs, ys: HOST arrays of d DEVICE pointers; xs[k], ys[k]: n[k] doubles,
+ *   each sorted non-decreasing and finite.  eps > 0 and finite.
+ * Grid arrays passed to the other entry points hold prod(n) values with axis
+ * 0 fastest: point (i_1, ..., i_d) at i_1 + n_1 (i_2 + n_2 (i_3 + ...)) (the
+ * paper's vec() for d = 2).  finom_kv (v on nu's grid, out on mu's),
+ * finom_ktu, finom_kv_log, finom_ktu_log, finom_solve, finom_solve_begin /
+ * step / poll / end, finom_cost and finom_solve_eps_scaling take these plans
+ * and run Algorithm 2's loop (Phi = Psi = 1 / prod(n) at the start) with the
+ * products done axis by axis by the half-step kernel, every 1D product in
+ * log-domain levels; W1 = <C, Gamma> and the marginal error are evaluated in
+ * float64.  finom_plan_shape reports dim = d, N = n[0], M = prod(n) / n[0];
+ * finom_plan_axes returns n.  Synchronous.  Errors as finom_plan.
+ */
+finom_status finom_plan_nd(int32_t d, const int64_t* n, const double* const* xs, const double* const* ys,
+                           double eps, finom_precision prec, void* stream, finom_plan_t* out);
+
+/*
+ * finom_plan_axes -- the number of axes d and the axis sizes n[0 .. d) (host
+ * array of at least d entries) of a plan made by finom_plan_nd; other plans:
+ * FINOM_ENOTSUP.  Either pointer may be NULL.
+ */
+finom_status finom_plan_axes(finom_plan_t plan, int32_t* d, int64_t* n);
+
+/*
  * finom_plan_shape -- dimension of a plan and its sizes: dim = 1 with the
  * mesh sizes (N, M), or dim = 2 with the grid sides (N points along x, M
  * along y).  Any pointer may be NULL.

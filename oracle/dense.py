@@ -33,7 +33,7 @@ from scipy.special import logsumexp
 __all__ = [
     "cost_1d", "cost_2d", "kernel", "kv_dense", "ktu_dense", "log_apply_dense",
     "SinkhornResult", "sinkhorn_log", "sinkhorn_linear", "marginal_error",
-    "transport_cost", "plan_from_potentials", "barycentric", "kron_2d",
+    "transport_cost", "plan_from_potentials", "barycentric", "kron_2d", "cost_nd",
 ]
 
 
@@ -72,6 +72,33 @@ def cost_2d(x1, y1, x2, y2):
     X2 = np.tile(x2, M)
     Y2 = np.repeat(y2, N)
     return np.abs(X1[:, None] - X2[None, :]) + np.abs(Y1[:, None] - Y2[None, :])
+
+
+def grid_coords(axes):
+    """Coordinates of the points of the tensor-product grid of the given axis
+    node arrays, one row per axis, points numbered with axis 0 fastest
+    (index i_0 + n_0 (i_1 + n_1 (i_2 + ...)))."""
+    axes = [np.asarray(a, dtype=np.float64) for a in axes]
+    n = [len(a) for a in axes]
+    G = int(np.prod(n))
+    idx = np.arange(G)
+    out = np.empty((len(axes), G))
+    inner = 1
+    for k, a in enumerate(axes):
+        out[k] = a[(idx // inner) % n[k]]
+        inner *= n[k]
+    return out
+
+
+def cost_nd(xs, ys):
+    """L1 cost between the d-dimensional tensor-product grids of the axes xs
+    (first measure) and ys (second), sum_k |x^k - y^k| (the separable cost of
+    Sec. 3, in d dimensions), points numbered with axis 0 fastest."""
+    X, Y = grid_coords(xs), grid_coords(ys)
+    C = np.zeros((X.shape[1], Y.shape[1]))
+    for k in range(X.shape[0]):
+        C += np.abs(X[k][:, None] - Y[k][None, :])
+    return C
 
 
 def kernel(C, eps):

@@ -69,6 +69,8 @@ _SIGS = {
     "finom_kv_log_noalloc": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "finom_plan_2d": ([_P, _P, _I64, _P, _P, _I64, _D, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_plan_shape": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "finom_plan_nd": ([_I32, _P, _P, _P, _D, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "finom_plan_axes": ([_P, ctypes.POINTER(_I32), _P], ctypes.c_int),
     "finom_plan_batch": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "finom_plan_instances": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
     "finom_plan_batch_elems": ([_P, _P, _P, _P, _I64, _P, ctypes.c_int, _I32, _P, ctypes.POINTER(_P)],
@@ -201,6 +203,36 @@ def finom_plan_2d(x1, x2, y1, y2, eps, precision="f32_log", stream=None) -> Plan
                               _dev(y1, M, torch.float64, "y1"), _dev(y2, M, torch.float64, "y2"), M,
                               float(eps), _PREC[precision], _stream(stream), ctypes.byref(h)))
     return Plan(h, N * M, N * M, float(eps), _PREC[precision], x1.device.index or 0, 2, N, M)
+
+
+def finom_plan_nd(xs, ys, eps, precision="f32_log", stream=None) -> Plan:
+    """Plan for the d-dimensional grids x^1 (x) ... (x) x^d (mu) and
+    y^1 (x) ... (x) y^d (nu): xs, ys are sequences of d device float64
+    tensors (axis k of each grid).  Grid arrays of the other calls are flat
+    with axis 0 fastest."""
+    import torch
+    load()
+    d = len(xs)
+    if len(ys) != d:
+        raise ValueError("xs and ys need the same number of axes")
+    n = (ctypes.c_int64 * d)(*[int(x.numel()) for x in xs])
+    px = (ctypes.c_void_p * d)(*[_dev(x, int(x.numel()), torch.float64, f"xs[{k}]") for k, x in enumerate(xs)])
+    py = (ctypes.c_void_p * d)(*[_dev(y, int(n[k]), torch.float64, f"ys[{k}]") for k, y in enumerate(ys)])
+    h = ctypes.c_void_p()
+    _check(_lib.finom_plan_nd(d, ctypes.cast(n, ctypes.c_void_p), ctypes.cast(px, ctypes.c_void_p),
+                              ctypes.cast(py, ctypes.c_void_p), float(eps), _PREC[precision], _stream(stream),
+                              ctypes.byref(h)))
+    G = 1
+    for v in n:
+        G *= v
+    return Plan(h, G, G, float(eps), _PREC[precision], xs[0].device.index or 0, d, int(n[0]), G // int(n[0]))
+
+
+def finom_plan_axes(plan: Plan):
+    d = _I32()
+    n = (ctypes.c_int64 * 8)()
+    _check(_lib.finom_plan_axes(plan.handle, ctypes.byref(d), ctypes.cast(n, ctypes.c_void_p)))
+    return list(n[:d.value])
 
 
 def finom_plan_shape(plan: Plan):

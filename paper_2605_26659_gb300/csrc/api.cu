@@ -504,6 +504,7 @@ finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const dou
   }
   DeviceGuard dg(p->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->nd) return kv_nd(p, transpose, logmode, a, b, out, s);
   if (p->dim == 2) return kv2d(p, transpose, logmode, a, b, out, s);
   return p->prec == FINOM_F32_LOG ? kv_impl<float>(p, transpose, logmode, a, b, out, s)
                                   : kv_impl<double>(p, transpose, logmode, a, b, out, s);
@@ -583,6 +584,57 @@ finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const 
   return FINOM_OK;
 }
 
+finom_status finom_plan_nd(int32_t d, const int64_t* n, const double* const* xs, const double* const* ys,
+                           double eps, finom_precision prec, void* stream, finom_plan_t* out) {
+  if (!out) {
+    set_error("finom_plan_nd: out is NULL");
+    return FINOM_EINVAL;
+  }
+  *out = nullptr;
+  if (d < 1 || d > finom_plan_s::kMaxDim || !n || !xs || !ys || !(eps > 0.0) || !std::isfinite(eps) ||
+      (prec != FINOM_F64 && prec != FINOM_F32_LOG)) {
+    set_error("finom_plan_nd: need 1 <= d <= 8, n, xs, ys non-null, eps > 0 finite, known precision");
+    return FINOM_EINVAL;
+  }
+  int64_t G = 1;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1 || !xs[k] || !ys[k] || 2 * n[k] > (int64_t)INT32_MAX / 2) {
+      set_error("finom_plan_nd: every axis needs n[k] >= 1 and non-null node arrays");
+      return FINOM_EINVAL;
+    }
+    G *= n[k];
+    if (G > (int64_t)INT32_MAX) {
+      set_error("finom_plan_nd: the grid must have fewer than 2^31 points");
+      return FINOM_EINVAL;
+    }
+  }
+  finom_plan_s* p = new (std::nothrow) finom_plan_s();
+  if (!p) return FINOM_ENOMEM;
+  p->eps = eps;
+  p->prec = prec;
+  cudaGetDevice(&p->device);
+  finom_status rc = plan_nd_build(p, d, n, xs, ys, (cudaStream_t)stream);
+  if (rc != FINOM_OK) {
+    plan_nd_free(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return FINOM_OK;
+}
+
+finom_status finom_plan_axes(finom_plan_t plan, int32_t* d, int64_t* n) {
+  if (bad_plan(plan)) return FINOM_EINVAL;
+  if (!plan->nd) {
+    set_error("finom_plan_axes: not a plan of finom_plan_nd");
+    return FINOM_ENOTSUP;
+  }
+  if (d) *d = plan->dim;
+  if (n)
+    for (int k = 0; k < plan->dim; ++k) n[k] = plan->nd_n[k];
+  return FINOM_OK;
+}
+
 finom_status finom_plan_destroy(finom_plan_t plan) {
   if (!plan) return FINOM_OK;
   DeviceGuard dg(plan->device);
@@ -590,6 +642,7 @@ finom_status finom_plan_destroy(finom_plan_t plan) {
   free_state(plan);
   free_plan(plan);
   plan2d_free(plan);
+  plan_nd_free(plan);
   plan_batch_free(plan);
   delete plan;
   return FINOM_OK;
@@ -733,6 +786,11 @@ finom_status finom_solve_batch(finom_plan_t plan, const double* u, const double*
 finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64_t* M) {
   if (bad_plan(plan)) return FINOM_EINVAL;
   if (dim) *dim = plan->dim;
+  if (plan->nd) {
+    if (N) *N = plan->nd_n[0];
+    if (M) *M = plan->nd_G / plan->nd_n[0];
+    return FINOM_OK;
+  }
   if (N) *N = plan->dim == 2 ? plan->ax->N : plan->N;
   if (M) *M = plan->dim == 2 ? plan->ay->N : plan->M;
   return FINOM_OK;
@@ -791,6 +849,11 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
     return FINOM_EINVAL;
   }
   DeviceGuard dg(plan->device);
+  if (plan->nd) {
+    finom_status rc = solve_nd(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
+    if (res && rc != FINOM_OK) res->status = rc;
+    return rc;
+  }
   if (plan->dim == 2) {
     finom_status rc = solve2d(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
     if (res && rc != FINOM_OK) res->status = rc;
@@ -873,10 +936,20 @@ finom_status finom_solve_eps_scaling(finom_plan_t plan, const double* u, const d
     // the same meshes at the larger eps: a plan of its own, warm-started from
     // the potentials of the previous stage
     finom_plan_t q = nullptr;
-    finom_status rc = plan->dim == 2
-                          ? finom_plan_2d(plan->ax->x, plan->ax->y, plan->ax->N, plan->ay->x, plan->ay->y,
+    finom_status rc;
+    if (plan->nd) {
+      const double* xs[finom_plan_s::kMaxDim];
+      const double* ys[finom_plan_s::kMaxDim];
+      for (int k = 0; k < plan->dim; ++k) {
+        xs[k] = plan->nd_ax[k]->x;
+        ys[k] = plan->nd_ax[k]->y;
+      }
+      rc = finom_plan_nd(plan->dim, plan->nd_n, xs, ys, e, plan->prec, stream, &q);
+    } else {
+      rc = plan->dim == 2 ? finom_plan_2d(plan->ax->x, plan->ax->y, plan->ax->N, plan->ay->x, plan->ay->y,
                                           plan->ay->N, e, plan->prec, stream, &q)
                           : finom_plan(plan->x, plan->N, plan->y, plan->M, e, plan->prec, stream, &q);
+    }
     finom_result r{};
     if (rc == FINOM_OK) rc = finom_solve(q, u, v, tol_stage, maxit - done, f, g, warm, &r, stream);
     finom_plan_destroy(q);
@@ -902,6 +975,7 @@ finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double*
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->nd) return solve_nd_begin(plan, u, v, tol, maxit, f0, g0, s);
   if (plan->dim == 2) return solve2d_begin(plan, u, v, tol, maxit, f0, g0, s);
   return plan->prec == FINOM_F32_LOG ? solve_begin<float>(plan, u, v, tol, maxit, f0, g0, s)
                                      : solve_begin<double>(plan, u, v, tol, maxit, f0, g0, s);
@@ -916,6 +990,7 @@ finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* strea
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->nd) return solve_nd_step(plan, iterations, s);
   if (plan->dim == 2) return solve2d_step(plan, iterations, s);
   return plan->prec == FINOM_F32_LOG ? solve_step<float>(plan, iterations, s)
                                      : solve_step<double>(plan, iterations, s);
@@ -954,6 +1029,7 @@ finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_resu
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->nd) return solve_nd_end(plan, f, g, res, s);
   if (plan->dim == 2) return solve2d_end(plan, f, g, res, s);
   return plan->prec == FINOM_F32_LOG ? solve_end<float>(plan, f, g, res, s)
                                      : solve_end<double>(plan, f, g, res, s);
@@ -969,6 +1045,7 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
   }
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (plan->nd) return cost_nd(plan, u, v, f, g, w1, err, s);
   if (plan->dim == 2) return cost2d(plan, u, v, f, g, w1, err, s);
   finom_status rc = plan->prec == FINOM_F32_LOG ? ensure_state<float>(plan) : ensure_state<double>(plan);
   if (rc != FINOM_OK) return rc;

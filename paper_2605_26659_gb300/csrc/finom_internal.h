@@ -123,6 +123,24 @@ struct finom_plan_s {
   std::vector<int32_t> hitilec;  // per instance: first 2048-point tile of the float64 evaluation
   int32_t* tile_x0c = nullptr;   // the evaluation's tile tables (as tile_x0, 2048-point tiles)
   double* ieps = nullptr;        // per instance
+  // d-dimensional tensor-product plans (nd.cu; finom_plan_nd): grids of
+  // nd_n[0] x ... x nd_n[d-1] points, axis 0 fastest; one 1D plan per axis
+  // merging mu's nodes (x side) with nu's (y side); per axis the node
+  // positions in bits (level pairs in the plan precision, float64 copies)
+  // and log2 of their distance to the axis minimum (float64, the cost)
+  static constexpr int kMaxDim = 8;
+  bool nd = false;
+  int64_t nd_n[kMaxDim] = {};
+  int64_t nd_G = 0;
+  finom_plan_s* nd_ax[kMaxDim] = {};
+  void* nd_zx[kMaxDim] = {};
+  void* nd_zy[kMaxDim] = {};
+  double* nd_zx64[kMaxDim] = {};
+  double* nd_zy64[kMaxDim] = {};
+  double* nd_lx64[kMaxDim] = {};
+  double* nd_ly64[kMaxDim] = {};
+  double nd_z0s[kMaxDim] = {};   // axis minimum over both meshes, in bits
+  double* nd_w64 = nullptr;      // float64 workspace of the checks (grids, aggregates)
   finom::SolveState st;
 };
 
@@ -164,4 +182,18 @@ finom_status solve_batch_begin(finom_plan_s* p, const double* u, const double* v
                                cudaStream_t s);
 finom_status solve_batch_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
 finom_status solve_batch_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
+// d-dimensional plans (nd.cu)
+finom_status plan_nd_build(finom_plan_s* p, int d, const int64_t* n, const double* const* xs,
+                           const double* const* ys, cudaStream_t s);
+void plan_nd_free(finom_plan_s* p);
+finom_status kv_nd(finom_plan_s* p, bool transpose_k, bool logmode, const double* a, const double* b,
+                   double* out, cudaStream_t s);
+finom_status solve_nd(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                      double* f, double* g, int32_t warm, finom_result* res, cudaStream_t s);
+finom_status solve_nd_begin(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
+                            const double* f0, const double* g0, cudaStream_t s);
+finom_status solve_nd_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
+finom_status solve_nd_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
+finom_status cost_nd(finom_plan_s* p, const double* u, const double* v, const double* f, const double* g,
+                     double* w1, double* err, cudaStream_t s);
 }  // namespace finom

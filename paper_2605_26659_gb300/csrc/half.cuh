@@ -66,6 +66,12 @@ enum : int {
   H_LIN = 128,        // products: the sum at the O points (float64)
   H_RAW = 256,        // products: levels formed from the caller's float64 vectors and the
                       // plan's positions inside the kernel (no converted copies)
+  H_LINES = 512,      // axis pass of a tensor-product grid: units are (line, tile) of an
+                      // axis plan; log-weights on the grid, positions per axis node
+  H_QOUT = 1024,      // axis pass: write log2 of the product at the O nodes (a level pair)
+  H_FB = 2048,        // axis pass: write log2 of the lower and of the upper block sums apart
+                      // (float64, out and out + grid size)
+  H_ZLOG = 4096,      // axis pass: the W levels carry log2(z - z_min) of their node as well
 };
 
 constexpr int kHalfY = H_POT | H_ERR | H_NEXT | H_CHECK_DONE;       // psi <- nu / K^T phi
@@ -76,6 +82,17 @@ constexpr int kHalfLog = H_LOG;
 constexpr int kHalfLin = H_LIN;
 constexpr int kHalfRawAgg = H_AGG | H_RAW;
 constexpr int kHalfRawLog = H_LOG | H_RAW;
+// axis passes of a d-dimensional application (Sec. 3, applied axis by axis)
+constexpr int kLineAgg = H_AGG | H_LINES;                    // tile aggregates of the W side
+constexpr int kLineQ = H_QOUT | H_LINES;                     // a pass before the last one
+constexpr int kLineY = H_POT | H_ERR | H_CHECK_DONE | H_LINES;  // last pass of K^T phi: divide + check
+constexpr int kLineX = H_POT | H_ITER_END | H_CHECK_DONE | H_LINES;  // last pass of K psi
+constexpr int kLineCheck = H_ERR | H_LINES;
+// the cost-weighted pass of <C, Gamma> (float64): both block sums apart,
+// with plain and with distance-weighted levels
+constexpr int kLineFB = H_FB | H_LINES;
+constexpr int kLineFBZ = H_FB | H_ZLOG | H_LINES;
+constexpr int kLineAggZ = H_AGG | H_ZLOG | H_LINES;
 
 // Level arithmetic per precision.  Beta holds (beta+, beta-) of one point.
 template <class R>
@@ -129,6 +146,24 @@ struct HT<float> {
     const float hi = s + lo;
     lo = lo - (hi - s);
     return make_float2(hi, lo);
+  }
+  // (b + z, b - z) of two level pairs, the hi parts added with their
+  // rounding error kept (b none: none)
+  __device__ __forceinline__ static Beta beta_of(Lv b, Lv z) {
+    if (!(b.x > 0.5f * kNone)) return make_float4(kNone, 0.f, kNone, 0.f);
+    const float s = b.x + z.x, bs = s - b.x, e = (b.x - (s - bs)) + (z.x - bs);
+    const float d = b.x - z.x, bd = d - b.x, f = (b.x - (d - bd)) + (-z.x - bd);
+    return make_float4(s, e + (b.y + z.y), d, f + (b.y - z.y));
+  }
+  // a + b for level pairs (b may be none)
+  __device__ __forceinline__ static Lv add_lv(Lv a, Lv b) {
+    const float s = a.x + b.x, bs = s - a.x, e = (a.x - (s - bs)) + (b.x - bs);
+    return make_float2(s, e + (a.y + b.y));
+  }
+  // a float64 value as a level pair
+  __device__ __forceinline__ static Lv from_double(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
   }
   // a - t with the rounding error of the hi part moved to lo (exact when
   // |a.x| >= |t|, the case of a division step near the fixed point); the pair
@@ -192,6 +227,12 @@ struct HT<double> {
   __device__ __forceinline__ static Lv mk(double h, double) { return h; }
   __device__ __forceinline__ static Lv sub(Lv a, double t) { return a - t; }
   __device__ __forceinline__ static Lv sub_fast(Lv a, double t) { return a - t; }
+  __device__ __forceinline__ static Beta beta_of(Lv b, Lv z) {
+    if (!(b > 0.5 * kNone)) return make_double2(kNone, kNone);
+    return make_double2(b + z, b - z);
+  }
+  __device__ __forceinline__ static Lv from_double(double v) { return v; }
+  __device__ __forceinline__ static Lv add_lv(Lv a, Lv b) { return a + b; }
   __device__ __forceinline__ static double to_double(Lv a) { return a; }
   __device__ __forceinline__ static Beta make_beta(double b, double z) {
     if (!(b > -INFINITY)) return make_double2(kNone, kNone);
@@ -284,6 +325,18 @@ struct HalfArgs {
   const double* posO;
   double scale;       // 1 / (eps ln 2)
   double inv_eps;
+  // H_LINES: lines of the launch; line l's node i sits at grid index
+  // (l % inner) + (l / inner) * inner * nk + i * inner
+  int lines;
+  int64_t inner, nk;
+  const typename HT<R>::Lv* gW;    // W log-weights on the grid (bits)
+  const typename HT<R>::Lv* gO;    // O log-weights on the grid (frames; H_POT / H_ERR)
+  typename HT<R>::Lv* gO_out;      // new O log-weights (H_POT)
+  typename HT<R>::Lv* q_out;       // H_QOUT: log2 of the product at the O nodes
+  const typename HT<R>::Lv* zW;    // positions of the axis nodes in bits (W, O side)
+  const typename HT<R>::Lv* zO;
+  const typename HT<R>::Lv* zlogW; // H_ZLOG: log2(z - z_min) of the W axis nodes (bits)
+  int64_t grid;                    // H_FB: grid points (the upper sums follow the lower ones)
 };
 
 constexpr int kHSlots = kThreads + kThreads / 32;
@@ -445,12 +498,19 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   using Beta = typename H::Beta;
   constexpr int kT = E * kThreads;
   constexpr bool kAgg = (kFlags & H_AGG) != 0;
-  constexpr bool kProd = (kFlags & (H_LOG | H_LIN)) != 0;
+  constexpr bool kLines = (kFlags & H_LINES) != 0;
+  constexpr bool kProd = (kFlags & (H_LOG | H_LIN | H_QOUT | H_FB)) != 0;
   constexpr bool kDiv = (kFlags & (H_POT | H_ERR)) != 0;
   const int tid = threadIdx.x;
 
-  const int x0 = a.tile_x0[unit], x1 = a.tile_x0[unit + 1];
-  const int64_t k0 = (int64_t)unit * kT;
+  // line mode: unit = line * C + tile; grid index of node i of the line:
+  // gbase + i * inner
+  const int line = kLines ? unit / a.C : 0;
+  const int tile = unit - line * a.C;
+  const int64_t inner = kLines ? a.inner : 1;
+  const int64_t gbase = kLines ? (line % inner) + (line / inner) * inner * a.nk : 0;
+  const int x0 = a.tile_x0[tile], x1 = a.tile_x0[tile + 1];
+  const int64_t k0 = (int64_t)tile * kT;
   const int64_t kend = min(k0 + (int64_t)kT, a.L);
   const int y0 = (int)(k0 - x0), y1 = (int)(kend - x1);
   const int o_start = a.o_is_x ? x0 : y0;
@@ -490,6 +550,10 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   auto wbeta = [&](int i) -> Beta {
     if constexpr ((kFlags & H_RAW) != 0) {
       return H::make_beta(a.rawW[w_start + i] * a.scale, a.posW[w_start + i] * a.scale);
+    } else if constexpr (kLines) {
+      Lv b = a.gW[gbase + (int64_t)(w_start + i) * inner];
+      if constexpr ((kFlags & H_ZLOG) != 0) b = H::add_lv(b, a.zlogW[w_start + i]);
+      return H::beta_of(b, a.zW[w_start + i]);
     } else {
       return bW[i];
     }
@@ -569,9 +633,11 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
     const int j = min(olo + e, ol);
     Beta bo;
     Lv lm;
+    const int64_t gi = gbase + (int64_t)(o_start + j) * inner;   // line mode: grid index
     if constexpr ((kFlags & H_RAW) != 0) bo = H::make_beta(0.0, a.posO[o_start + j] * a.scale);
+    else if constexpr (kLines) bo = H::beta_of(kDiv ? a.gO[gi] : H::zero(), a.zO[o_start + j]);
     else bo = bO[j];
-    if constexpr (kDiv) lm = a.lmO[o_start + j];
+    if constexpr (kDiv) lm = kLines ? a.lmO[gi] : a.lmO[o_start + j];
     const int z = sm.zl[j];
     // forward: the W points before z (entry of the owner of W point z-1
     // and its local prefix); backward: the W points from z on
@@ -592,11 +658,20 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
         const R sb = g1 ? F.s : B.s, so = g1 ? B.s : F.s;
         const bool none = !(sb > R(0)) || big < 0.5 * (double)H::kNone;
         const double l2 = big + (double)H::lg2_acc(fma(so, H::ex2(d), sb));
-        double val;
-        if constexpr ((kFlags & H_LOG) != 0) val = none ? -INFINITY : 0.69314718055994530942 * l2;
-        else val = none ? 0.0 : exp2(l2);
-        if constexpr ((kFlags & H_RAW) != 0) val += a.rawO[o_start + j] * a.inv_eps;
-        if (v) a.out[o_start + j] = val;
+        if constexpr ((kFlags & H_FB) != 0) {
+          if (v) {
+            a.out[gi] = (F.s > R(0) && a1 > 0.5 * (double)H::kNone) ? a1 + (double)H::lg2_acc(F.s) : -INFINITY;
+            a.out[a.grid + gi] = (B.s > R(0) && a2 > 0.5 * (double)H::kNone) ? a2 + (double)H::lg2_acc(B.s) : -INFINITY;
+          }
+        } else if constexpr ((kFlags & H_QOUT) != 0) {
+          if (v) a.q_out[gi] = none ? H::none() : H::from_double(l2);
+        } else {
+          double val;
+          if constexpr ((kFlags & H_LOG) != 0) val = none ? -INFINITY : 0.69314718055994530942 * l2;
+          else val = none ? 0.0 : exp2(l2);
+          if constexpr ((kFlags & H_RAW) != 0) val += a.rawO[o_start + j] * a.inv_eps;
+          if (v) a.out[o_start + j] = val;
+        }
       } else {
         const bool has_mass = H::valid(lm);
         const Lv c = has_mass ? lm : H::zero();
@@ -619,6 +694,9 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
         }
         if constexpr ((kFlags & H_POT) != 0) {
           const bool ok = v && has_mass && delta > R(0.5) * H::kNone;
+          if constexpr (kLines) {
+            if (v) a.gO_out[gi] = ok ? H::sub_fast(a.gO[gi], delta) : H::none();
+          } else {
           const Lv np = ok ? H::sub_fast(op, delta) : H::none();
           const Lv nm = ok ? H::sub_fast(om, delta) : H::none();
           if (v) a.bO_out[o_start + j] = H::pack(np, nm);
@@ -626,6 +704,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
             // the tile aggregate of the next application (new levels)
             st_term(nf, np);
             st_term(nb, nm);
+          }
           }
         }
       }
@@ -718,6 +797,35 @@ __device__ __forceinline__ void half_carry_chunk(const HalfArgs<R>& a, HalfSmem<
   run = {sm.totM, sm.tots};
 }
 
+// Last CTA, line mode: each thread scans the tiles of whole lines (a line
+// spans a few tiles); a line starts and ends empty.
+template <class R>
+__device__ void half_carries_lines(const HalfArgs<R>& a) {
+  using H = HT<R>;
+  constexpr int kS = H::kSt;
+  const int C = a.C;
+#pragma unroll 1
+  for (int l = threadIdx.x; l < a.lines; l += kThreads) {
+    const int64_t u0 = (int64_t)l * C;
+    St<R> st = st_empty<R>();
+#pragma unroll 1
+    for (int t = 0; t < C; ++t) {
+      H::put(a.carry_out + 2 * kS * (u0 + t), st.M, st.s);
+      St<R> u;
+      H::get(a.agg_out + 2 * kS * (u0 + t), u.M, u.s);
+      st = st_comb(st, u);
+    }
+    st = st_empty<R>();
+#pragma unroll 1
+    for (int t = C - 1; t >= 0; --t) {
+      H::put(a.carry_out + 2 * kS * (u0 + t) + kS, st.M, st.s);
+      St<R> u;
+      H::get(a.agg_out + 2 * kS * (u0 + t) + kS, u.M, u.s);
+      st = st_comb(st, u);
+    }
+  }
+}
+
 template <class R, int E>
 __device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
   constexpr int K = E * kThreads;   // tiles per chunk
@@ -758,7 +866,10 @@ __device__ void half_finish(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int units)
 #pragma unroll 4
     for (int i = tid; i < units; i += kThreads) ep += __ldcg(a.part + i);
   }
-  if (kFlags & (H_NEXT | H_AGG)) half_carries<R, E>(a, sm);
+  if (kFlags & (H_NEXT | H_AGG)) {
+    if (kFlags & H_LINES) half_carries_lines<R>(a);
+    else half_carries<R, E>(a, sm);
+  }
   double errsum = 0.0;
   if (kFlags & H_ERR) {
     ep = warp_sum(ep);
@@ -817,7 +928,7 @@ template <class R, int kFlags, int E>
 __global__ void __launch_bounds__(kThreads, half_min_blocks<R, E>()) k_half(HalfArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HalfSmem<R, E>& sm = *reinterpret_cast<HalfSmem<R, E>*>(smem_raw);
-  const int units = a.C;
+  const int units = (kFlags & H_LINES) ? a.lines * a.C : a.C;
   for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
     if (!half_unit<R, kFlags, E>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done
     __syncthreads();

@@ -39,7 +39,8 @@ cudaError_t half_launch_me(const HalfArgs<R>& a, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3(half_grid<R, M, E>(a.C, smem));
+  const int64_t units = (M & H_LINES) ? (int64_t)a.lines * a.C : (int64_t)a.C;
+  cfg.gridDim = dim3(half_grid<R, M, E>(units, smem));
   return cudaLaunchKernelEx(&cfg, k_half<R, M, E>, a);
 }
 
@@ -55,6 +56,22 @@ cudaError_t half_launch_e(const HalfArgs<R>& a, int mode, cudaStream_t s, bool* 
     case kHalfLin: return half_launch_me<R, kHalfLin, E>(a, s);
     case kHalfRawAgg: return half_launch_me<R, kHalfRawAgg, E>(a, s);
     case kHalfRawLog: return half_launch_me<R, kHalfRawLog, E>(a, s);
+    case kLineAgg: return half_launch_me<R, kLineAgg, E>(a, s);
+    case kLineQ: return half_launch_me<R, kLineQ, E>(a, s);
+    case kLineY: return half_launch_me<R, kLineY, E>(a, s);
+    case kLineX: return half_launch_me<R, kLineX, E>(a, s);
+    case kLineCheck: return half_launch_me<R, kLineCheck, E>(a, s);
+    default: break;
+  }
+  if constexpr (sizeof(R) == sizeof(double)) {
+    switch (mode) {
+      case kLineFB: return half_launch_me<R, kLineFB, E>(a, s);
+      case kLineFBZ: return half_launch_me<R, kLineFBZ, E>(a, s);
+      case kLineAggZ: return half_launch_me<R, kLineAggZ, E>(a, s);
+      default: break;
+    }
+  }
+  switch (mode) {
     default: *known = false; return cudaSuccess;
   }
 }
