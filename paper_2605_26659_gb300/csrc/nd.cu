@@ -35,7 +35,6 @@ finom_status normalise_masses(const double*, int64_t, void*, double*, double*, i
                               cudaStream_t);
 void fill_d(double*, int64_t, double, cudaStream_t);
 void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
-int tune_pick(finom_precision prec, int64_t L);
 
 namespace {
 
@@ -648,7 +647,11 @@ finom_status plan_nd_build(finom_plan_s* p, int d, const int64_t* n, const doubl
     ax->prec = p->prec;
     ax->device = p->device;
     finom_status rc = build_plan(ax, xs[k], ys[k], s);
-    if (rc == FINOM_OK) rc = build_tiles_e(ax, tune_pick(p->prec, 2 * n[k]), s);
+    // the smallest tile that holds a whole line (lines give the parallelism;
+    // a line in one tile needs no carries and no aggregate launch)
+    int e = 1;
+    while (e < kElems && (int64_t)e * kThreads < 2 * n[k]) e *= 2;
+    if (rc == FINOM_OK) rc = build_tiles_e(ax, e, s);
     if (rc != FINOM_OK) return rc;
     // the axis minimum over both meshes (the sorted copies' first entries)
     double x0 = 0.0, y0 = 0.0;
