@@ -50,8 +50,13 @@ if ROOT not in sys.path:
 METRIC = "point-iters/s (K·v) vs HBM roofline; served solves/s, p99 at W1 relerr≤1e-4"
 UNIT = "point-iters/s"
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_MD = os.path.join(ROOT, "profiles", "k_apply_graded_1d_2e20.md")
-KERNEL_SOURCES = ["paper_2605_26659_gb300/csrc/apply.cuh", "paper_2605_26659_gb300/csrc/dev_common.cuh"]
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_half_graded_1d_2e20.md")
+KERNEL_SOURCES = ["paper_2605_26659_gb300/csrc/half.cuh", "paper_2605_26659_gb300/csrc/dev_common.cuh"]
+# algorithmic bytes of one kernel application per merged point (N = M): x 8,
+# y 8, input potentials 8, reference potentials 8, masses 4, new potentials 8
+# per output point, i.e. 44 N bytes = 22 B per merged point
+ALG_BYTES_PER_POINT = 22.0
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "full_config2.json")
 
 
 def parse():
@@ -78,6 +83,8 @@ def parse():
                     help="batch: instances solved one at a time in FP64 for the plain-form comparison")
     ap.add_argument("--side", type=int, default=1024, help="2D grid side (default 1024)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="1d: skip the served and batched sub-results of the default line")
     return ap.parse_args()
 
 
@@ -438,7 +445,7 @@ def _concat_batch(probs):
     return cat("x"), cat("y"), cat("u"), cat("v"), offx, offy, [q.eps for q in probs]
 
 
-def run_finom_batch(args, ws, rank, local):
+def run_finom_batch(args, ws, rank, local, emit=True):
     import torch
 
     from paper_2605_26659_gb300 import api, inputs
@@ -478,7 +485,7 @@ def run_finom_batch(args, ws, rank, local):
     total_ms = max_over_ranks(float(sum(s.elapsed_time(e) for s, e in evs)), ws)
     step_s = total_ms / 1e3 / args.steps
     value = ws * L * args.steps / (total_ms / 1e3)
-    bytes_per_step = 2 * 0.5 * (8.25 * L + 32.0 * L)   # two half steps, 20.125 B per merged point
+    bytes_per_step = 2 * ALG_BYTES_PER_POINT * L   # two half steps
     peak, peak_kind = peaks()
     achieved = bytes_per_step / step_s / 1e9
     api.finom_plan_destroy(plan)
@@ -527,7 +534,7 @@ def run_finom_batch(args, ws, rank, local):
                "plain_fp64_one_at_a_time": {"solves_per_s": 1.0 / plain_per_solve, "sample": len(plain),
                                             "seconds_per_solve": plain_per_solve}}
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if emit and rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(probs)
     if rank == 0:
         line = {
@@ -546,7 +553,10 @@ def run_finom_batch(args, ws, rank, local):
                          "algorithmic_bytes_per_step": bytes_per_step},
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def _submit_request(srv, pr):
@@ -586,7 +596,7 @@ def _serve_once(api, args, reqs, probs, stages):
     return wall, [done[k] for k in range(len(probs))], peak_active
 
 
-def run_finom_serve(args, ws, rank, local):
+def run_finom_serve(args, ws, rank, local, emit=True):
     """Served solves/s and latency of the serving loop on the arrival process."""
     import numpy as np
     import torch
@@ -671,7 +681,11 @@ def run_finom_serve(args, ws, rank, local):
             w1_dev.append(abs(res[k]["w1"] - r1["w1"]) / abs(r1["w1"]))
     plain_per_solve = sum(plain) / len(plain)
     peak, peak_kind = peaks()
-    achieved = 20.125 * pts / wall / 1e9   # algorithmic bytes of every half step served
+    # algorithmic bytes of every application served: 22 B per merged point
+    # (1D), 36 B per grid point (2D), two applications per iteration
+    alg = sum(r["iters"] * (2 * ALG_BYTES_PER_POINT * (len(q.x) + len(q.y)) if hasattr(q, "x") else 72.0 * q.U.size)
+              for q, r in zip(probs, res))
+    achieved = alg / wall / 1e9
     if rank == 0:
         line = {
             "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws,
@@ -695,7 +709,7 @@ def run_finom_serve(args, ws, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "every k_apply launch of the served solves, over the wall time",
-                         "algorithmic_bytes": 20.125 * pts},
+                         "algorithmic_bytes": alg},
             "clocks": clocks,
             "e2e": {"value": solves_per_s, "unit": "solves/s", "h2d_bytes_per_step": h2d / len(probs),
                     "d2h_bytes_per_step": d2h / len(probs)},
@@ -706,7 +720,10 @@ def run_finom_serve(args, ws, rank, local):
             "rate_sweep": sweep,
             "cpu_baseline": None,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def cpu_baseline_batch(probs, budget_s=12.0):
@@ -756,8 +773,8 @@ def run_finom(args, ws, rank, local):
     step_s = total_ms / 1e3 / args.steps
     value = ws * L * args.steps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (the fused half step; two launches per step)
-    bytes_per_launch = 0.5 * (8.25 * L + 32.0 * (N + M))
+    # roofline of the dominant kernel (the half step; two launches per step)
+    bytes_per_launch = ALG_BYTES_PER_POINT * L
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / (step_s / 2) / 1e9
     traffic = profiled_traffic()
@@ -787,10 +804,34 @@ def run_finom(args, ws, rank, local):
         e2e = {"value": ws * pts / secs, "unit": UNIT, "h2d_bytes_per_step": 8 * (2 * N + 2 * M),
                "d2h_bytes_per_step": 8 * (N + M), "solve_iters": res["iters"], "converged": res["converged"],
                "marginal_err": res["marginal_err"], "w1": res["w1"], "seconds_per_solve": secs / args.e2e_steps}
+        # the CPU float64 oracle's full solve of the same workload (stored by
+        # tests/golden/make_full_size.py, which calls only the oracle)
+        try:
+            gold = json.load(open(GOLDEN_C2))
+            if gold["N"] == N and gold["M"] == M:
+                e2e["oracle"] = {"w1": gold["w1"], "iters": gold["iters"], "marginal_err": gold["marginal_err"],
+                                 "w1_relerr": abs(res["w1"] - gold["w1"]) / abs(gold["w1"]),
+                                 "source": "tests/golden/full_config2.json (serial C float64 FINOM oracle)"}
+        except (OSError, KeyError, ValueError):
+            pass
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pr)
+
+    # the second half of the metric, bounded so that the default run stays
+    # short: served solves/s with p50 / p99 on the first arrivals of the
+    # serving process, and the batched form, each beside the plain
+    # one-at-a-time FP64 form
+    serve = batch = None
+    if not args.no_sub:
+        sub = argparse.Namespace(**vars(args))
+        sub.requests, sub.plain_count, sub.slots, sub.budget_gb, sub.policy = 100, 4, 64, 64.0, "smallest"
+        sub.rates, sub.eps_stages, sub.warmup = "", 0, 3
+        serve = run_finom_serve(sub, ws, rank, local, emit=False)
+        sub = argparse.Namespace(**vars(args))
+        sub.count, sub.e2e_count, sub.plain_count, sub.steps, sub.warmup, sub.e2e_steps = 4096, 512, 8, 10, 3, 1
+        batch = run_finom_batch(sub, ws, rank, local, emit=False)
 
     if rank == 0:
         line = {
@@ -801,12 +842,21 @@ def run_finom(args, ws, rank, local):
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "finom::k_apply<float, 113|89> (fused half steps)",
-                         "algorithmic_bytes_per_launch": bytes_per_launch},
+                         "kernel": "finom::k_half<float, kHalfY|kHalfX, 8> (half steps on absolute levels)",
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "algorithmic_bytes_per_merged_point": ALG_BYTES_PER_POINT},
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
+        if serve is not None:
+            line["serve"] = {k: serve[k] for k in ("value", "unit", "steps", "latency_s", "converged",
+                                                   "point_iters_per_s", "roofline", "clocks", "e2e",
+                                                   "plain_fp64_one_at_a_time", "config")}
+            line["serve"]["requests"] = serve["steps"]
+        if batch is not None:
+            line["batch"] = {k: batch[k] for k in ("value", "unit", "ms_per_step", "roofline", "clocks", "e2e",
+                                                   "config")}
         print(json.dumps(line), flush=True)
     api.finom_plan_destroy(plan)
 
