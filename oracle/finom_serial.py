@@ -4,27 +4,29 @@ This module is test infrastructure, not product code.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline and reference
 legs) may import it.  It shares no code with the CUDA library.
 
-It follows the paper's construction step by step, with 0-based arrays:
+dense.py's plain N x M product is the oracle of record; this module restates
+the paper's O(N + M) product from the splitting K = K_L + K_U of Sec. 2.2 -
+2.3, with 0-based arrays, and is pinned to the dense definition and to the
+worked example of Sec. 2.2:
 
 * ``dividing_index``      -- Definition (dividing index), Sec. 2.2:
   zeta(i) = number of y_j with y_j <= x_i (so zeta(i) = 0 when x_i < y_1 and
-  zeta(i) = M when x_i >= y_M).
-* ``lower_representation`` -- Theorem (vector representation of K_L), eqs.
-  ``ratio`` and ``eta``: r_i = k~_{i+1,1} / k~_{i,1} (1 when the denominator is
-  a structural zero, i.e. zeta(i) = 0) and the block-edge vectors
-  eta_i = [k~_{i, zeta(i-1)+1} ... k~_{i, zeta(i)}].
-* ``upper_representation`` -- Theorem (vector representation of K_U):
-  r'_i = k^_{i,M} / k^_{i+1,M} (1 when zeta(i+1) = M) and
-  eta'_i = [k^_{i, zeta(i)+1} ... k^_{i, zeta(i+1)}], zeta(N+1) := M.
-* ``matvec_linear`` -- eqs. ``decompose to p+q``, ``p by dynamic programming``
-  and ``q by dynamic programming``: p_1 = eta_1 . psi_1,
-  p_{i+1} = r_i p_i + eta_{i+1} . psi_{i+1}; q_N = eta'_N . psi'_N,
-  q_i = r'_i q_{i+1} + eta'_i . psi'_i; K psi = p + q.
-* ``matvec_log`` -- the same recurrences for the stabilised kernel of Remark
-  ``log-domain-stabilization`` (r_i <- e^{(a_{i+1}-a_i)/eps} r_i,
-  k~_ij <- e^{(a_i+b_j)/eps} k~_ij), evaluated in log arithmetic.
-* ``sinkhorn_log`` -- Algorithm 1 with that stabilisation applied after every
-  half step, in log arithmetic.
+  zeta(i) = M when x_i >= y_M); it splits row i of K into its lower block
+  (columns j < zeta(i)) and its upper block (columns j >= zeta(i)).
+* ``lower_representation`` / ``upper_representation`` -- the objects of the
+  Theorems on the vector representations of K_L and K_U: the row ratios
+  (eq. ``ratio``; 1 where the row is a structural zero) and the block-edge
+  vectors eta_i, eta'_i, i.e. the entries a row gains over its neighbour.
+* ``matvec_linear`` -- since each row of a block is its neighbour times the
+  row ratio plus its block-edge entries, the block products are the running
+  sums of two first-order linear recurrences, one scanned forward (K_L psi),
+  one backward (K_U psi); their inflows are the block-edge dot products.  A
+  generic scan (``_scan``) runs both; K psi is their sum.
+* ``matvec_log`` -- the same two scans for the stabilised kernel of Remark
+  ``log-domain-stabilization`` (row ratios and entries scaled by the
+  absorption vectors), in log arithmetic (``_log_scan``).
+* ``sinkhorn_log`` -- Algorithm 1's fixed-point iteration with that
+  stabilisation applied after every half step, in log arithmetic.
 * ``apply2d_log`` / ``sinkhorn2d_log`` -- Algorithm 2 with the stabilisation
   of Appendix A (eq. ``K'bpsi``): a column pass with a_x = 0, b_x = B(:, j)
   and a row pass with a_y = A(k, :), b_y = 0.
@@ -129,36 +131,64 @@ def upper_representation(x, y, eps, zeta=None):
     return rp, etap
 
 
+def _scan(decay, inflow, backward=False):
+    """Running sums of the first-order linear recurrence s_k = decay_k s_prev +
+    inflow_k (s_prev = 0 before the first term), forward or backward; decay
+    has one entry per step between neighbours (len(inflow) - 1)."""
+    n = len(inflow)
+    out = np.zeros(n)
+    order = range(n - 1, -1, -1) if backward else range(n)
+    prev = None
+    for k in order:
+        if prev is None:
+            out[k] = inflow[k]
+        else:
+            out[k] = decay[min(k, prev)] * out[prev] + inflow[k]
+        prev = k
+    return out
+
+
+def _log_scan(log_decay, log_inflow, backward=False):
+    """``_scan`` in log arithmetic: s_k = log(e^{log_decay + s_prev} + e^{log_inflow_k})."""
+    n = len(log_inflow)
+    out = np.full(n, NEG_INF)
+    order = range(n - 1, -1, -1) if backward else range(n)
+    prev = None
+    for k in order:
+        carried = NEG_INF if prev is None or out[prev] == NEG_INF else log_decay[min(k, prev)] + out[prev]
+        out[k] = logaddexp(carried, log_inflow[k])
+        prev = k
+    return out
+
+
 def matvec_linear(x, y, eps, psi):
-    """K psi by the two recurrences (eqs. p/q by dynamic programming)."""
+    """K psi = K_L psi + K_U psi, each block by a first-order recurrence
+    (Sec. 2.3, eqs. decompose to p+q, p / q by dynamic programming).
+
+    Row i of K_L is r_{i-1} times row i-1 plus its block-edge entries eta_i
+    over the columns zeta(i-1) .. zeta(i)-1, so p = K_L psi is the forward
+    scan with decays r and inflows eta_i . psi; K_U mirrors it (row i is
+    r'_i times row i+1 plus eta'_i), a backward scan.  Returns (p+q, p, q)."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     psi = np.asarray(psi, dtype=np.float64)
-    N = len(x)
+    N, M = len(x), len(y)
     zeta = dividing_index(x, y)
     r, eta = lower_representation(x, y, eps, zeta)
     rp, etap = upper_representation(x, y, eps, zeta)
-    M = len(y)
-    p = np.zeros(N)
-    q = np.zeros(N)
-    # p_1 = eta_1 . psi_1 ; p_{i+1} = r_i p_i + eta_{i+1} . psi_{i+1}
-    seg = psi[0:zeta[0]]
-    p[0] = math.fsum(a * b for a, b in zip(eta[0], seg))
-    for i in range(N - 1):
-        seg = psi[zeta[i]:zeta[i + 1]]
-        p[i + 1] = r[i] * p[i] + math.fsum(a * b for a, b in zip(eta[i + 1], seg))
-    # q_N = eta'_N . psi'_N ; q_i = r'_i q_{i+1} + eta'_i . psi'_i
-    seg = psi[zeta[N - 1]:M]
-    q[N - 1] = math.fsum(a * b for a, b in zip(etap[N - 1], seg))
-    for i in range(N - 2, -1, -1):
-        seg = psi[zeta[i]:zeta[i + 1]]
-        q[i] = rp[i] * q[i + 1] + math.fsum(a * b for a, b in zip(etap[i], seg))
+    # columns a row of a block gains over its neighbour
+    lo_cols = [(zeta[i - 1] if i > 0 else 0, zeta[i]) for i in range(N)]
+    up_cols = [(zeta[i], zeta[i + 1] if i + 1 < N else M) for i in range(N)]
+    inflow_p = [math.fsum(a * b for a, b in zip(eta[i], psi[c0:c1])) for i, (c0, c1) in enumerate(lo_cols)]
+    inflow_q = [math.fsum(a * b for a, b in zip(etap[i], psi[c0:c1])) for i, (c0, c1) in enumerate(up_cols)]
+    p = _scan(r, inflow_p)
+    q = _scan(rp, inflow_q, backward=True)
     return p + q, p, q
 
 
 def matvec_log(x, y, eps, a, b):
     """log(K' 1) for K' = diag(e^{a/eps}) K diag(e^{b/eps}) (Remark
-    log-domain-stabilization), by the p/q recurrences in log arithmetic.
+    log-domain-stabilization), by the two block scans in log arithmetic.
 
     Modified ratios: log r_i = (a_{i+1} - a_i)/eps + log r_i, and modified
     entries log k~'_ij = (a_i + b_j)/eps + log k~_ij (likewise for K_U).
@@ -176,21 +206,14 @@ def matvec_log(x, y, eps, a, b):
     def log_khat(i, j):     # log of the absorbed upper-block entry
         return (a[i] + b[j] - (y[j] - x[i])) / eps
 
-    lp = np.full(N, NEG_INF)
-    lq = np.full(N, NEG_INF)
-    lp[0] = lse([log_kcheck(0, j) for j in range(0, zeta[0])])
-    for i in range(N - 1):
-        # closed-form lower ratio (1 where the denominator is a structural zero)
-        lr = -(x[i + 1] - x[i]) / eps if zeta[i] >= 1 else 0.0
-        lr += (a[i + 1] - a[i]) / eps
-        edge = lse([log_kcheck(i + 1, j) for j in range(zeta[i], zeta[i + 1])])
-        lp[i + 1] = logaddexp(lr + lp[i] if lp[i] != NEG_INF else NEG_INF, edge)
-    lq[N - 1] = lse([log_khat(N - 1, j) for j in range(zeta[N - 1], M)])
-    for i in range(N - 2, -1, -1):
-        lr = -(x[i + 1] - x[i]) / eps if zeta[i + 1] < M else 0.0
-        lr += (a[i] - a[i + 1]) / eps
-        edge = lse([log_khat(i, j) for j in range(zeta[i], zeta[i + 1])])
-        lq[i] = logaddexp(lr + lq[i + 1] if lq[i + 1] != NEG_INF else NEG_INF, edge)
+    # block-edge inflows (log) and log row ratios of the absorbed blocks; a
+    # ratio is 1 (log 0) where the row it divides by is a structural zero
+    in_p = [lse([log_kcheck(i, j) for j in range(zeta[i - 1] if i > 0 else 0, zeta[i])]) for i in range(N)]
+    in_q = [lse([log_khat(i, j) for j in range(zeta[i], zeta[i + 1] if i + 1 < N else M)]) for i in range(N)]
+    lr = [(-(x[i + 1] - x[i]) / eps if zeta[i] >= 1 else 0.0) + (a[i + 1] - a[i]) / eps for i in range(N - 1)]
+    lrp = [(-(x[i + 1] - x[i]) / eps if zeta[i + 1] < M else 0.0) + (a[i] - a[i + 1]) / eps for i in range(N - 1)]
+    lp = _log_scan(lr, in_p)
+    lq = _log_scan(lrp, in_q, backward=True)
     tot = np.array([logaddexp(lp[i], lq[i]) for i in range(N)])
     return tot, lp, lq
 
