@@ -38,7 +38,7 @@ extern "C" {
 typedef enum {
   FINOM_OK = 0,
   FINOM_EINVAL = 1,           /* invalid argument: sizes, eps, unsorted or non-finite meshes, bad masses */
-  FINOM_ENOMEM = 2,           /* a device allocation failed */
+  FINOM_ENOMEM = 2,           /* a device (or, in the serving calls, host) allocation failed */
   FINOM_ECUDA = 3,            /* a CUDA runtime call failed (message in finom_last_error) */
   FINOM_EDEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up */
   FINOM_ENOTSUP = 5,          /* the plan's precision or kind does not support the call */
@@ -364,7 +364,11 @@ finom_status finom_server_submit_2d(finom_server_t srv, const double* x1, const 
 /*
  * finom_server_step -- one scheduling round (see above).  Returns the number
  * of queued, active and finished-but-not-collected requests (any pointer may
- * be NULL).  Errors of a request are reported through its result, not here.
+ * be NULL).  Errors of a request are reported through its result, not here:
+ * a request whose admission or finish fails (device memory, or host memory
+ * for its result) is released with that status and can be collected.
+ * FINOM_ENOMEM when the round's own host bookkeeping cannot be allocated;
+ * then nothing has changed and the round can be retried.
  */
 finom_status finom_server_step(finom_server_t srv, int32_t* n_pending, int32_t* n_active, int32_t* n_finished);
 

@@ -569,19 +569,12 @@ finom_status finom_plan_2d(const double* x1, const double* x2, int64_t N, const 
     set_error("finom_plan_2d: grid too large (N*M <= 2^31 points per grid)");
     return FINOM_EINVAL;
   }
-  finom_plan_s* p = new (std::nothrow) finom_plan_s();
-  if (!p) return FINOM_ENOMEM;
-  p->eps = eps;
-  p->prec = prec;
-  cudaGetDevice(&p->device);
-  finom_status rc = plan2d_build(p, x1, x2, N, y1, y2, M, (cudaStream_t)stream);
-  if (rc != FINOM_OK) {
-    plan2d_free(p);
-    delete p;
-    return rc;
-  }
-  *out = p;
-  return FINOM_OK;
+  // the d = 2 case of a d-dimensional plan: axis 0 merges x1 with x2, axis 1
+  // y1 with y2; grid points (k, i) at k + N i are axis 0 fastest
+  const int64_t n[2] = {N, M};
+  const double* xs[2] = {x1, y1};
+  const double* ys[2] = {x2, y2};
+  return finom_plan_nd(2, n, xs, ys, eps, prec, stream, out);
 }
 
 finom_status finom_plan_nd(int32_t d, const int64_t* n, const double* const* xs, const double* const* ys,
@@ -710,7 +703,7 @@ finom_status finom_plan_batch_elems(const double* x, const int64_t* offx, const 
 
 finom_status finom_plan_set_elems(finom_plan_t plan, int32_t elems, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
-  if (plan->dim != 1 || plan->B > 0) {
+  if (plan->dim != 1 || plan->nd || plan->B > 0) {
     set_error("finom_plan_set_elems: only 1D single-problem plans choose their tile size");
     return FINOM_ENOTSUP;
   }
@@ -809,8 +802,8 @@ finom_status finom_plan_info(finom_plan_t plan, int64_t* N, int64_t* M, double* 
 finom_status finom_dividing_index(finom_plan_t plan, int32_t* zeta, int32_t* zetaT, void* stream) {
   if (bad_plan(plan)) return FINOM_EINVAL;
   if (batch_plan(plan, "finom_dividing_index")) return FINOM_ENOTSUP;
-  if (plan->dim != 1) {
-    set_error("finom_dividing_index: a 2D plan has one dividing index per axis; use 1D plans of the axes");
+  if (plan->dim != 1 || plan->nd) {
+    set_error("finom_dividing_index: a grid plan has one dividing index per axis; use 1D plans of the axes");
     return FINOM_ENOTSUP;
   }
   DeviceGuard dg(plan->device);

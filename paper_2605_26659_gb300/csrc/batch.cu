@@ -1,30 +1,32 @@
 // Batches of independent 1D instances in one launch per half step.
 //
 // Thousands of Sinkhorn solves of uneven sizes (each its own mesh pair, eps
-// and masses) run as one sequence of launches of the fused half-step kernel:
-// the instances' merged sequences are packed one after another, each starting
-// on a tile boundary, so that a tile belongs to one instance and every kernel
-// unit (a tile) finds its instance in a table.  After each half step,
-// k_batch_end gives every instance a warp that scans its tile maps into the
-// carries of the next application, sums its marginal error, counts its
-// iterations and retires it when it has converged (its tiles are skipped from
-// then on).  The loop is captured in a CUDA graph and runs until the last
-// instance has retired.
+// and masses) run as one sequence of launches of the half-step kernel
+// (half.cuh, H_BATCH): the instances' merged sequences are packed one after
+// another, each starting on a tile boundary, so that a tile belongs to one
+// instance and every kernel unit (a tile of the active list) finds its
+// instance in a table.  Every point carries its levels beta+- = b +- Z with
+// Z = z / (eps_b ln 2) in its own instance's eps.  After each half step,
+// k_batch_end gives every instance a warp that scans its tile aggregates into
+// the carries of the next application, sums its marginal error, counts its
+// iterations and retires it when it has converged (its tiles leave the
+// active list).  The loop is captured in a CUDA graph and runs until the
+// last instance has retired.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
-#include "apply.cuh"
 #include "finom_internal.h"
+#include "half.cuh"
 
 namespace finom {
 
 template <class R>
-finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s);
+finom_status half_launch(const HalfArgs<R>&, int, int, cudaStream_t);
 template <class R>
-void fill_pot(void*, int64_t, double, cudaStream_t);
+void log_mass(const double*, int64_t, void*, cudaStream_t);
 void fill_d(double*, int64_t, double, cudaStream_t);
 
 namespace {
@@ -83,7 +85,7 @@ __global__ void k_bpos(const double* a, int64_t n, const int64_t* offa, const do
 // packed position (the packed length is a whole number of tiles)
 __global__ void k_bgaps(const double* z, const uint8_t* type, const int32_t* tinst, const int32_t* itile,
                         const int64_t* offx, const int64_t* offy, const double* ieps, int64_t tile,
-                        int64_t total, double* gap64, float* gap32, uint32_t* bits) {
+                        int64_t total, double* gap64, uint32_t* bits) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool live = k < total;
   int ty = 0;
@@ -101,7 +103,6 @@ __global__ void k_bgaps(const double* z, const uint8_t* type, const int32_t* tin
   if (!live) return;
   if ((threadIdx.x & 31) == 0) bits[k >> 5] = w;
   gap64[k] = gv;
-  if (gap32) gap32[k] = (float)gv;
 }
 
 // tile_x0 of every instance: C_b + 1 entries from itile[b] + b, the number of
@@ -160,17 +161,32 @@ __global__ void k_bmass(const double* u, const int64_t* off, Mass* m, double* m6
   }
 }
 
-__device__ __forceinline__ double bload_pot(const float2* p, int64_t i) {
-  const float2 q = p[i];
-  return (double)q.x + (double)q.y;
+__device__ __forceinline__ void bput(float4* p, double bp, double bm) {
+  const float ph = (float)bp, mh = (float)bm;
+  *p = make_float4(ph, (float)(bp - (double)ph), mh, (float)(bm - (double)mh));
 }
-__device__ __forceinline__ double bload_pot(const double* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ void bput(double2* p, double bp, double bm) { *p = make_double2(bp, bm); }
+__device__ __forceinline__ double blevel(float4 v) { return 0.5 * (((double)v.x + (double)v.y) + ((double)v.z + (double)v.w)); }
+__device__ __forceinline__ double blevel(double2 v) { return 0.5 * (v.x + v.y); }
+
+// start levels of every point: b = log2(1 / n_b) (phi = 1/N, psi = 1/M of
+// its instance, Algorithm 1), Z = z / (eps_b ln 2)
+template <class Beta>
+__global__ void k_bbeta_start(const double* z, const int64_t* off, int B, const double* ieps, int64_t n,
+                              Beta* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = find_inst(off, B, i);
+  const double lb = -log2((double)(off[b + 1] - off[b]));
+  const double Z = z[i] / (ieps[b] * kLn2);
+  bput(out + i, lb + Z, lb - Z);
+}
 
 // potentials of the state each instance stopped in (the buffer of its
-// iteration count, shifted by its resumes): f = eps ln2 (P + log2 m), -inf
-// where m = 0; P into p64
-template <class Pot>
-__global__ void k_bexport(const Pot* pa, const Pot* pb, const double* m64, const int64_t* off, int B,
+// iteration count, shifted by its resumes): f = eps ln2 b (-inf where m = 0)
+// and the smooth potential P = b - log2 m (0 where m = 0) into p64
+template <class Beta>
+__global__ void k_bexport(const Beta* pa, const Beta* pb, const double* m64, const int64_t* off, int B,
                           const int32_t* ictl, const double* ieps, int64_t n, double* f, double* p64) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -183,10 +199,10 @@ __global__ void k_bexport(const Pot* pa, const Pot* pb, const double* m64, const
     f[i] = ieps[b] * log(1.0 / (double)(off[b + 1] - off[b]));
     return;
   }
-  const double P = bload_pot(q ? pb : pa, i);
-  p64[i] = P;
+  const double lv = blevel((q ? pb : pa)[i]);
   const double w = m64[i];
-  f[i] = (w > 0.0) ? ieps[b] * kLn2 * (P + log2(w)) : -INFINITY;
+  p64[i] = (w > 0.0) ? lv - log2(w) : 0.0;
+  f[i] = (w > 0.0) ? ieps[b] * kLn2 * lv : -INFINITY;
 }
 
 // 1/n of each point's instance (the start weights)
@@ -198,8 +214,8 @@ __global__ void k_buniform(const int64_t* off, int B, int64_t n, double* out) {
 }
 
 // dst[i] = src[i] for the points of the instances flagged in swap
-template <class Pot>
-__global__ void k_bswap(Pot* dst, const Pot* src, const int64_t* off, int B, const int32_t* swap, int64_t n) {
+template <class T>
+__global__ void k_bswap(T* dst, const T* src, const int64_t* off, int B, const int32_t* swap, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (swap[find_inst(off, B, i)]) dst[i] = src[i];
@@ -225,8 +241,8 @@ template <class R>
 struct BatchEndArgs {
   const int32_t* itile;
   int B;
-  const R* agg;       // 6 per tile: maps of the next application
-  R* carry;           // 4 per tile
+  const R* agg;       // 2 kSt per tile: tile aggregates of the next application (forward | backward)
+  R* carry;           // 2 kSt per tile
   const double* part; // per tile: error partials
   int32_t* ictl;      // 6 x B: done | completed iterations | iterations at exit | converged | parity flip |
                       //        iteration budget (0: maxit)
@@ -244,10 +260,35 @@ __device__ __forceinline__ void retire(int32_t* ctrl) {
   if (atomicSub(ctrl + 2, 1) == 1) ctrl[1] = 1;
 }
 
-// After a half step: one warp per instance.  Its tile maps become carries
-// (forward and backward, 32 tiles per step of a running state), its error
-// partials its loop-head error (Algorithm 1 check), and its iteration count
-// and retirement are updated.
+// carries of one direction of one instance (a warp): the log-sum of the
+// aggregates of the tiles before (dir 0) or after (dir 1) each tile, 32
+// tiles per step of a running state
+template <class R, int dir>
+__device__ __forceinline__ void bend_carries(const BatchEndArgs<R>& a, int t0, int nt, int lane) {
+  using H = HT<R>;
+  constexpr int kS = H::kSt;
+  St<R> run = st_empty<R>();
+  for (int c = 0; c < nt; c += 32) {
+    const int t = dir == 0 ? c + lane : nt - 1 - c - lane;
+    const bool in = dir == 0 ? t < nt : t >= 0;
+    St<R> inc = st_empty<R>();
+    if (in) H::get(a.agg + 2 * kS * (int64_t)(t0 + t) + dir * kS, inc.M, inc.s);
+#pragma unroll 1
+    for (int o = 1; o < 32; o <<= 1) {
+      const St<R> u = st_shfl_up(inc, o);
+      if (lane >= o) inc = st_comb(u, inc);
+    }
+    St<R> ex = st_shfl_up(inc, 1);
+    if (lane == 0) ex = st_empty<R>();
+    const St<R> st = st_comb(run, ex);
+    if (in) H::put(a.carry + 2 * kS * (int64_t)(t0 + t) + dir * kS, st.M, st.s);
+    run = st_comb(run, st_shfl_idx(inc, 31));
+  }
+}
+
+// After a half step: one warp per instance.  Its tile aggregates become
+// carries (forward and backward), its error partials its loop-head error
+// (Algorithm 1 check), and its iteration count and retirement are updated.
 template <class R>
 __global__ void k_batch_end(BatchEndArgs<R> a) {
   const int lane = threadIdx.x & 31;
@@ -257,50 +298,8 @@ __global__ void k_batch_end(BatchEndArgs<R> a) {
   if (*done) return;
   const int t0 = a.itile[b], nt = a.itile[b + 1] - t0;
   if (a.maps) {
-    // forward: lane = tile of the chunk, left to right
-    LS<R> run = ls_empty<R>();
-    for (int c0 = 0; c0 < nt; c0 += 32) {
-      const int t = c0 + lane;
-      const bool in = t < nt;
-      Agg<R> inc = in ? ld_map(a.agg + 6 * (int64_t)(t0 + t)) : agg_identity<R>();
-#pragma unroll 1
-      for (int o = 1; o < 32; o <<= 1) {
-        const Agg<R> tt = shfl_up_agg(inc, o);
-        if (lane >= o) inc = agg_then(tt, inc);
-      }
-      Agg<R> ex = shfl_up_agg(inc, 1);
-      if (lane == 0) ex = agg_identity<R>();
-      const LS<R> st = agg_apply(ex, run);
-      if (in) {
-        a.carry[4 * (int64_t)(t0 + t) + 0] = st.m;
-        a.carry[4 * (int64_t)(t0 + t) + 1] = st.s;
-      }
-      const Agg<R> tot = {__shfl_sync(0xffffffffu, inc.D, 31), __shfl_sync(0xffffffffu, inc.m, 31),
-                          __shfl_sync(0xffffffffu, inc.s, 31)};
-      run = agg_apply(tot, run);
-    }
-    // backward: lane = tile of the chunk, right to left
-    run = ls_empty<R>();
-    for (int c1 = nt; c1 > 0; c1 -= 32) {
-      const int t = c1 - 1 - lane;
-      const bool in = t >= 0;
-      Agg<R> inc = in ? ld_map(a.agg + 6 * (int64_t)(t0 + t) + 3) : agg_identity<R>();
-#pragma unroll 1
-      for (int o = 1; o < 32; o <<= 1) {
-        const Agg<R> tt = shfl_up_agg(inc, o);
-        if (lane >= o) inc = agg_then(tt, inc);
-      }
-      Agg<R> ex = shfl_up_agg(inc, 1);
-      if (lane == 0) ex = agg_identity<R>();
-      const LS<R> st = agg_apply(ex, run);
-      if (in) {
-        a.carry[4 * (int64_t)(t0 + t) + 2] = st.m;
-        a.carry[4 * (int64_t)(t0 + t) + 3] = st.s;
-      }
-      const Agg<R> tot = {__shfl_sync(0xffffffffu, inc.D, 31), __shfl_sync(0xffffffffu, inc.m, 31),
-                          __shfl_sync(0xffffffffu, inc.s, 31)};
-      run = agg_apply(tot, run);
-    }
+    bend_carries<R, 0>(a, t0, nt, lane);
+    bend_carries<R, 1>(a, t0, nt, lane);
   }
   if (a.err) {
     double e = 0.0;
@@ -365,19 +364,20 @@ finom_status ensure_state_batch(finom_plan_s* p) {
   SolveState& st = p->st;
   if (st.ready) return FINOM_OK;
   const int64_t N = p->N, M = p->M, T = p->C, B = p->B;
-  const size_t ps = sizeof(typename Tr<R>::Pot), ms = sizeof(typename Tr<R>::Mass);
+  const size_t bs = sizeof(typename HT<R>::Beta), ls = sizeof(typename HT<R>::Lv);
+  const size_t per_tile = 2 * HT<R>::kSt;
   for (int q = 0; q < 2; ++q) {
-    FINOM_CUDA(cudaMalloc(&st.px[q], ps * N));
-    FINOM_CUDA(cudaMalloc(&st.py[q], ps * M));
+    FINOM_CUDA(cudaMalloc(&st.px[q], bs * N));
+    FINOM_CUDA(cudaMalloc(&st.py[q], bs * M));
   }
-  FINOM_CUDA(cudaMalloc(&st.mu, ms * N));
-  FINOM_CUDA(cudaMalloc(&st.nu, ms * M));
+  FINOM_CUDA(cudaMalloc(&st.qom, ls * N));   // log2 masses of x
+  FINOM_CUDA(cudaMalloc(&st.qwm, ls * M));   // log2 masses of y
   FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * N));
   FINOM_CUDA(cudaMalloc(&st.nu64, sizeof(double) * M));
   FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * std::max<int64_t>(N, 512)));
   FINOM_CUDA(cudaMalloc(&st.ty, sizeof(double) * std::max<int64_t>(M, 512)));
-  FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * 6 * T));
-  FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * 4 * T));
+  FINOM_CUDA(cudaMalloc(&st.aggs, sizeof(R) * per_tile * T));
+  FINOM_CUDA(cudaMalloc(&st.carries, sizeof(R) * per_tile * T));
   FINOM_CUDA(cudaMalloc(&st.part, sizeof(double) * T));
   FINOM_CUDA(cudaMalloc(&st.scal, sizeof(double) * std::max<int64_t>(520, 2 * B)));
   FINOM_CUDA(cudaMalloc(&st.ctrl, sizeof(int32_t) * 8));
@@ -385,7 +385,6 @@ finom_status ensure_state_batch(finom_plan_s* p) {
   FINOM_CUDA(cudaMalloc(&st.ictl, sizeof(int32_t) * 6 * B));
   FINOM_CUDA(cudaMalloc(&st.ierr, sizeof(double) * B));
   FINOM_CUDA(cudaMalloc(&st.itol, sizeof(double) * B));
-  FINOM_CUDA(cudaMalloc(&st.iuni, sizeof(R) * 2 * B));
   FINOM_CUDA(cudaMalloc(&st.alist, sizeof(int32_t) * T));
   FINOM_CUDA(cudaMemset(st.ctrl, 0, sizeof(int32_t) * 8));
   FINOM_CUDA(cudaMemset(st.part, 0, sizeof(double) * T));
@@ -394,51 +393,48 @@ finom_status ensure_state_batch(finom_plan_s* p) {
   return FINOM_OK;
 }
 
+// the half step of parity q (psi: o_is_x = false, levels py[q] -> py[1-q]
+// against phi px[q]; phi: px[q] -> px[1-q] against psi py[1-q]), or with
+// mode the aggregate / check launch of that application
 template <class R>
-ApplyArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q, bool start) {
-  using Pot = typename Tr<R>::Pot;
-  using Mass = typename Tr<R>::Mass;
+HalfArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q) {
+  using Beta = typename HT<R>::Beta;
+  using Lv = typename HT<R>::Lv;
   SolveState& st = p->st;
-  ApplyArgs<R> a{};
+  HalfArgs<R> a{};
   a.tbits = p->tbits;
-  a.gap = (const R*)p->gap;
   a.tile_x0 = p->tile_x0;
-  a.C = (int)p->C;   // units: all tiles of all instances
-  a.elems = (int)(p->btile / kThreads);
-  a.lines = 1;
-  a.o_es = 1;
-  a.w_es = 1;
+  a.L = p->L;
+  a.C = (int)p->C;   // grid sizing: all tiles of all instances
+  a.o_is_x = o_is_x ? 1 : 0;
   a.tinst = p->tinst;
   a.itile = p->itile;
   a.ioffx = p->ioffx;
   a.ioffy = p->ioffy;
-  a.idone = st.ictl;
   a.alist = st.alist;
   a.acount = st.ctrl + 3;
-  a.iuni = start ? (const R*)st.iuni : nullptr;
   a.agg_out = (R*)st.aggs;
   a.carry_in = (const R*)st.carries;
-  a.carry_out = (R*)st.carries;
   a.part = st.part;
   a.scal = st.scal;
   a.ctrl = st.ctrl;
-  a.o_is_x = o_is_x ? 1 : 0;
   if (!o_is_x) {   // psi <- v / (K^T phi)
-    a.pO = (const Pot*)st.py[q];
-    a.mO = (const Mass*)st.nu;
-    a.pO_out = (Pot*)st.py[1 - q];
-    a.pW = (const Pot*)st.px[q];
-    a.mW = (const Mass*)st.mu;
-    a.flags = kModeBHalfY;
+    a.bO = (const Beta*)st.py[q];
+    a.bO_out = (Beta*)st.py[1 - q];
+    a.bW = (const Beta*)st.px[q];
+    a.lmO = (const Lv*)st.qwm;
   } else {         // phi <- u / (K psi)
-    a.pO = (const Pot*)st.px[q];
-    a.mO = (const Mass*)st.mu;
-    a.pO_out = (Pot*)st.px[1 - q];
-    a.pW = (const Pot*)st.py[1 - q];
-    a.mW = (const Mass*)st.nu;
-    a.flags = kModeBHalfX;
+    a.bO = (const Beta*)st.px[q];
+    a.bO_out = (Beta*)st.px[1 - q];
+    a.bW = (const Beta*)st.py[1 - q];
+    a.lmO = (const Lv*)st.qom;
   }
   return a;
+}
+
+template <class R>
+finom_status launch_half(finom_plan_s* p, bool o_is_x, int q, int mode, cudaStream_t s) {
+  return half_launch<R>(batch_args<R>(p, o_is_x, q), mode, (int)(p->btile / kThreads), s);
 }
 
 template <class R>
@@ -467,9 +463,9 @@ finom_status launch_end(finom_plan_s* p, int maps, int err, int iter_end, cudaSt
 
 template <class R>
 finom_status batch_iteration(finom_plan_s* p, int q, cudaStream_t s) {
-  finom_status rc = launch_apply<R>(batch_args<R>(p, false, q, false), false, s);
+  finom_status rc = launch_half<R>(p, false, q, kBatchY, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 1, 0, s);
-  if (rc == FINOM_OK) rc = launch_apply<R>(batch_args<R>(p, true, q, false), false, s);
+  if (rc == FINOM_OK) rc = launch_half<R>(p, true, q, kBatchX, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);
   return rc;
 }
@@ -521,17 +517,17 @@ finom_status run_loop(finom_plan_s* p, int64_t maxit, cudaStream_t s) {
 template <class R>
 finom_status evaluate(finom_plan_s* p, double tol, int64_t maxit, double* f, double* g, finom_result* res,
                       cudaStream_t s, double* err64_out, const std::vector<char>* only = nullptr) {
-  using Pot = typename Tr<R>::Pot;
+  using Beta = typename HT<R>::Beta;
   SolveState& st = p->st;
   const int64_t B = p->B, N = p->N, M = p->M;
   std::vector<int32_t> ictl(4 * B);
   std::vector<double> ierr(B);
   FINOM_CUDA(cudaMemcpyAsync(ictl.data(), st.ictl, sizeof(int32_t) * 4 * B, cudaMemcpyDeviceToHost, s));
   FINOM_CUDA(cudaMemcpyAsync(ierr.data(), st.ierr, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
-  k_bexport<Pot><<<nblk(N, 256), 256, 0, s>>>((const Pot*)st.px[0], (const Pot*)st.px[1], st.mu64, p->ioffx,
-                                                (int)B, st.ictl, p->ieps, N, f, st.tx);
-  k_bexport<Pot><<<nblk(M, 256), 256, 0, s>>>((const Pot*)st.py[0], (const Pot*)st.py[1], st.nu64, p->ioffy,
-                                                (int)B, st.ictl, p->ieps, M, g, st.ty);
+  k_bexport<Beta><<<nblk(N, 256), 256, 0, s>>>((const Beta*)st.px[0], (const Beta*)st.px[1], st.mu64, p->ioffx,
+                                                 (int)B, st.ictl, p->ieps, N, f, st.tx);
+  k_bexport<Beta><<<nblk(M, 256), 256, 0, s>>>((const Beta*)st.py[0], (const Beta*)st.py[1], st.nu64, p->ioffy,
+                                                 (int)B, st.ictl, p->ieps, M, g, st.ty);
   double* dual = st.scal;   // 2 x B: sum u f | sum v g per instance
   FINOM_CUDA(cudaMemsetAsync(dual, 0, sizeof(double) * 2 * B, s));
   k_bdot<<<(unsigned)B, 256, 0, s>>>(st.mu64, f, p->ioffx, dual);
@@ -593,15 +589,15 @@ finom_status evaluate(finom_plan_s* p, double tol, int64_t maxit, double* f, dou
 template <class R>
 finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
                          cudaStream_t s) {
-  using Mass = typename Tr<R>::Mass;
+  using Beta = typename HT<R>::Beta;
   finom_status rc = ensure_state_batch<R>(p);
   if (rc != FINOM_OK) return rc;
   SolveState& st = p->st;
   const int64_t B = p->B, N = p->N, M = p->M;
-  // masses, per instance
+  // masses, per instance, and their log2
   FINOM_CUDA(cudaMemsetAsync(st.bad, 0, sizeof(int), s));
-  k_bmass<Mass><<<(unsigned)B, 256, 0, s>>>(u, p->ioffx, (Mass*)st.mu, st.mu64, st.bad);
-  k_bmass<Mass><<<(unsigned)B, 256, 0, s>>>(v, p->ioffy, (Mass*)st.nu, st.nu64, st.bad);
+  k_bmass<double><<<(unsigned)B, 256, 0, s>>>(u, p->ioffx, st.mu64, st.mu64, st.bad);
+  k_bmass<double><<<(unsigned)B, 256, 0, s>>>(v, p->ioffy, st.nu64, st.nu64, st.bad);
   int hbad = 0;
   FINOM_CUDA(cudaMemcpyAsync(&hbad, st.bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   FINOM_CUDA(cudaStreamSynchronize(s));
@@ -609,15 +605,11 @@ finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, doub
     set_error("finom_solve_batch: every instance's masses must be finite, >= 0, with a positive sum");
     return FINOM_EINVAL;
   }
-  // start: phi = 1/N_b, psi = 1/M_b (absorbed potentials 0 with uniform weights)
-  fill_pot<R>(st.px[0], N, 0.0, s);
-  fill_pot<R>(st.py[0], M, 0.0, s);
-  std::vector<R> uni(2 * B);
-  for (int64_t b = 0; b < B; ++b) {
-    uni[2 * b] = (R)(1.0 / (double)(p->hoffx[b + 1] - p->hoffx[b]));
-    uni[2 * b + 1] = (R)(1.0 / (double)(p->hoffy[b + 1] - p->hoffy[b]));
-  }
-  FINOM_CUDA(cudaMemcpyAsync(st.iuni, uni.data(), sizeof(R) * 2 * B, cudaMemcpyHostToDevice, s));
+  log_mass<R>(st.mu64, N, st.qom, s);
+  log_mass<R>(st.nu64, M, st.qwm, s);
+  // start: phi = 1/N_b, psi = 1/M_b
+  k_bbeta_start<Beta><<<nblk(N, 256), 256, 0, s>>>(p->x, p->ioffx, (int)B, p->ieps, N, (Beta*)st.px[0]);
+  k_bbeta_start<Beta><<<nblk(M, 256), 256, 0, s>>>(p->y, p->ioffy, (int)B, p->ieps, M, (Beta*)st.py[0]);
   fill_d(st.itol, B, tol, s);
   FINOM_CUDA(cudaMemsetAsync(st.ictl, 0, sizeof(int32_t) * 6 * B, s));
   FINOM_CUDA(cudaMemsetAsync(st.ierr, 0, sizeof(double) * B, s));
@@ -626,25 +618,21 @@ finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, doub
   st.tol = tol;
   st.maxit = maxit;
   k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3, st.ctrl + 6);
-  // iteration 0: maps of the first K^T phi, then its half step with the
-  // check at the first loop head, then the phi half step
-  ApplyArgs<R> a0 = batch_args<R>(p, false, 0, true);
-  a0.flags = kModeBAgg;
-  rc = launch_apply<R>(a0, false, s);
+  // iteration 0: aggregates of the first K^T phi, then its half step with
+  // the check at the first loop head, then the phi half step
+  rc = launch_half<R>(p, false, 0, kBatchAgg, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 0, s);
   if (rc != FINOM_OK) return rc;
   st.active = true;
   st.launched = 0;
   if (maxit == 0) {
-    a0.flags = kModeBCheck;
-    rc = launch_apply<R>(a0, false, s);
+    rc = launch_half<R>(p, false, 0, kBatchCheck, s);
     if (rc == FINOM_OK) rc = launch_end<R>(p, 0, 1, 0, s);
     return rc;
   }
-  a0.flags = kModeBHalfY;
-  rc = launch_apply<R>(a0, false, s);
+  rc = launch_half<R>(p, false, 0, kBatchY, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 1, 0, s);
-  if (rc == FINOM_OK) rc = launch_apply<R>(batch_args<R>(p, true, 0, false), false, s);
+  if (rc == FINOM_OK) rc = launch_half<R>(p, true, 0, kBatchX, s);
   if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);
   st.launched = 1;
   return rc;
@@ -653,7 +641,7 @@ finom_status begin_batch(finom_plan_s* p, const double* u, const double* v, doub
 template <class R>
 finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
                               double* f, double* g, finom_result* res, cudaStream_t us) {
-  using Pot = typename Tr<R>::Pot;
+  using Beta = typename HT<R>::Beta;
   FINOM_CUDA(cudaStreamSynchronize(us));
   finom_status rc = ensure_state_batch<R>(p);
   if (rc != FINOM_OK) return rc;
@@ -722,14 +710,14 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     FINOM_CUDA(cudaMemcpyAsync(dswap, swap.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s));
     FINOM_CUDA(cudaMemcpyAsync(st.ictl, ictl.data(), sizeof(int32_t) * 6 * B, cudaMemcpyHostToDevice, s));
     FINOM_CUDA(cudaMemcpyAsync(st.itol, itol.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
-    k_bswap<Pot><<<nblk(N, 256), 256, 0, s>>>((Pot*)st.px[0], (const Pot*)st.px[1], p->ioffx, (int)B, dswap, N);
-    k_bswap<Pot><<<nblk(M, 256), 256, 0, s>>>((Pot*)st.py[1], (const Pot*)st.py[0], p->ioffy, (int)B, dswap, M);
+    k_bswap<Beta><<<nblk(N, 256), 256, 0, s>>>((Beta*)st.px[0], (const Beta*)st.px[1], p->ioffx, (int)B, dswap, N);
+    k_bswap<Beta><<<nblk(M, 256), 256, 0, s>>>((Beta*)st.py[1], (const Beta*)st.py[0], p->ioffy, (int)B, dswap, M);
     cudaFreeAsync(dswap, s);
     int32_t c1[8] = {0, 0, n_resume, 0, 0, 0, 1, 0};
     FINOM_CUDA(cudaMemcpyAsync(st.ctrl, c1, sizeof(c1), cudaMemcpyHostToDevice, s));
     k_batch_compact<<<1, 1024, 0, s>>>(p->itile, st.ictl, (int)B, st.alist, st.ctrl + 3, st.ctrl + 6);
     // the phi half step of the stop iterations, at parity 0
-    rc = launch_apply<R>(batch_args<R>(p, true, 0, false), false, s);
+    rc = launch_half<R>(p, true, 0, kBatchX, s);
     if (rc == FINOM_OK) rc = launch_end<R>(p, 1, 0, 1, s);
     if (rc != FINOM_OK) return rc;
   }
@@ -817,14 +805,7 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
   FINOM_CUDA(cudaMemsetAsync(p->tbits, 0, sizeof(uint32_t) * (alloc / 32), s));
   FINOM_CUDA(cudaMalloc(&p->gap64, sizeof(double) * alloc));
   FINOM_CUDA(cudaMemsetAsync(p->gap64, 0, sizeof(double) * alloc, s));
-  float* gap32 = nullptr;
-  if (p->prec == FINOM_F32_LOG) {
-    FINOM_CUDA(cudaMalloc(&gap32, sizeof(float) * alloc));
-    FINOM_CUDA(cudaMemsetAsync(gap32, 0, sizeof(float) * alloc, s));
-    p->gap = gap32;
-  } else {
-    p->gap = p->gap64;
-  }
+  p->gap = p->gap64;
   FINOM_CUDA(cudaMalloc(&p->tile_x0, sizeof(int32_t) * (T + B)));
   FINOM_CUDA(cudaMalloc(&p->tile_x0c, sizeof(int32_t) * (Tc + B)));
   int32_t* itilec = nullptr;
@@ -844,7 +825,7 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
   k_bpos<<<nblk(M, 256), 256, 0, s>>>(p->y, M, p->ioffy, p->x, p->ioffx, p->itile, (int)B, tile, 1, posy, z,
                                        type, 0);
   k_bgaps<<<nblk(total, 256), 256, 0, s>>>(z, type, p->tinst, p->itile, p->ioffx, p->ioffy, p->ieps, tile, total,
-                                            p->gap64, gap32, p->tbits);
+                                            p->gap64, p->tbits);
   k_btiles<<<nblk(T + B, 256), 256, 0, s>>>(posx, p->ioffx, p->itile, (int)B, tile, T + B, p->tile_x0);
   k_btiles<<<nblk(Tc + B, 256), 256, 0, s>>>(posx, p->ioffx, itilec, (int)B, kTile, Tc + B, p->tile_x0c);
   FINOM_CUDA(cudaGetLastError());

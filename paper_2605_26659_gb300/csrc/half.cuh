@@ -72,6 +72,9 @@ enum : int {
   H_FB = 2048,        // axis pass: write log2 of the lower and of the upper block sums apart
                       // (float64, out and out + grid size)
   H_ZLOG = 4096,      // axis pass: the W levels carry log2(z - z_min) of their node as well
+  H_BATCH = 8192,     // batch of independent 1D problems: units are the tiles of the active
+                      // list; carries, errors and loop control per problem come from the
+                      // batch end kernel (no launch tail)
 };
 
 constexpr int kHalfY = H_POT | H_ERR | H_NEXT | H_CHECK_DONE;       // psi <- nu / K^T phi
@@ -93,6 +96,11 @@ constexpr int kLineCheck = H_ERR | H_LINES;
 constexpr int kLineFB = H_FB | H_LINES;
 constexpr int kLineFBZ = H_FB | H_ZLOG | H_LINES;
 constexpr int kLineAggZ = H_AGG | H_ZLOG | H_LINES;
+// batches of independent 1D problems (Algorithm 1 per problem)
+constexpr int kBatchY = H_POT | H_ERR | H_NEXT | H_BATCH;
+constexpr int kBatchX = H_POT | H_NEXT | H_BATCH;
+constexpr int kBatchAgg = H_AGG | H_BATCH;
+constexpr int kBatchCheck = H_ERR | H_BATCH;
 
 // Level arithmetic per precision.  Beta holds (beta+, beta-) of one point.
 template <class R>
@@ -197,6 +205,9 @@ struct HT<float> {
   __device__ __forceinline__ static Lv shfl_down(Lv a, int o) {
     return make_float2(__shfl_down_sync(0xffffffffu, a.x, o), __shfl_down_sync(0xffffffffu, a.y, o));
   }
+  __device__ __forceinline__ static Lv shfl_idx(Lv a, int l) {
+    return make_float2(__shfl_sync(0xffffffffu, a.x, l), __shfl_sync(0xffffffffu, a.y, l));
+  }
 };
 
 template <>
@@ -249,6 +260,7 @@ struct HT<double> {
   }
   __device__ __forceinline__ static Lv shfl_up(Lv a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
   __device__ __forceinline__ static Lv shfl_down(Lv a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+  __device__ __forceinline__ static Lv shfl_idx(Lv a, int l) { return __shfl_sync(0xffffffffu, a, l); }
 };
 
 // log-sum state: value s * 2^M (s = 0: empty)
@@ -295,6 +307,10 @@ template <class R>
 __device__ __forceinline__ St<R> st_shfl_down(const St<R>& a, int o) {
   return {HT<R>::shfl_down(a.M, o), __shfl_down_sync(0xffffffffu, a.s, o)};
 }
+template <class R>
+__device__ __forceinline__ St<R> st_shfl_idx(const St<R>& a, int l) {
+  return {HT<R>::shfl_idx(a.M, l), __shfl_sync(0xffffffffu, a.s, l)};
+}
 
 template <class R>
 struct HalfArgs {
@@ -337,6 +353,17 @@ struct HalfArgs {
   const typename HT<R>::Lv* zO;
   const typename HT<R>::Lv* zlogW; // H_ZLOG: log2(z - z_min) of the W axis nodes (bits)
   int64_t grid;                    // H_FB: grid points (the upper sums follow the lower ones)
+  // H_BATCH: problem b owns the packed tiles itile[b] .. itile[b+1] - 1 (the
+  // first point of each on a tile boundary) and the points ioffx[b] ..
+  // ioffx[b+1] - 1 of x (ioffy of y); tile_x0 holds, from itile[b] + b on,
+  // the x points of problem b before each of its tile boundaries; the
+  // launch handles the acount tiles listed in alist
+  const int32_t* tinst;
+  const int32_t* itile;
+  const int64_t* ioffx;
+  const int64_t* ioffy;
+  const int32_t* alist;
+  const int32_t* acount;
 };
 
 constexpr int kHSlots = kThreads + kThreads / 32;
@@ -501,31 +528,57 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   constexpr bool kLines = (kFlags & H_LINES) != 0;
   constexpr bool kProd = (kFlags & (H_LOG | H_LIN | H_QOUT | H_FB)) != 0;
   constexpr bool kDiv = (kFlags & (H_POT | H_ERR)) != 0;
+  constexpr bool kBatch = (kFlags & H_BATCH) != 0;
   const int tid = threadIdx.x;
 
-  // line mode: unit = line * C + tile; grid index of node i of the line:
-  // gbase + i * inner
-  const int line = kLines ? unit / a.C : 0;
-  const int tile = unit - line * a.C;
+  // The unit's tile: its merged points [k0, kend) in its problem's own
+  // numbering (pk0: the packed position of k0 in the type bits), its x and y
+  // points, and the index of the first x / y point in the point arrays.
+  // Line mode: unit = line * C + tile; grid index of node i of the line:
+  // gbase + i * inner.  Batches: unit = entry of the active tile list.
+  int line = 0, tile, x0, x1;
+  int64_t k0, kend, pk0, xb = 0, yb = 0;
+  if constexpr (kBatch) {
+    tile = a.alist[unit];
+    const int b = a.tinst[tile];
+    const int lt = tile - a.itile[b];
+    const int32_t* tx = a.tile_x0 + a.itile[b] + b;
+    x0 = tx[lt];
+    x1 = tx[lt + 1];
+    xb = a.ioffx[b];
+    yb = a.ioffy[b];
+    const int64_t Lb = (a.ioffx[b + 1] - xb) + (a.ioffy[b + 1] - yb);
+    k0 = (int64_t)lt * kT;
+    kend = min(k0 + (int64_t)kT, Lb);
+    pk0 = (int64_t)tile * kT;
+  } else {
+    line = kLines ? unit / a.C : 0;
+    tile = unit - line * a.C;
+    x0 = a.tile_x0[tile];
+    x1 = a.tile_x0[tile + 1];
+    k0 = (int64_t)tile * kT;
+    kend = min(k0 + (int64_t)kT, a.L);
+    pk0 = k0;
+  }
+  // per-tile slots of the aggregates, carries and error partials
+  const int64_t slot = kBatch ? (int64_t)tile : (int64_t)unit;
   const int64_t inner = kLines ? a.inner : 1;
   const int64_t gbase = kLines ? (line % inner) + (line / inner) * inner * a.nk : 0;
-  const int x0 = a.tile_x0[tile], x1 = a.tile_x0[tile + 1];
-  const int64_t k0 = (int64_t)tile * kT;
-  const int64_t kend = min(k0 + (int64_t)kT, a.L);
   const int y0 = (int)(k0 - x0), y1 = (int)(kend - x1);
-  const int o_start = a.o_is_x ? x0 : y0;
+  const int64_t o_start = a.o_is_x ? xb + x0 : yb + y0;
   const int n_o = a.o_is_x ? (x1 - x0) : (y1 - y0);
-  const int w_start = a.o_is_x ? y0 : x0;
+  const int64_t w_start = a.o_is_x ? yb + y0 : xb + x0;
   const int n_w = a.o_is_x ? (y1 - y0) : (x1 - x0);
   const Beta* bO = a.bO + o_start;
   const Beta* bW = a.bW + w_start;
 
   // 1. local dividing index of the O points of this thread's merged points
   if (!kAgg) {
-    const int64_t seg = k0 + (int64_t)tid * E;
+    const int64_t segl = k0 + (int64_t)tid * E;
+    const int64_t seg = pk0 + (int64_t)tid * E;
     uint32_t omask = 0;
-    if (seg < a.L) {
-      const int64_t nv = a.L - seg;
+    if (segl < kend) {
+      const int64_t nv = kend - segl;
       const uint32_t vmask = nv >= E ? ((1u << E) - 1u) : ((1u << nv) - 1u);
       const uint32_t bits = (a.tbits[seg >> 5] >> (seg & 31)) & ((1u << E) - 1u);
       omask = (a.o_is_x ? bits : ~bits) & vmask;
@@ -570,7 +623,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
     hslot_put(sm, 0, tid, tf);
     hslot_put(sm, 1, tid, tb);
     __syncthreads();
-    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * (int64_t)unit);
+    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * slot);
     return true;
   } else {
   // longest run of the tile (block-uniform trip count); the loads of a run
@@ -610,7 +663,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   const int qo = (int)(((int64_t)(tid + 1) * n_o) / kThreads) - olo;
   St<R> cf = st_empty<R>(), cb = st_empty<R>();
   if (a.carry_in) {
-    const R* c = a.carry_in + 2 * H::kSt * (int64_t)unit;
+    const R* c = a.carry_in + 2 * H::kSt * slot;
     H::get(c, cf.M, cf.s);
     H::get(c + H::kSt, cb.M, cb.s);
   }
@@ -648,7 +701,21 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
     const St<R> B = z < n_w ? Bo : cb;
     {
       const Lv op = H::bp(bo), om = H::bm(bo);
-      if constexpr (kProd) {
+      if constexpr ((kFlags & H_QOUT) != 0 && sizeof(R) == 4) {
+        // log2 of p + q with the O frame 0 (levels +-Z) as a level pair, in
+        // float arithmetic: each block's level, with the binary exponent of
+        // its mantissa sum joined exactly, then the larger one plus log2 of
+        // the mantissas in its frame
+        R m1, m2;
+        const R k1 = H::mant_exp(F.s, m1), k2 = H::mant_exp(B.s, m2);
+        const bool e1 = F.s > R(0) && H::valid(F.M), e2 = B.s > R(0) && H::valid(B.M);
+        const Lv A1 = H::add_lv(H::add_lv(F.M, om), H::mk(k1, R(0)));
+        const Lv A2 = H::add_lv(H::add_lv(B.M, op), H::mk(k2, R(0)));
+        const R D = e1 && e2 ? H::diff(A2, A1) : (e1 ? R(-1000) : R(1000));
+        const bool g2 = D > R(0);
+        const R t = H::lg2_acc(g2 ? fma(m1, H::ex2(-D), m2) : fma(m2, H::ex2(D), m1));
+        if (v) a.q_out[gi] = (e1 || e2) ? H::sub(g2 ? A2 : A1, -t) : H::none();
+      } else if constexpr (kProd) {
         // ln of p + q with the O frame 0 (levels +-Z), in float64
         const double a1 = H::to_double(F.M) + H::to_double(om);
         const double a2 = H::to_double(B.M) + H::to_double(op);
@@ -721,14 +788,14 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
       double tot = 0.0;
 #pragma unroll
       for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
-      a.part[unit] = tot;
+      a.part[slot] = tot;
     }
   }
   if constexpr ((kFlags & H_NEXT) != 0) {
     hslot_put(sm, 0, tid, nf);
     hslot_put(sm, 1, tid, nb);
     __syncthreads();
-    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * (int64_t)unit);
+    if (tid < 64) hrake_reduce(sm, a.agg_out + 2 * H::kSt * slot);
   }
   return true;
   }
@@ -928,6 +995,18 @@ template <class R, int kFlags, int E>
 __global__ void __launch_bounds__(kThreads, half_min_blocks<R, E>()) k_half(HalfArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HalfSmem<R, E>& sm = *reinterpret_cast<HalfSmem<R, E>*>(smem_raw);
+  if constexpr ((kFlags & H_BATCH) != 0) {
+    // the active list and the done flag come from the preceding launch
+    griddep_wait();
+    if (*(volatile int32_t*)(a.ctrl + 1)) return;   // every problem retired
+    griddep_launch_dependents();
+    const int units = *(volatile const int32_t*)a.acount;
+    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+      half_unit<R, kFlags, E>(a, sm, unit, false);
+      __syncthreads();
+    }
+    return;
+  }
   const int units = (kFlags & H_LINES) ? a.lines * a.C : a.C;
   for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
     if (!half_unit<R, kFlags, E>(a, sm, unit, unit == (int)blockIdx.x)) return;   // the loop is done

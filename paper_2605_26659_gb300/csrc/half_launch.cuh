@@ -61,6 +61,10 @@ cudaError_t half_launch_e(const HalfArgs<R>& a, int mode, cudaStream_t s, bool* 
     case kLineY: return half_launch_me<R, kLineY, E>(a, s);
     case kLineX: return half_launch_me<R, kLineX, E>(a, s);
     case kLineCheck: return half_launch_me<R, kLineCheck, E>(a, s);
+    case kBatchY: return half_launch_me<R, kBatchY, E>(a, s);
+    case kBatchX: return half_launch_me<R, kBatchX, E>(a, s);
+    case kBatchAgg: return half_launch_me<R, kBatchAgg, E>(a, s);
+    case kBatchCheck: return half_launch_me<R, kBatchCheck, E>(a, s);
     default: break;
   }
   if constexpr (sizeof(R) == sizeof(double)) {

@@ -16,6 +16,16 @@
 // form, from the lower and upper block sums of plain and of
 // distance-weighted levels (sum (z_o - z_m) w_m = (z_o - z0) sum w_m -
 // sum (z_m - z0) w_m on the lower side, the mirror on the upper side).
+//
+// Layouts.  Every pass reads and writes whole contiguous lines: layout L_k
+// stores a grid with axis k fastest, then k+1, ..., d-1, 0, ..., k-1.  nu's
+// grid lives in L_0 (the caller's order), mu's in L_{d-1}.  K psi runs axes
+// 0, 1, ..., d-1 and turns its partial product from L_k into L_{k+1} between
+// passes (a transpose of an n_k x G/n_k matrix); K^T phi runs axes d-1, ...,
+// 0 and turns L_k into L_{k-1}.  The last pass of either meets the output
+// grid in its own layout, so no grid is ever read or written with a stride.
+// mu's grids change layout only at the ABI (masses and warm starts in, the
+// potentials out).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -171,12 +181,47 @@ __global__ void k_sum_parts(const double* part, int n, double* out) {
   }
 }
 
-int64_t nd_inner(const finom_plan_s* p, int k) {
-  int64_t v = 1;
-  for (int j = 0; j < k; ++j) v *= p->nd_n[j];
-  return v;
+// dst = the transpose of src: src holds an R x C matrix with its rows index
+// fastest (entry (r, c) at r + R c), dst holds it at c + C r.  32 x 32 tiles
+// staged in shared memory (coalesced on both sides), grid-stride over tiles.
+template <class T>
+__global__ void __launch_bounds__(256) k_rot(const T* __restrict__ src, int64_t R, int64_t C, T* __restrict__ dst) {
+  __shared__ T t[32][33];
+  const int64_t tr = (R + 31) / 32, tiles = tr * ((C + 31) / 32);
+  for (int64_t b = blockIdx.x; b < tiles; b += gridDim.x) {
+    const int64_t r0 = (b % tr) * 32, c0 = (b / tr) * 32;
+#pragma unroll
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const int64_t r = r0 + threadIdx.x, c = c0 + k;
+      if (r < R && c < C) t[k][threadIdx.x] = src[r + R * c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const int64_t c = c0 + threadIdx.x, r = r0 + k;
+      if (r < R && c < C) dst[c + C * r] = t[threadIdx.x][k];
+    }
+    __syncthreads();
+  }
 }
+
 int64_t nd_lines(const finom_plan_s* p, int k) { return p->nd_G / p->nd_n[k]; }
+
+// A grid from layout L_k to L_{k+1} (fwd) or L_{k-1} (!fwd), src -> dst.
+template <class T>
+void nd_rot(const finom_plan_s* p, int k, bool fwd, const T* src, T* dst, cudaStream_t s) {
+  const int d = p->dim, G = (int)p->nd_G;
+  if (d == 1) {   // one layout only
+    cudaMemcpyAsync(dst, src, sizeof(T) * G, cudaMemcpyDeviceToDevice, s);
+    return;
+  }
+  // L_k -> L_{k+1}: axis k (fastest) becomes the slowest; L_k -> L_{k-1}:
+  // the slowest axis, k-1, becomes the fastest
+  const int64_t R = fwd ? p->nd_n[k] : p->nd_G / p->nd_n[(k + d - 1) % d];
+  const int64_t C = p->nd_G / R;
+  const int64_t tiles = ((R + 31) / 32) * ((C + 31) / 32);
+  k_rot<T><<<(unsigned)std::min<int64_t>(tiles, 4096), dim3(32, 8), 0, s>>>(src, R, C, dst);
+}
 
 // largest (lines x tiles) over the axis passes
 int64_t nd_units(const finom_plan_s* p) {
@@ -245,7 +290,7 @@ finom_status nd_pass(finom_plan_s* p, int k, int o_is_x, const LvT<R>* gW, int m
   a.C = (int)ax->Ce;
   a.o_is_x = o_is_x;
   a.lines = (int)nd_lines(p, k);
-  a.inner = nd_inner(p, k);
+  a.inner = 1;   // the grid is in layout L_k: lines along axis k are contiguous
   a.nk = p->nd_n[k];
   a.gW = gW;
   a.gO = gO;
@@ -275,24 +320,29 @@ finom_status nd_pass(finom_plan_s* p, int k, int o_is_x, const LvT<R>* gW, int m
 }
 
 // One application of Algorithm 1 on the grids (o_is_x = 0: psi <- nu / K^T
-// phi with the loop-head check; 1: phi <- mu / K psi), axis 0 first.  The
-// source grid is read from src, the output grid's frames from dst_in, its
-// new log-weights go to dst_out.
+// phi with the loop-head check; 1: phi <- mu / K psi).  K psi: W = nu in L_0,
+// axes 0 .. d-1, output mu in L_{d-1}; K^T phi: W = mu in L_{d-1}, axes d-1
+// .. 0, output nu in L_0.  The source grid is read from src, the output
+// grid's frames from dst_in, its new log-weights go to dst_out.
 template <class R>
 finom_status nd_application(finom_plan_s* p, int o_is_x, const LvT<R>* src, const LvT<R>* dst_in,
                             LvT<R>* dst_out, bool check_only, cudaStream_t s) {
   SolveState& st = p->st;
   const int d = p->dim;
-  LvT<R>* Q = (LvT<R>*)st.q2;
+  LvT<R>* Qa = (LvT<R>*)st.q2;
+  LvT<R>* Qb = Qa + p->nd_G;
   const LvT<R>* lm = (const LvT<R>*)(o_is_x ? st.qom : st.qwm);
   const LvT<R>* w = src;
-  for (int k = 0; k < d; ++k) {
+  for (int j = 0; j < d; ++j) {
+    const int k = o_is_x ? j : d - 1 - j;
     finom_status rc;
-    if (k + 1 < d) {
-      LvT<R>* q = Q + (int64_t)(k & 1) * p->nd_G;
-      rc = nd_pass<R>(p, k, o_is_x, w, kLineQ, nullptr, nullptr, nullptr, q, nullptr, nullptr, (R*)st.aggs,
+    if (j + 1 < d) {
+      rc = nd_pass<R>(p, k, o_is_x, w, kLineQ, nullptr, nullptr, nullptr, Qa, nullptr, nullptr, (R*)st.aggs,
                       (R*)st.carries, st.part, s, st.tol, st.maxit);
-      w = q;
+      if (rc != FINOM_OK) return rc;
+      nd_rot(p, k, o_is_x != 0, Qa, Qb, s);
+      w = Qb;
+      continue;
     } else {
       const int mode = check_only ? kLineCheck : (o_is_x ? kLineX : kLineY);
       rc = nd_pass<R>(p, k, o_is_x, w, mode, dst_in, dst_out, lm, nullptr, nullptr, nullptr, (R*)st.aggs,
@@ -348,9 +398,12 @@ finom_status nd_begin(finom_plan_s* p, const double* u, const double* v, double 
   if (rc != FINOM_OK) return rc;
   SolveState& st = p->st;
   const int64_t G = p->nd_G;
-  rc = normalise_masses<R>(u, G, st.mu, st.mu64, st.tx, st.bad, nullptr, s);
+  // masses: nu's in L_0; mu's normalised in L_0, then turned into L_{d-1}
+  double* red = st.scal + 256;   // partial sums of the normalisation
+  rc = normalise_masses<double>(u, G, st.tx, st.tx, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
-  rc = normalise_masses<R>(v, G, st.nu, st.nu64, st.ty, st.bad, nullptr, s);
+  nd_rot(p, 0, false, (const double*)st.tx, st.mu64, s);
+  rc = normalise_masses<double>(v, G, st.nu64, st.nu64, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   const double none = (double)HT<R>::kNone;
   k_grid_lmass<<<nb(G), 256, 0, s>>>(st.mu64, G, (LvT<R>*)st.qom, none);
@@ -358,7 +411,9 @@ finom_status nd_begin(finom_plan_s* p, const double* u, const double* v, double 
   const double scale = 1.0 / (p->eps * kLn2);
   st.warm = (f0 != nullptr && g0 != nullptr);
   const double start = std::log2(1.0 / (double)G);   // Algorithm 2: Phi = Psi = 1/(NM)
-  k_grid_set<<<nb(G), 256, 0, s>>>((LvT<R>*)st.px[0], G, st.warm ? f0 : nullptr, scale, start, none);
+  LvT<R>* tmp = (LvT<R>*)st.q2;
+  k_grid_set<<<nb(G), 256, 0, s>>>(tmp, G, st.warm ? f0 : nullptr, scale, start, none);
+  nd_rot(p, 0, false, (const LvT<R>*)tmp, (LvT<R>*)st.px[0], s);
   k_grid_set<<<nb(G), 256, 0, s>>>((LvT<R>*)st.py[0], G, st.warm ? g0 : nullptr, scale, start, none);
   FINOM_CUDA(cudaGetLastError());
   FINOM_CUDA(cudaMemsetAsync(st.ctrl, 0, sizeof(int32_t) * 8, s));
@@ -409,7 +464,8 @@ finom_status nd_poll(finom_plan_s* p, cudaStream_t s, int32_t* done, int64_t* it
   return FINOM_OK;
 }
 
-// float64 check of given log-weight grids bx (mu) and by (nu), in bits:
+// float64 check of given log-weight grids bx (mu, layout L_{d-1}) and by
+// (nu, L_0), in bits, with the masses mu (L_{d-1}) and nu (L_0):
 // the marginal error sum_j |psi_j (K^T phi)_j - nu_j| of Algorithm 1's loop
 // head and W1 = <C, Gamma> = sum_k <C_k, Gamma> (C_k: the axis-k part of the
 // separable cost), from axis passes of the float64 kernel.
@@ -428,26 +484,29 @@ finom_status nd_check64(finom_plan_s* p, const double* bx, const double* by, con
          *sums = red + 256;
   const int d = p->dim;
   const int blocks = (int)std::min<int64_t>(256, (G + 255) / 256);
-  // marginal error: K^T phi on the nu grid
+  // marginal error: K^T phi on the nu grid (axes d-1 .. 0, from L_{d-1} to L_0)
   {
     const double* w = bx;
-    for (int k = 0; k < d; ++k) {
-      double* q = (k & 1) ? Qb : Qa;
-      finom_status rc = nd_pass<double>(p, k, 0, w, kLineQ, nullptr, nullptr, nullptr, q, nullptr, nullptr,
+    for (int k = d - 1; k >= 0; --k) {
+      finom_status rc = nd_pass<double>(p, k, 0, w, kLineQ, nullptr, nullptr, nullptr, Qa, nullptr, nullptr,
                                         aggs, carries, part, s, 0.0, 0);
       if (rc != FINOM_OK) return rc;
-      w = q;
+      w = Qa;
+      if (k > 0) {
+        nd_rot(p, k, false, (const double*)Qa, Qb, s);
+        w = Qb;
+      }
     }
     k_grid_sum<<<blocks, 256, 0, s>>>(by, w, nu, G, 0, red);
     k_sum_parts<<<1, 32, 0, s>>>(red, blocks, sums);
   }
-  // <C_k, Gamma> for every axis k: K psi with axis k cost-weighted, then
-  // sum_i phi_i (.)_i
+  // <C_k, Gamma> for every axis k: K psi (axes 0 .. d-1, from L_0 to
+  // L_{d-1}) with axis k cost-weighted, then sum_i phi_i (.)_i
   for (int k = 0; k < d; ++k) {
     const double* w = by;
     for (int j = 0; j < d; ++j) {
       finom_status rc;
-      double* q = (j & 1) ? Qb : Qa;
+      double* out = Qa;
       if (j == k) {
         rc = nd_pass<double>(p, j, 1, w, kLineFB, nullptr, nullptr, nullptr, nullptr, FB0, nullptr, aggs,
                              carries, part, s, 0.0, 0);
@@ -455,14 +514,19 @@ finom_status nd_check64(finom_plan_s* p, const double* bx, const double* by, con
           rc = nd_pass<double>(p, j, 1, w, kLineFBZ, nullptr, nullptr, nullptr, nullptr, FB1, p->nd_ly64[j],
                                aggs, carries, part, s, 0.0, 0);
         if (rc != FINOM_OK) return rc;
-        k_moment<<<nb(G), 256, 0, s>>>(FB0, FB1, G, p->nd_zx64[j], p->nd_z0s[j], nd_inner(p, j), p->nd_n[j], Qm);
-        w = Qm;   // (the passes after it write Qa / Qb)
-        continue;
+        // layout L_j: the node along axis j is the fastest index
+        k_moment<<<nb(G), 256, 0, s>>>(FB0, FB1, G, p->nd_zx64[j], p->nd_z0s[j], 1, p->nd_n[j], Qm);
+        out = Qm;
+      } else {
+        rc = nd_pass<double>(p, j, 1, w, kLineQ, nullptr, nullptr, nullptr, Qa, nullptr, nullptr, aggs, carries,
+                             part, s, 0.0, 0);
+        if (rc != FINOM_OK) return rc;
       }
-      rc = nd_pass<double>(p, j, 1, w, kLineQ, nullptr, nullptr, nullptr, q, nullptr, nullptr, aggs, carries,
-                           part, s, 0.0, 0);
-      if (rc != FINOM_OK) return rc;
-      w = q;
+      w = out;
+      if (j + 1 < d) {
+        nd_rot(p, j, true, (const double*)out, Qb, s);
+        w = Qb;
+      }
     }
     k_grid_sum<<<blocks, 256, 0, s>>>(bx, w, mu, G, 1, red);
     k_sum_parts<<<1, 32, 0, s>>>(red, blocks, sums + 1 + k);
@@ -498,16 +562,20 @@ finom_status nd_end(finom_plan_s* p, double* f, double* g, finom_result* res, cu
   finom_status rc = nd_check64(p, st.tx, st.ty, st.mu64, st.nu64, &err64, &w1, s);
   if (rc != FINOM_OK) return rc;
   const double eps_ln2 = p->eps * kLn2;
+  double* d2 = st.scal + 16;
   if (iters == 0 && !st.warm) {
     // the start Phi = Psi = 1/(NM) at every point (Algorithm 2)
     fill_d(f, G, p->eps * std::log(1.0 / (double)G), s);
     fill_d(g, G, p->eps * std::log(1.0 / (double)G), s);
+    dot_pos(st.mu64, f, G, d2, s);
   } else {
-    k_f_of<<<nb(G), 256, 0, s>>>(st.tx, st.mu64, G, eps_ln2, f);
+    // mu's potentials in L_{d-1}, then in the caller's order
+    double* fd = (double*)st.q2;
+    k_f_of<<<nb(G), 256, 0, s>>>(st.tx, st.mu64, G, eps_ln2, fd);
+    dot_pos(st.mu64, fd, G, d2, s);
+    nd_rot(p, p->dim - 1, true, (const double*)fd, f, s);
     k_f_of<<<nb(G), 256, 0, s>>>(st.ty, st.nu64, G, eps_ln2, g);
   }
-  double* d2 = st.scal + 16;
-  dot_pos(st.mu64, f, G, d2, s);
   dot_pos(st.nu64, g, G, d2 + 1, s);
   double hd[2];
   FINOM_CUDA(cudaMemcpyAsync(hd, d2, sizeof(hd), cudaMemcpyDeviceToHost, s));
@@ -607,14 +675,19 @@ finom_status nd_product(finom_plan_s* p, bool transpose, bool logmode, const dou
   if (logmode) k_grid_set<<<nb(G), 256, 0, s>>>(w0, G, bw, scale, 0.0, none);
   else k_grid_lin<<<nb(G), 256, 0, s>>>(w0, G, bw, none);
   const int o_is_x = transpose ? 0 : 1;
-  LvT<R>* Q = (LvT<R>*)st.q2;
+  // axes 0 .. d-1, each pass from L_k, then into L_{k+1} (L_d = L_0)
+  LvT<R>* Qa = (LvT<R>*)st.q2;
+  LvT<R>* Qb = Qa + G;
   const LvT<R>* w = w0;
   for (int k = 0; k < p->dim; ++k) {
-    LvT<R>* q = Q + (int64_t)(k & 1) * G;
-    rc = nd_pass<R>(p, k, o_is_x, w, kLineQ, nullptr, nullptr, nullptr, q, nullptr, nullptr, (R*)st.aggs,
+    rc = nd_pass<R>(p, k, o_is_x, w, kLineQ, nullptr, nullptr, nullptr, Qa, nullptr, nullptr, (R*)st.aggs,
                     (R*)st.carries, st.part, s, 0.0, 0);
     if (rc != FINOM_OK) return rc;
-    w = q;
+    w = Qa;
+    if (p->dim > 1) {
+      nd_rot(p, k, true, (const LvT<R>*)Qa, Qb, s);
+      w = Qb;
+    }
   }
   k_prod_out<<<nb(G), 256, 0, s>>>(w, G, ao, 1.0 / p->eps, logmode ? 0 : 1, none, out);
   FINOM_CUDA(cudaGetLastError());
@@ -728,12 +801,16 @@ finom_status cost_nd(finom_plan_s* p, const double* u, const double* v, const do
   if (rc != FINOM_OK) return rc;
   SolveState& st = p->st;
   const int64_t G = p->nd_G;
-  rc = normalise_masses<double>(u, G, st.mu64, st.mu64, st.tx, st.bad, nullptr, s);
+  double* red = st.scal + 256;
+  // mu's masses and log-weights into L_{d-1} (through ty), nu's in L_0
+  rc = normalise_masses<double>(u, G, st.ty, st.ty, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
-  rc = normalise_masses<double>(v, G, st.nu64, st.nu64, st.ty, st.bad, nullptr, s);
+  nd_rot(p, 0, false, (const double*)st.ty, st.mu64, s);
+  rc = normalise_masses<double>(v, G, st.nu64, st.nu64, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   const double scale = 1.0 / (p->eps * kLn2);
-  k_grid_set<<<nb(G), 256, 0, s>>>(st.tx, G, f, scale, 0.0, -INFINITY);
+  k_grid_set<<<nb(G), 256, 0, s>>>(st.ty, G, f, scale, 0.0, -INFINITY);
+  nd_rot(p, 0, false, (const double*)st.ty, st.tx, s);
   k_grid_set<<<nb(G), 256, 0, s>>>(st.ty, G, g, scale, 0.0, -INFINITY);
   st.active = false;
   return nd_check64(p, st.tx, st.ty, st.mu64, st.nu64, err, w1, s);

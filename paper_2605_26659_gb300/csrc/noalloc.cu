@@ -99,7 +99,7 @@ finom_status noalloc_dispatch(finom_plan_t p, bool transpose, const double* a, c
     set_error("finom_kv_log_noalloc: null argument");
     return FINOM_EINVAL;
   }
-  if (p->dim != 1 || p->B > 0) {
+  if (p->dim != 1 || p->nd || p->B > 0) {
     set_error("finom_kv_log_noalloc: single 1D plans only");
     return FINOM_ENOTSUP;
   }

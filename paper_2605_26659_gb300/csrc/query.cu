@@ -46,7 +46,7 @@ bool plain_1d(finom_plan_t p, const char* what) {
     set_error(std::string(what) + ": null plan");
     return false;
   }
-  if (p->dim != 1 || p->B > 0) {
+  if (p->dim != 1 || p->nd || p->B > 0) {
     set_error(std::string(what) + ": 1D single-problem plans only");
     return false;
   }

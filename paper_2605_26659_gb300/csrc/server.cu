@@ -20,7 +20,6 @@
 #include <chrono>
 #include <cmath>
 #include <deque>
-#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -61,9 +60,14 @@ struct finom_server_s {
   finom_precision prec = FINOM_F32_LOG;
   int device = 0;
   int64_t next_id = 1;
+  // Containers only grow where capacity was reserved beforehand (submit
+  // reserves room in finished for every request in flight, step reserves
+  // active, its successor list and the graveyard before it changes any
+  // state), so that a host allocation failure surfaces as FINOM_ENOMEM
+  // before any request changes hands.
   std::deque<Req*> pending;
   std::vector<Req*> active;
-  std::map<int64_t, Req*> finished;
+  std::vector<Req*> finished;
   std::vector<cudaStream_t> streams;
   std::vector<int> free_slots;
   // plans of retired requests, destroyed together: freeing device memory
@@ -122,7 +126,11 @@ void fail(finom_server_s* s, Req* r, finom_status rc) {
   r->res.status = rc;
   r->t_done = now_s();
   release(s, r);
-  s->finished[r->id] = r;
+  s->finished.push_back(r);   // (capacity reserved by submit)
+}
+
+std::vector<Req*>::iterator find_finished(finom_server_s* s, int64_t id) {
+  return std::find_if(s->finished.begin(), s->finished.end(), [id](const Req* r) { return r->id == id; });
 }
 
 // a plan of the request's meshes (device copies in r->dev) at eps e
@@ -234,10 +242,18 @@ finom_status finish(finom_server_s* s, Req* r, bool* more) {
 }
 
 finom_status submit(finom_server_s* s, Req* r, int64_t* id) {
+  try {
+    // room for every request in flight to finish without a reallocation
+    s->finished.reserve(s->finished.size() + s->pending.size() + s->active.size() + 1);
+    s->pending.push_back(r);
+  } catch (const std::bad_alloc&) {
+    delete r;
+    finom::set_error("finom_server_submit: out of host memory");
+    return FINOM_ENOMEM;
+  }
   r->id = s->next_id++;
   r->footprint = footprint(r->kind, r->N, r->M);
   r->t_submit = now_s();
-  s->pending.push_back(r);
   if (id) *id = r->id;
   return FINOM_OK;
 }
@@ -259,7 +275,14 @@ finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, f
   s->max_active = max_active;
   s->prec = prec;
   cudaGetDevice(&s->device);
-  s->streams.resize(max_active);
+  try {
+    s->streams.resize(max_active);
+    s->free_slots.reserve(max_active);
+  } catch (const std::bad_alloc&) {
+    delete s;
+    finom::set_error("finom_server_create: out of host memory");
+    return FINOM_ENOMEM;
+  }
   for (int k = 0; k < max_active; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -358,6 +381,19 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
     finom::set_error("finom_server_step: null server");
     return FINOM_EINVAL;
   }
+  // the only host allocations of a round, before any state changes: every
+  // request can move to the active list or its successor, and release up to
+  // three plans (two of a request, one of an eps-scaling stage)
+  std::vector<Req*> still;
+  try {
+    const size_t n = s->active.size() + s->free_slots.size();
+    s->active.reserve(n);
+    still.reserve(n);
+    s->graveyard.reserve(s->graveyard.size() + 3 * n);
+  } catch (const std::bad_alloc&) {
+    finom::set_error("finom_server_step: out of host memory");
+    return FINOM_ENOMEM;
+  }
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != s->device) cudaSetDevice(s->device);
@@ -377,7 +413,6 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
     else s->active.push_back(r);
   }
   // progress of the active solves whose launches have completed
-  std::vector<Req*> still;
   for (Req* r : s->active) {
     if (cudaEventQuery(r->ev) == cudaErrorNotReady) {
       still.push_back(r);
@@ -406,7 +441,7 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
       still.push_back(r);
       continue;
     }
-    s->finished[r->id] = r;
+    s->finished.push_back(r);
   }
   s->active.swap(still);
   if (s->graveyard.size() >= kGraveyard || (s->active.empty() && !s->graveyard.empty())) flush_graveyard(s);
@@ -422,12 +457,12 @@ finom_status finom_server_result(finom_server_t s, int64_t id, finom_server_done
     finom::set_error("finom_server_result: null argument");
     return FINOM_EINVAL;
   }
-  auto it = s->finished.find(id);
+  auto it = find_finished(s, id);
   if (it == s->finished.end()) {
     finom::set_error("finom_server_result: request not finished (or unknown)");
     return FINOM_EPENDING;
   }
-  Req* r = it->second;
+  Req* r = *it;
   out->id = r->id;
   out->kind = r->kind;
   out->status = r->status;
@@ -436,7 +471,8 @@ finom_status finom_server_result(finom_server_t s, int64_t id, finom_server_done
   out->queue_s = r->t_admit > 0.0 ? r->t_admit - r->t_submit : out->latency_s;
   if (f && !r->f.empty()) std::copy(r->f.begin(), r->f.end(), f);
   if (g && !r->g.empty()) std::copy(r->g.begin(), r->g.end(), g);
-  s->finished.erase(it);
+  *it = s->finished.back();
+  s->finished.pop_back();
   delete r;
   return FINOM_OK;
 }
@@ -446,14 +482,20 @@ finom_status finom_server_cancel(finom_server_t s, int64_t id) {
     finom::set_error("finom_server_cancel: null server");
     return FINOM_EINVAL;
   }
-  if (s->finished.count(id)) return FINOM_OK;
+  if (find_finished(s, id) != s->finished.end()) return FINOM_OK;
+  try {
+    s->graveyard.reserve(s->graveyard.size() + 2);
+  } catch (const std::bad_alloc&) {
+    finom::set_error("finom_server_cancel: out of host memory");
+    return FINOM_ENOMEM;
+  }
   for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
     if ((*it)->id != id) continue;
     Req* r = *it;
     s->pending.erase(it);
     r->status = r->res.status = FINOM_ECANCELED;
     r->t_done = now_s();
-    s->finished[id] = r;
+    s->finished.push_back(r);
     return FINOM_OK;
   }
   for (auto it = s->active.begin(); it != s->active.end(); ++it) {
@@ -480,7 +522,7 @@ finom_status finom_server_destroy(finom_server_t s) {
     delete r;
   }
   for (Req* r : s->pending) delete r;
-  for (auto& kv : s->finished) delete kv.second;
+  for (Req* r : s->finished) delete r;
   flush_graveyard(s);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   delete s;

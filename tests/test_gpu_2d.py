@@ -5,9 +5,12 @@ arrays cross the C ABI flat and column-major (point (k, i) at k + N i).  The
 oracle is the plain-C line-by-line evaluation of the same products
 (oracle/finom_serial.c, pinned against the dense 2D definition), and the dense
 2D definition itself at small sizes.
-"""
-import math
 
+Acceptance: products 1e-5 (float32 log-domain) and 1e-12 (float64) on every
+mesh, including axes whose merged gaps are tens of bits (coarse and disjoint
+supports); W1 1e-4 / 1e-9; the float64 marginal error recomputed by the
+oracle within tol.
+"""
 import numpy as np
 import pytest
 
@@ -17,6 +20,10 @@ from tests.gpu_util import H, T, relerr
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32_log": 1e-5}
+# float32 loop against the oracle at the same iterations: the float64
+# marginal error of the float32 potentials (their rounding, ~1e-6 eps per
+# point and iteration, moves it by a relative few 1e-5 at most)
+F32_ERR_REL, F32_ERR_ABS = 2e-4, 2e-7
 LOCK_TOL = {"f64": 1e-10, "f32_log": 3e-5}   # |f_gpu - f_oracle| / eps on points with mass
 # FP32: every half step rounds each weight level (~log2 of the grid size, 14
 # bits here) to float32 in both passes of an application, ~1e-6 eps per
@@ -40,6 +47,12 @@ def _axes(seed, N, M, kind="random"):
     if kind == "ties":
         r = lambda n: np.sort(np.round(g.uniform(0, 1, n) * 41) / 41)
         return r(N), r(M), r(N), r(M)
+    if kind == "disjoint":   # mu's axes left of nu's: merged gaps of tens of bits
+        return (np.sort(g.uniform(0, 0.4, N)), np.sort(g.uniform(0, 0.3, M)),
+                np.sort(g.uniform(0.6, 1, N)), np.sort(g.uniform(0.7, 1, M)))
+    if kind == "coarse":     # few nodes far apart
+        return (np.sort(g.choice(np.linspace(0, 1, 9), N)), np.sort(g.choice(np.linspace(0, 1, 7), M)),
+                np.sort(g.choice(np.linspace(0.05, 0.95, 9), N)), np.sort(g.choice(np.linspace(0.02, 0.98, 7), M)))
     raise ValueError(kind)
 
 
@@ -68,20 +81,8 @@ def _assert_lockstep(f, g, fo, go, u, v, eps, prec, iters):
     assert abs(c) / eps <= 20 * tol
 
 
-def f32_bound(axes, eps):
-    """The 1D float32 bound (4 ulp of the largest gap in bits) on each axis,
-    for the two passes of a 2D product."""
-    x1, y1, x2, y2 = axes
-    gm = 0.0
-    for a, b in ((x1, x2), (y1, y2)):
-        z = np.sort(np.concatenate([a, b]))
-        if len(z) > 1:
-            gm = max(gm, float(np.max(np.diff(z))) / (eps * math.log(2.0)))
-    return max(TOL["f32_log"], 2 * 2.4e-7 * gm)
-
-
-def _tol(prec, axes, eps):
-    return TOL["f64"] if prec == "f64" else f32_bound(axes, eps)
+def _tol(prec):
+    return TOL[prec]
 
 
 SHAPES_2D = [(1, 1), (1, 7), (6, 1), (9, 7), (130, 70), (1024, 3), (1500, 40), (40, 2500)]
@@ -103,23 +104,23 @@ def test_2d_log_products_match_oracle(lib, prec, N, M):
     assert lib.finom_plan_shape(p) == (2, N, M)
     got = H(lib.finom_kv_log(p, T(_flat(A)), T(_flat(B))))
     want = _flat(A) / eps + _flat(serial_c.log_apply2d(x1, y1, x2, y2, eps, B))
-    tol = _tol(prec, axes, eps)
+    tol = _tol(prec)
     fin = np.isfinite(want)
     assert np.array_equal(np.isfinite(got), fin)
     if fin.any():
-        assert np.max(np.abs(got[fin] - want[fin])) <= tol * 1.5
+        assert np.max(np.abs(got[fin] - want[fin])) <= tol
     got_t = H(lib.finom_ktu_log(p, T(_flat(A)), T(_flat(B))))
     want_t = _flat(B) / eps + _flat(serial_c.log_apply2d(x2, y2, x1, y1, eps, A))
     fin = np.isfinite(want_t)
     assert np.array_equal(np.isfinite(got_t), fin)
     if fin.any():
-        assert np.max(np.abs(got_t[fin] - want_t[fin])) <= tol * 1.5
+        assert np.max(np.abs(got_t[fin] - want_t[fin])) <= tol
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
-@pytest.mark.parametrize("kind", ["random", "ties"])
-def test_2d_linear_products_match_dense(lib, prec, kind):
-    N, M, eps = 23, 17, 0.05
+@pytest.mark.parametrize("kind,eps", [("random", 0.05), ("ties", 0.05), ("disjoint", 0.004), ("coarse", 0.004)])
+def test_2d_linear_products_match_dense(lib, prec, kind, eps):
+    N, M = 23, 17
     axes = _axes(5, N, M, kind)
     x1, y1, x2, y2 = axes
     K = dense.kernel(dense.cost_2d(x1, y1, x2, y2), eps)
@@ -127,8 +128,27 @@ def test_2d_linear_products_match_dense(lib, prec, kind):
     v = g.uniform(0, 1, N * M)
     v[g.random(N * M) < 0.1] = 0.0
     p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
-    assert relerr(H(lib.finom_kv(p, T(v))), K @ v) <= _tol(prec, axes, eps) * 1.5
-    assert relerr(H(lib.finom_ktu(p, T(v))), K.T @ v) <= _tol(prec, axes, eps) * 1.5
+    assert relerr(H(lib.finom_kv(p, T(v))), K @ v) <= _tol(prec)
+    assert relerr(H(lib.finom_ktu(p, T(v))), K.T @ v) <= _tol(prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("kind", ["disjoint", "coarse"])
+def test_2d_log_products_large_gaps(lib, prec, kind):
+    """Stabilised products on axes with merged gaps of up to ~100 bits
+    (eps = 0.004) against the line-by-line oracle, with rough absorptions."""
+    N, M, eps = 300, 200, 0.004
+    x1, y1, x2, y2 = _axes(41, N, M, kind)
+    g = np.random.default_rng(42)
+    A = eps * g.normal(0, 3, (N, M))
+    B = eps * g.normal(0, 3, (N, M))
+    B[g.random((N, M)) < 0.05] = -np.inf
+    p = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
+    got = H(lib.finom_kv_log(p, T(_flat(A)), T(_flat(B))))
+    want = _flat(A) / eps + _flat(serial_c.log_apply2d(x1, y1, x2, y2, eps, B))
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isfinite(got), fin)
+    assert np.max(np.abs(got[fin] - want[fin])) <= _tol(prec)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
@@ -147,8 +167,10 @@ def test_2d_lockstep_with_oracle(lib, prec, maxit, N, M, eps):
     if maxit > 0:
         _assert_lockstep(fa, ga, _flat(Ao), _flat(Bo), u, v, eps, prec, maxit)
         assert np.all(np.isneginf(fa[u == 0])) and np.all(np.isneginf(ga[v == 0]))
-        assert res["marginal_err"] == pytest.approx(err, rel=1e-6 if prec == "f64" else 1e-3,
-                                                    abs=1e-9 if prec == "f64" else 3e-6)
+        if prec == "f64":
+            assert res["marginal_err"] == pytest.approx(err, rel=1e-6, abs=1e-9)
+        else:
+            assert abs(res["marginal_err"] - err) <= F32_ERR_REL * err + F32_ERR_ABS
     else:
         assert np.allclose(fa, _flat(Ao), rtol=1e-14) and np.allclose(ga, _flat(Bo), rtol=1e-14)
         assert res["marginal_err_loop"] == pytest.approx(err, rel=1e-5)
@@ -176,7 +198,7 @@ def test_2d_converged_matches_oracle(lib, prec, tol):
         assert res["w1"] == pytest.approx(w1o, rel=1e-4)
     A, B = _grid(H(f), 96, 80), _grid(H(g), 96, 80)
     e_or = serial_c.marginal_error2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, A, B, pr.V)
-    assert e_or <= (tol if prec == "f64" else 3 * tol)
+    assert e_or <= tol
     assert res["marginal_err"] == pytest.approx(e_or, rel=1e-6, abs=1e-13)
     assert res["w1"] == pytest.approx(serial_c.cost2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, A, B), rel=1e-10)
 
@@ -188,30 +210,29 @@ def test_2d_full_size_application_and_iterations(lib):
     from paper_2605_26659_gb300 import inputs
     pr = inputs.config3()
     N = M = 1024
-    axes = (pr.x1, pr.y1, pr.x2, pr.y2)
     p = lib.finom_plan_2d(T(pr.x1), T(pr.x2), T(pr.y1), T(pr.y2), pr.eps, "f32_log")
     g = np.random.default_rng(0)
     A = g.normal(0, 0.002, (N, M))
     B = np.where(pr.V > 0, pr.eps * np.log(np.maximum(pr.V, 1e-300)), -np.inf)
     got = H(lib.finom_kv_log(p, T(_flat(A)), T(_flat(B))))
     want = _flat(A) / pr.eps + _flat(serial_c.log_apply2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.eps, B))
-    assert np.max(np.abs(got - want)) <= f32_bound(axes, pr.eps) * 1.5
+    assert np.max(np.abs(got - want)) <= TOL["f32_log"]
     f, gg, res = lib.finom_solve(p, T(_flat(pr.U)), T(_flat(pr.V)), 0.0, 3)
     Ao, Bo, it, err = serial_c.sinkhorn2d(pr.x1, pr.y1, pr.x2, pr.y2, pr.U, pr.V, pr.eps, 0.0, 3)
     u, v = _flat(pr.U), _flat(pr.V)
     assert res["iters"] == 3
     _assert_lockstep(H(f), H(gg), _flat(Ao), _flat(Bo), u, v, pr.eps, "f32_log", 3)
-    assert res["marginal_err"] == pytest.approx(err, rel=1e-3)
+    assert abs(res["marginal_err"] - err) <= F32_ERR_REL * err + F32_ERR_ABS
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
-def test_2d_single_row_grid_is_the_1d_solve(lib, prec):
-    """M = 1: the 2D problem is the 1D one with a constant cost offset |y1 - y2|.
-    The offset is kept at a fraction of a bit (|y1 - y2| / (eps ln 2) < 1): a
-    single axis gap of G bits costs float32 plans ~2.4e-7 G relative precision."""
+@pytest.mark.parametrize("offset", [0.004, 0.3])
+def test_2d_single_row_grid_is_the_1d_solve(lib, prec, offset):
+    """M = 1: the 2D problem is the 1D one with a constant cost offset
+    |y1 - y2| (0.3 is a gap of 43 bits at eps = 0.01)."""
     N, eps = 700, 0.01
     x1, y1, x2, y2 = _axes(3, N, 1)
-    y2 = y1 + 0.004
+    y2 = y1 + offset
     U, V = _grid_masses(N, 1, 4)
     p2 = lib.finom_plan_2d(T(x1), T(x2), T(y1), T(y2), eps, prec)
     p1 = lib.finom_plan(T(x1), T(x2), eps, prec)
