@@ -22,8 +22,8 @@ of requests one at a time in FP64).
 
 `--workload 2d` times the 2D path instead (Algorithm 2 with the Appendix A
 stabilisation): 1024 x 1024 grids, tanh-clustered axes, four anisotropic
-Gaussians, eps = 2e-3; one step = one iteration = four line-batch launches,
-2 * 1024^2 point-iterations.
+Gaussians, eps = 2e-3; one step = one iteration = four axis passes of the
+half-step kernel and two tiled transposes, 2 * 1024^2 point-iterations.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
 (serial float64 FINOM recurrences in plain C) on the same workload instead.
@@ -385,10 +385,11 @@ def run_finom_2d(args, ws, rank, local):
     step_s = total_ms / 1e3 / args.steps
     pts = 2 * NM
     value = ws * pts * args.steps / (total_ms / 1e3)
-    # per application: first pass reads W potentials + masses (12 B) and writes
-    # log2 Q (8 B); second pass reads O potentials + masses (12 B) and Q (8 B)
-    # and writes O potentials (8 B): 48 B per grid point, two applications
-    bytes_per_step = 2 * 48.0 * NM
+    # algorithmic bytes per application: 36 B per grid point (potentials in,
+    # reference and out 8 + 8 + 8, mass 4, a 4-byte intermediate written and
+    # read 8); two applications per step.  The path itself moves more: level
+    # pairs of 8 B, 16 B + 16 B of transpose and 32 B of division pass.
+    bytes_per_step = 2 * 36.0 * NM
     peak, peak_kind = peaks()
     achieved = bytes_per_step / step_s / 1e9
 
@@ -426,10 +427,10 @@ def run_finom_2d(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_2d(N, M, pr.eps, ws),
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 6 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "finom::k_apply line batches (2D passes, 4 launches per step)",
+                         "kernel": "the whole 2D step: finom::k_half axis passes (4) + k_rot transposes (2)",
                          "algorithmic_bytes_per_step": bytes_per_step},
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
@@ -549,7 +550,7 @@ def run_finom_batch(args, ws, rank, local, emit=True):
             "gpu_launches": 6 * args.steps,   # per iteration: 2 half steps, 2 instance ends, 2 compactions
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "finom::k_apply<float, BHalfY|BHalfX> + k_batch_end",
+                         "kernel": "finom::k_half<float, kBatchY|kBatchX> + k_batch_end + k_batch_compact",
                          "algorithmic_bytes_per_step": bytes_per_step},
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
@@ -708,7 +709,7 @@ def run_finom_serve(args, ws, rank, local, emit=True):
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "every k_apply launch of the served solves, over the wall time",
+                         "kernel": "every k_half launch of the served solves, over the wall time",
                          "algorithmic_bytes": alg},
             "clocks": clocks,
             "e2e": {"value": solves_per_s, "unit": "solves/s", "h2d_bytes_per_step": h2d / len(probs),

@@ -8,7 +8,6 @@
 #include <new>
 #include <string>
 
-#include "apply.cuh"
 #include "finom_internal.h"
 #include "half.cuh"
 
@@ -24,30 +23,6 @@ finom_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 template <class R>
-finom_status launch_apply(const ApplyArgs<R>& a, bool agg_only, cudaStream_t s);
-template <class R>
-void conv_weights_log(const double*, int64_t, double, void*, void*, cudaStream_t);
-template <class R>
-void conv_weights_lin(const double*, int64_t, void*, void*, cudaStream_t);
-template <class R>
-void conv_pot_scale(const double*, int64_t, double, void*, cudaStream_t);
-template <class R>
-void fill_pot(void*, int64_t, double, cudaStream_t);
-template <class R>
-void fill_mass(void*, int64_t, double, cudaStream_t);
-template <class R>
-void conv_pot_from_f(const double*, const double*, int64_t, double, void*, cudaStream_t);
-template <class R>
-void conv_f_from_pot(const void*, const double*, int64_t, double, double*, double*, cudaStream_t);
-template <class R>
-finom_status normalise_masses(const double*, int64_t, void*, double*, double*, int*, double*,
-                              cudaStream_t);
-void fill_d(double*, int64_t, double, cudaStream_t);
-template <class R>
-void frame_from_log(const double*, int64_t, void*, cudaStream_t);
-void combine_passes(const double*, const double*, double, int64_t, int, double*, cudaStream_t);
-void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
-template <class R>
 finom_status half_launch(const HalfArgs<R>&, int, int, cudaStream_t);
 template <class R>
 void beta_set(void*, const double*, int64_t, double, const double*, double, double, cudaStream_t);
@@ -57,7 +32,6 @@ template <class R>
 void log_mass(const double*, int64_t, void*, cudaStream_t);
 template <class R>
 void f_from_beta(const void*, const double*, int64_t, double, double*, double*, cudaStream_t);
-void add_scaled(double*, const double*, double, int64_t, cudaStream_t);
 
 namespace {
 
@@ -79,8 +53,6 @@ template <class R>
 constexpr size_t beta_size() { return sizeof(typename HT<R>::Beta); }
 template <class R>
 constexpr size_t level_size() { return sizeof(typename HT<R>::Lv); }
-template <class R>
-constexpr size_t mass_size() { return sizeof(typename Tr<R>::Mass); }
 
 // Device state of the loop of a 1D plan: per point its two levels
 // (beta+, beta-) of the half-step kernel (half.cuh), ping-pong; log2 masses;
@@ -95,8 +67,6 @@ finom_status ensure_state(finom_plan_s* p) {
     FINOM_CUDA(cudaMalloc(&st.px[q], beta_size<R>() * N));
     FINOM_CUDA(cudaMalloc(&st.py[q], beta_size<R>() * M));
   }
-  FINOM_CUDA(cudaMalloc(&st.mu, mass_size<R>() * N));
-  FINOM_CUDA(cudaMalloc(&st.nu, mass_size<R>() * M));
   FINOM_CUDA(cudaMalloc(&st.qom, level_size<R>() * N));   // log2 masses of x
   FINOM_CUDA(cudaMalloc(&st.qwm, level_size<R>() * M));   // log2 masses of y
   FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * N));
@@ -128,9 +98,8 @@ void free_state(finom_plan_s* p) {
     cudaFree(st.px[q]);
     cudaFree(st.py[q]);
   }
-  void* bufs[] = {st.mu, st.nu, st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part,
-                  st.scal, st.ctrl, st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.t2, st.z,
-                  st.ictl, st.ierr, st.itol, st.iuni, st.alist};
+  void* bufs[] = {st.mu64, st.nu64, st.tx, st.ty, st.aggs, st.carries, st.part, st.scal, st.ctrl,
+                  st.bad, st.qo, st.qom, st.qw, st.qwm, st.q2, st.ictl, st.ierr, st.itol, st.alist};
   for (void* b : bufs) cudaFree(b);
   if (st.stream) cudaStreamDestroy(st.stream);
   st = SolveState();
@@ -242,9 +211,9 @@ finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, doub
   if (rc != FINOM_OK) return rc;
   SolveState& st = p->st;
   const int64_t N = p->N, M = p->M;
-  rc = normalise_masses<R>(u, N, st.mu, st.mu64, st.tx, st.bad, nullptr, s);
+  rc = normalise_masses(u, N, st.mu64, st.tx, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
-  rc = normalise_masses<R>(v, M, st.nu, st.nu64, st.ty, st.bad, nullptr, s);
+  rc = normalise_masses(v, M, st.nu64, st.ty, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   log_mass<R>(st.mu64, N, st.qom, s);
   log_mass<R>(st.nu64, M, st.qwm, s);
@@ -505,7 +474,6 @@ finom_status kv_dispatch(finom_plan_t p, bool transpose, bool logmode, const dou
   DeviceGuard dg(p->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (p->nd) return kv_nd(p, transpose, logmode, a, b, out, s);
-  if (p->dim == 2) return kv2d(p, transpose, logmode, a, b, out, s);
   return p->prec == FINOM_F32_LOG ? kv_impl<float>(p, transpose, logmode, a, b, out, s)
                                   : kv_impl<double>(p, transpose, logmode, a, b, out, s);
 }
@@ -634,7 +602,6 @@ finom_status finom_plan_destroy(finom_plan_t plan) {
   cudaDeviceSynchronize();
   free_state(plan);
   free_plan(plan);
-  plan2d_free(plan);
   plan_nd_free(plan);
   plan_batch_free(plan);
   delete plan;
@@ -784,8 +751,8 @@ finom_status finom_plan_shape(finom_plan_t plan, int32_t* dim, int64_t* N, int64
     if (M) *M = plan->nd_G / plan->nd_n[0];
     return FINOM_OK;
   }
-  if (N) *N = plan->dim == 2 ? plan->ax->N : plan->N;
-  if (M) *M = plan->dim == 2 ? plan->ay->N : plan->M;
+  if (N) *N = plan->N;
+  if (M) *M = plan->M;
   return FINOM_OK;
 }
 
@@ -844,11 +811,6 @@ finom_status finom_solve(finom_plan_t plan, const double* u, const double* v, do
   DeviceGuard dg(plan->device);
   if (plan->nd) {
     finom_status rc = solve_nd(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
-    if (res && rc != FINOM_OK) res->status = rc;
-    return rc;
-  }
-  if (plan->dim == 2) {
-    finom_status rc = solve2d(plan, u, v, tol, maxit, f, g, warm, res, (cudaStream_t)stream);
     if (res && rc != FINOM_OK) res->status = rc;
     return rc;
   }
@@ -939,9 +901,7 @@ finom_status finom_solve_eps_scaling(finom_plan_t plan, const double* u, const d
       }
       rc = finom_plan_nd(plan->dim, plan->nd_n, xs, ys, e, plan->prec, stream, &q);
     } else {
-      rc = plan->dim == 2 ? finom_plan_2d(plan->ax->x, plan->ax->y, plan->ax->N, plan->ay->x, plan->ay->y,
-                                          plan->ay->N, e, plan->prec, stream, &q)
-                          : finom_plan(plan->x, plan->N, plan->y, plan->M, e, plan->prec, stream, &q);
+      rc = finom_plan(plan->x, plan->N, plan->y, plan->M, e, plan->prec, stream, &q);
     }
     finom_result r{};
     if (rc == FINOM_OK) rc = finom_solve(q, u, v, tol_stage, maxit - done, f, g, warm, &r, stream);
@@ -969,7 +929,6 @@ finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double*
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->nd) return solve_nd_begin(plan, u, v, tol, maxit, f0, g0, s);
-  if (plan->dim == 2) return solve2d_begin(plan, u, v, tol, maxit, f0, g0, s);
   return plan->prec == FINOM_F32_LOG ? solve_begin<float>(plan, u, v, tol, maxit, f0, g0, s)
                                      : solve_begin<double>(plan, u, v, tol, maxit, f0, g0, s);
 }
@@ -984,7 +943,6 @@ finom_status finom_solve_step(finom_plan_t plan, int64_t iterations, void* strea
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->nd) return solve_nd_step(plan, iterations, s);
-  if (plan->dim == 2) return solve2d_step(plan, iterations, s);
   return plan->prec == FINOM_F32_LOG ? solve_step<float>(plan, iterations, s)
                                      : solve_step<double>(plan, iterations, s);
 }
@@ -1023,7 +981,6 @@ finom_status finom_solve_end(finom_plan_t plan, double* f, double* g, finom_resu
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->nd) return solve_nd_end(plan, f, g, res, s);
-  if (plan->dim == 2) return solve2d_end(plan, f, g, res, s);
   return plan->prec == FINOM_F32_LOG ? solve_end<float>(plan, f, g, res, s)
                                      : solve_end<double>(plan, f, g, res, s);
 }
@@ -1039,7 +996,6 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
   DeviceGuard dg(plan->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->nd) return cost_nd(plan, u, v, f, g, w1, err, s);
-  if (plan->dim == 2) return cost2d(plan, u, v, f, g, w1, err, s);
   finom_status rc = plan->prec == FINOM_F32_LOG ? ensure_state<float>(plan) : ensure_state<double>(plan);
   if (rc != FINOM_OK) return rc;
   SolveState& st = plan->st;
@@ -1047,8 +1003,8 @@ finom_status finom_cost(finom_plan_t plan, const double* u, const double* v, con
   // masses as given (not renormalised) and smooth potentials P = f/(eps ln2) - log2 u
   FINOM_CUDA(cudaMemcpyAsync(st.mu64, u, sizeof(double) * plan->N, cudaMemcpyDeviceToDevice, s));
   FINOM_CUDA(cudaMemcpyAsync(st.nu64, v, sizeof(double) * plan->M, cudaMemcpyDeviceToDevice, s));
-  conv_pot_from_f<double>(f, st.mu64, plan->N, scale, st.tx, s);
-  conv_pot_from_f<double>(g, st.nu64, plan->M, scale, st.ty, s);
+  pot_from_f(f, st.mu64, plan->N, scale, st.tx, s);
+  pot_from_f(g, st.nu64, plan->M, scale, st.ty, s);
   st.active = false;
   return cost64(plan, st.tx, st.ty, st.mu64, st.nu64, err, w1, s);
 }

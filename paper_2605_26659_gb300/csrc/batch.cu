@@ -27,7 +27,6 @@ template <class R>
 finom_status half_launch(const HalfArgs<R>&, int, int, cudaStream_t);
 template <class R>
 void log_mass(const double*, int64_t, void*, cudaStream_t);
-void fill_d(double*, int64_t, double, cudaStream_t);
 
 namespace {
 
@@ -805,7 +804,6 @@ finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* o
   FINOM_CUDA(cudaMemsetAsync(p->tbits, 0, sizeof(uint32_t) * (alloc / 32), s));
   FINOM_CUDA(cudaMalloc(&p->gap64, sizeof(double) * alloc));
   FINOM_CUDA(cudaMemsetAsync(p->gap64, 0, sizeof(double) * alloc, s));
-  p->gap = p->gap64;
   FINOM_CUDA(cudaMalloc(&p->tile_x0, sizeof(int32_t) * (T + B)));
   FINOM_CUDA(cudaMalloc(&p->tile_x0c, sizeof(int32_t) * (Tc + B)));
   int32_t* itilec = nullptr;

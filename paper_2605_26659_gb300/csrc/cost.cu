@@ -13,7 +13,8 @@
 
 #include <algorithm>
 
-#include "apply.cuh"
+#include "dev_common.cuh"
+#include "finom_internal.h"
 
 namespace finom {
 
@@ -41,6 +42,27 @@ __device__ __forceinline__ LSM lsm_add(double ma, double sa, double ta, double m
     r.m += 1.0;
   }
   return r;
+}
+
+// w = mant 2^e with mant in [1, 2) (w = 0: mant = 0, e a very negative level)
+__device__ __forceinline__ void split_mass(double w, double& e, double& mant) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  const int ex = (int)((b >> 52) & 0x7ffull);
+  const bool z = ex == 0;
+  e = z ? -1.0e300 : (double)(ex - 1023);
+  mant = z ? 0.0 : __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+}
+
+// the kElems gaps of a thread's merged points (16-byte loads; the gap array
+// is padded to whole tiles)
+__device__ __forceinline__ void load_gaps(const double* gap, int64_t seg, double (&g)[kElems]) {
+  const double2* p = reinterpret_cast<const double2*>(gap + seg);
+#pragma unroll
+  for (int q = 0; q < kElems / 2; ++q) {
+    const double2 v = __ldg(p + q);
+    g[2 * q] = v.x;
+    g[2 * q + 1] = v.y;
+  }
 }
 
 __device__ __forceinline__ AggM aggm_identity() { return {0.0, 0.0, -1.0e300, 0.0, 0.0}; }
@@ -99,29 +121,16 @@ __device__ AggM scan_m(AggM x, AggM* sh, AggM& total) {
   return aggm_then(wp, exc);
 }
 
-// How the weights and frames of a cost pass are given.
-enum : int {
-  C_ZERO_FRAME = 1,  // O side has no potentials: frame 0 (the first 2D pass)
-  C_LEVELS = 2,      // W side gives (log2 level, moment ratio) instead of (potential, mass)
-  C_INTER = 4,       // write log2 S and T/S per O point instead of reducing (err, sum v T)
-};
-
 struct CostArgs {
   const uint32_t* tbits;
   const double* gap;
   const int32_t* tile_x0;
   int64_t L;
-  int C;              // tiles per line
-  int lines;
-  int64_t o_ls, o_es; // O-side arrays: offset between lines, stride between points
-  int64_t w_ls, w_es; // W-side arrays
-  const double* px;   // W side: smooth potentials (log2 units) or log2 levels (C_LEVELS)
-  const double* py;   // O side: smooth potentials (frames)
-  const double* u;    // W side: masses, or moment ratios T/S (C_LEVELS)
+  int C;              // tiles
+  const double* px;   // W side (x): smooth potentials (log2 units)
+  const double* py;   // O side (y): smooth potentials (frames)
+  const double* u;    // W side: masses
   const double* v;    // O side: masses
-  double* z1;         // C_INTER outputs: log2 S, T/S
-  double* z2;
-  int64_t z_ls, z_es;
   double* agg;        // 10 per tile
   double* carry;      // 6 per tile
   double* part;       // 2 per tile
@@ -138,20 +147,20 @@ struct CostSmem {
   int last;
 };
 
-// Points: O = y (outputs), W = x (weights).  Exponents as in point_terms;
-// Bt is the moment a weight brings with it (C_LEVELS).
-template <int kMode>
+// Points: O = y (outputs), W = x (weights).  Per merged point e: Af / Ab
+// the exponent a forward / backward state moves by (frame change minus the
+// gap), and for a W point its log2 level Bl, mantissa Bs and moment Bt (0).
 __device__ __forceinline__ void cost_terms(uint32_t omask, uint32_t wmask, const double (&g)[kElems],
                                            const double* po, int o0, const double* pw,
                                            const double* mw, int w0, double (&Af)[kElems],
                                            double (&Ab)[kElems], double (&Bl)[kElems],
                                            double (&Bs)[kElems], double (&Bt)[kElems]) {
-  double cprev = (kMode & C_ZERO_FRAME) ? 0.0 : po[o0];
+  double cprev = po[o0];
   int oi = o0 + 1, wi = w0;
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
     double dc = 0.0;
-    if (!(kMode & C_ZERO_FRAME) && ((omask >> e) & 1u)) {
+    if ((omask >> e) & 1u) {
       double c = po[oi++];
       dc = c - cprev;
       cprev = c;
@@ -162,20 +171,11 @@ __device__ __forceinline__ void cost_terms(uint32_t omask, uint32_t wmask, const
     Bs[e] = 0.0;
     Bt[e] = 0.0;
     if ((wmask >> e) & 1u) {
-      if (kMode & C_LEVELS) {
-        const double lv = pw[wi];
-        if (lv > -1.0e290) {
-          Bl[e] = cprev + lv;
-          Bs[e] = 1.0;
-          Bt[e] = mw[wi];
-        }
-      } else {
-        double ex, mt;
-        Tr<double>::split(mw[wi], ex, mt);
-        if (mt > 0.0) {
-          Bl[e] = (cprev + pw[wi]) + ex;
-          Bs[e] = mt;
-        }
+      double ex, mt;
+      split_mass(mw[wi], ex, mt);
+      if (mt > 0.0) {
+        Bl[e] = (cprev + pw[wi]) + ex;
+        Bs[e] = mt;
       }
       ++wi;
     }
@@ -222,15 +222,13 @@ __device__ __forceinline__ AggM load_aggm(const double* o) {
   return AggM{__ldcg(o), __ldcg(o + 1), __ldcg(o + 2), __ldcg(o + 3), __ldcg(o + 4)};
 }
 
-template <bool kMaps, int kMode>
+template <bool kMaps>
 __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CostSmem& sm = *reinterpret_cast<CostSmem*>(smem_raw);
   const int tid = threadIdx.x;
   const int C = a.C;
-  const int line = (int)(blockIdx.x / (unsigned)C);
-  const int tile = (int)blockIdx.x - line * C;
-  const int64_t ob = (int64_t)line * a.o_ls, wb = (int64_t)line * a.w_ls;
+  const int tile = (int)blockIdx.x;
   const int64_t k0 = (int64_t)tile * kTile;
   const int64_t kend = min(k0 + (int64_t)kTile, a.L);
   const int x0 = a.tile_x0[tile], x1 = a.tile_x0[tile + 1];
@@ -245,23 +243,23 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
   uint32_t bits = (seg < a.L) ? ((a.tbits[seg >> 5] >> (seg & 31)) & ((1u << kElems) - 1u)) : 0u;
   const uint32_t wmask = bits & vmask, omask = (~bits) & vmask;
   double g[kElems];
-  load_gaps<double>(a.gap, seg, g);
+  load_gaps(a.gap, seg, g);
   const int o_before = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
   // threads past the end of the sequence own no points; keep their index in range
   const int w_before = min((int)(seg - k0) - o_before, n_w);
   for (int i = tid; i < n_o + 1; i += kThreads) {
-    const int64_t gi = ob + (int64_t)max(y0 - 1 + i, 0) * a.o_es;
-    sm.pot[i] = (kMode & C_ZERO_FRAME) ? 0.0 : a.py[gi];
-    sm.mass[i] = (kMode & C_INTER) ? 0.0 : a.v[gi];
+    const int64_t gi = max(y0 - 1 + i, 0);
+    sm.pot[i] = a.py[gi];
+    sm.mass[i] = a.v[gi];
   }
   for (int i = tid; i < n_w + 1; i += kThreads) {
-    const int64_t gi = wb + (int64_t)max(x0 - 1 + i, 0) * a.w_es;
+    const int64_t gi = max(x0 - 1 + i, 0);
     sm.pot[wofs + i] = a.px[gi];
     sm.mass[wofs + i] = a.u[gi];
   }
   __syncthreads();
   double Af[kElems], Ab[kElems], Bl[kElems], Bs[kElems], Bt[kElems];
-  cost_terms<kMode>(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
+  cost_terms(omask, wmask, g, sm.pot, o_before, sm.pot + wofs, sm.mass + wofs, w_before + 1,
                     Af, Ab, Bl, Bs, Bt);
   AggM tf, tb;
   if (kMaps) {
@@ -291,42 +289,33 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
 #pragma unroll
     for (int e = kElems - 1; e >= 0; --e) {
       if ((omask >> e) & 1u) {
-        LSM s2 = lsm_add(fm[e], fs[e], ft[e], st.m, st.s, st.t);
-        if (kMode & C_INTER) {
-          const bool pos = s2.s > 0.0;
-          const int64_t zi = (int64_t)line * a.z_ls + (int64_t)(y0 + oi - 1) * a.z_es;
-          a.z1[zi] = pos ? s2.m + log2(s2.s) : -1.0e300;
-          a.z2[zi] = pos ? s2.t / s2.s : 0.0;
-        } else {
-          double sc = exp2(s2.m);
-          double vj = sm.mass[oi];
-          err += fabs(vj * (s2.s * sc) - vj);
-          wt += vj * (s2.t * sc);
-        }
+        const LSM s2 = lsm_add(fm[e], fs[e], ft[e], st.m, st.s, st.t);
+        const double sc = exp2(s2.m);
+        const double vj = sm.mass[oi];
+        err += fabs(vj * (s2.s * sc) - vj);
+        wt += vj * (s2.t * sc);
         --oi;
       }
       if ((wmask >> e) & 1u) st = lsm_add(st.m, st.s, st.t, Bl[e], Bs[e], Bt[e]);
       st.t = fma(g[e], st.s, st.t);
       st.m += Ab[e];
     }
-    if (!(kMode & C_INTER)) {
-      err = warp_sum(err);
-      wt = warp_sum(wt);
-      if ((tid & 31) == 0) {
-        sm.red[0][tid >> 5] = err;
-        sm.red[1][tid >> 5] = wt;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double se = 0.0, sw = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) { se += sm.red[0][w]; sw += sm.red[1][w]; }
-        a.part[2 * (int64_t)blockIdx.x] = se;
-        a.part[2 * (int64_t)blockIdx.x + 1] = sw;
-      }
+    err = warp_sum(err);
+    wt = warp_sum(wt);
+    if ((tid & 31) == 0) {
+      sm.red[0][tid >> 5] = err;
+      sm.red[1][tid >> 5] = wt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double se = 0.0, sw = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) { se += sm.red[0][w]; sw += sm.red[1][w]; }
+      a.part[2 * (int64_t)blockIdx.x] = se;
+      a.part[2 * (int64_t)blockIdx.x + 1] = sw;
     }
   }
   // ticket
-  const int total = a.lines * C;
+  const int total = C;
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -335,24 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
   __syncthreads();
   if (!sm.last) return;
   __threadfence();
-  if (kMaps && a.lines > 1) {
-    // line batches: one thread per line scans its few tiles; lines start empty
-    for (int l = tid; l < a.lines; l += kThreads) {
-      const int64_t b = (int64_t)l * C;
-      LSM st = LSM{-1.0e300, 0.0, 0.0};
-      for (int t = 0; t < C; ++t) {
-        double* cw = a.carry + 6 * (b + t);
-        cw[0] = st.m; cw[1] = st.s; cw[2] = st.t;
-        st = aggm_apply(load_aggm(a.agg + 10 * (b + t)), st);
-      }
-      st = LSM{-1.0e300, 0.0, 0.0};
-      for (int t = C - 1; t >= 0; --t) {
-        double* cw = a.carry + 6 * (b + t);
-        cw[3] = st.m; cw[4] = st.s; cw[5] = st.t;
-        st = aggm_apply(load_aggm(a.agg + 10 * (b + t) + 5), st);
-      }
-    }
-  } else if (kMaps) {
+  if (kMaps) {
     // scan the tile maps into carries (same layout as carry_scan, 3 values per state)
     const int per = (C + kThreads - 1) / kThreads;
     const int t0 = min(C, tid * per), t1 = min(C, t0 + per);
@@ -373,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
       a.carry[6 * t + 3] = st.m; a.carry[6 * t + 4] = st.s; a.carry[6 * t + 5] = st.t;
       st = aggm_apply(load_aggm(a.agg + 10 * t + 5), st);
     }
-  } else if (!(kMode & C_INTER)) {
+  } else {
     double se = 0.0, sw = 0.0;
     for (int t = tid; t < total; t += kThreads) {
       se += __ldcg(a.part + 2 * t);
@@ -398,33 +370,28 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
   if (tid == 0) *a.ticket = 0;
 }
 
-template <int kMode>
 finom_status run_cost(const CostArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(CostSmem);
   static bool attr = false;
   if (!attr) {
-    FINOM_CUDA(cudaFuncSetAttribute(k_cost<true, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FINOM_CUDA(cudaFuncSetAttribute(k_cost<false, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FINOM_CUDA(cudaFuncSetAttribute(k_cost<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FINOM_CUDA(cudaFuncSetAttribute(k_cost<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  const unsigned grid = (unsigned)((int64_t)a.C * a.lines);
-  k_cost<true, kMode><<<grid, kThreads, smem, s>>>(a);
-  k_cost<false, kMode><<<grid, kThreads, smem, s>>>(a);
+  k_cost<true><<<(unsigned)a.C, kThreads, smem, s>>>(a);
+  k_cost<false><<<(unsigned)a.C, kThreads, smem, s>>>(a);
   FINOM_CUDA(cudaGetLastError());
   return FINOM_OK;
 }
 
-CostArgs cost_args(const finom_plan_s* p, int lines, double* scratch, int32_t* ticket) {
+CostArgs cost_args(const finom_plan_s* p, double* scratch, int32_t* ticket) {
   CostArgs a{};
   a.tbits = p->tbits;
   a.gap = p->gap64;
   a.tile_x0 = p->tile_x0;
   a.L = p->L;
   a.C = (int)p->C;
-  a.lines = lines;
-  a.o_es = 1;
-  a.w_es = 1;
-  const size_t T = (size_t)p->C * lines;
+  const size_t T = (size_t)p->C;
   a.agg = scratch;
   a.carry = scratch + 10 * T;
   a.part = scratch + 16 * T;
@@ -445,57 +412,12 @@ finom_status cost64(finom_plan_s* p, const double* px, const double* py, const d
   FINOM_CUDA(cudaMallocAsync(&scratch, sizeof(double) * (18 * T + 2), s));
   FINOM_CUDA(cudaMallocAsync(&ticket, sizeof(int32_t), s));
   FINOM_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int32_t), s));
-  CostArgs a = cost_args(p, 1, scratch, ticket);
+  CostArgs a = cost_args(p, scratch, ticket);
   a.px = px; a.py = py; a.u = u; a.v = v;
-  finom_status rc = run_cost<0>(a, s);
+  finom_status rc = run_cost(a, s);
   if (rc != FINOM_OK) return rc;
   double h[2];
   FINOM_CUDA(cudaMemcpyAsync(h, a.out, sizeof(h), cudaMemcpyDeviceToHost, s));
-  FINOM_CUDA(cudaStreamSynchronize(s));
-  cudaFreeAsync(scratch, s);
-  cudaFreeAsync(ticket, s);
-  *err = h[0];
-  *w1 = h[1] * p->eps * 0.69314718055994530942;
-  return FINOM_OK;
-}
-
-// The same for a 2D plan (Sec. 3, Appendix A).  pa: smooth potentials of the
-// first grid, row-major (i + M k); pb: of the second grid, column-major
-// (l + N j); u, v: masses in the same layouts.  The separable cost
-// |x1_k - x2_l| + |y1_i - y2_j| is carried as a moment through both passes:
-//   pass y (rows k of the first grid): S'(k, j) = sum_i phi(k,i) Ky(i,j),
-//       T'(k, j) = sum_i phi(k,i) Ky(i,j) Gy(i,j)
-//   pass x (columns j): S(l, j) = sum_k Kx(k,l) S'(k,j),
-//       T(l, j) = sum_k Kx(k,l) (T'(k,j) + Gx(k,l) S'(k,j))
-// so that err = sum v |S psi - 1| and <C, Gamma> = eps ln2 sum v T psi.
-finom_status cost64_2d(finom_plan_s* p, const double* pa, const double* pb, const double* u,
-                       const double* v, double* err, double* w1, cudaStream_t s) {
-  finom_plan_s* ax = p->ax;
-  finom_plan_s* ay = p->ay;
-  const int64_t N = ax->N, M = ay->N;
-  const size_t T = std::max((size_t)ax->C * M, (size_t)ay->C * N);
-  double* scratch = nullptr;
-  int32_t* ticket = nullptr;
-  FINOM_CUDA(cudaMallocAsync(&scratch, sizeof(double) * (18 * T + 2), s));
-  FINOM_CUDA(cudaMallocAsync(&ticket, sizeof(int32_t), s));
-  FINOM_CUDA(cudaMemsetAsync(ticket, 0, sizeof(int32_t), s));
-  double* z1 = p->st.z;
-  double* z2 = p->st.z + N * M;
-  // pass y: lines = rows k of the first grid (W = y1, weights phi), outputs
-  // on y2 with frame 0, written column-major (k + N j)
-  CostArgs a = cost_args(ay, (int)N, scratch, ticket);
-  a.px = pa; a.u = u; a.w_ls = M; a.w_es = 1;
-  a.z1 = z1; a.z2 = z2; a.z_ls = 1; a.z_es = N;
-  finom_status rc = run_cost<C_ZERO_FRAME | C_INTER>(a, s);
-  if (rc != FINOM_OK) return rc;
-  // pass x: lines = columns j (W = x1 with the moments of pass y, O = x2)
-  CostArgs b = cost_args(ax, (int)M, scratch, ticket);
-  b.px = z1; b.u = z2; b.w_ls = N; b.w_es = 1;
-  b.py = pb; b.v = v; b.o_ls = N; b.o_es = 1;
-  rc = run_cost<C_LEVELS>(b, s);
-  if (rc != FINOM_OK) return rc;
-  double h[2];
-  FINOM_CUDA(cudaMemcpyAsync(h, b.out, sizeof(h), cudaMemcpyDeviceToHost, s));
   FINOM_CUDA(cudaStreamSynchronize(s));
   cudaFreeAsync(scratch, s);
   cudaFreeAsync(ticket, s);

@@ -39,32 +39,30 @@ constexpr int kChunkIters = 16;
 
 struct SolveState {
   bool ready = false;
-  void* px[2] = {nullptr, nullptr};   // absorbed x-side potential (log2 units), ping-pong
-  void* py[2] = {nullptr, nullptr};   // absorbed y-side potential
-  void* mu = nullptr;                 // x masses, plan precision (normalised)
-  void* nu = nullptr;                 // y masses
+  void* px[2] = {nullptr, nullptr};   // x-side (mu) levels of the loop, ping-pong: 1D plans and
+  void* py[2] = {nullptr, nullptr};   //   batches (beta+, beta-) per point; grid plans log-weights
   double* mu64 = nullptr;             // x masses, float64 (normalised)
   double* nu64 = nullptr;
   double* tx = nullptr;               // float64 scratch, N
   double* ty = nullptr;               // float64 scratch, M
-  void* aggs = nullptr;               // 6 * C tile maps
-  void* carries = nullptr;            // 4 * C tile carries
-  double* part = nullptr;             // C per-tile partial sums
-  double* scal = nullptr;             // 512 + 8 float64 scalars
-  int32_t* ctrl = nullptr;            // loop control words (see apply.cuh)
+  void* aggs = nullptr;               // per tile (unit): two log-sum states of the tile aggregates
+  void* carries = nullptr;            // per tile (unit): two log-sum states entering the tile
+  double* part = nullptr;             // per tile (unit): marginal-error partial sums
+  double* scal = nullptr;             // 512 + 8 float64 scalars ([0]: error of the last check)
+  int32_t* ctrl = nullptr;            // loop control: [0] ticket [1] done [2] iteration [3] iterations at
+                                      //   exit [4] converged (batches: [2] active instances [3] active
+                                      //   tiles [6] an instance retired since the last compaction)
   int* bad = nullptr;
-  void* qo = nullptr;                 // products: O-side frame potentials
-  void* qom = nullptr;                // products: O-side masses (read, unused)
-  void* qw = nullptr;                 // products: W-side potentials
-  void* qwm = nullptr;                // products: W-side masses
-  void* q2 = nullptr;                 // 2D: log2 sums between the two passes of an application
-  int32_t* ictl = nullptr;            // batch: 4 x B per-instance control (done | iteration | at exit | converged)
+  void* qo = nullptr;                 // products: O-side frame levels
+  void* qom = nullptr;                // log2 masses of x (products: unused)
+  void* qw = nullptr;                 // products: W-side levels
+  void* qwm = nullptr;                // log2 masses of y
+  void* q2 = nullptr;                 // grid plans: partial products between the axis passes (2 grids)
+  int32_t* ictl = nullptr;            // batch: 6 x B per-instance control (done | iteration | at exit |
+                                      //   converged | parity flip | iteration budget)
   double* ierr = nullptr;             // batch: per instance, the error of its last check
   double* itol = nullptr;             // batch: per instance, the loop tolerance
-  void* iuni = nullptr;               // batch: per instance (1/N, 1/M) for the start phi, psi
   int32_t* alist = nullptr;           // batch: the tiles of the active instances
-  double* t2 = nullptr;               // 2D: float64 scratch, one grid
-  double* z = nullptr;                // 2D: float64 moments between the two cost passes (2 grids)
   cudaStream_t stream = nullptr;      // internal stream (graph capture needs a non-legacy stream)
   cudaGraphExec_t body = nullptr;     // two Sinkhorn iterations
   cudaGraphExec_t chunk = nullptr;    // kChunkIters iterations (stepwise solves)
@@ -91,8 +89,7 @@ struct finom_plan_s {
   int32_t* zeta = nullptr;       // #{j : y_j <= x_i}
   int32_t* zetaT = nullptr;      // #{i : x_i <= y_j}
   uint32_t* tbits = nullptr;     // merged type bits, bit set = x point
-  void* gap = nullptr;           // per merged point: (z_k - z_{k-1}) / (eps ln 2), plan precision
-  double* gap64 = nullptr;       // float64 gaps (the cost kernel uses them)
+  double* gap64 = nullptr;       // per merged point: (z_k - z_{k-1}) / (eps ln 2) (the float64 cost kernel)
   int32_t* tile_x0 = nullptr;    // C + 1 entries: number of x points before each tile
   // tiles of the fused half-step kernel on a 1D plan: elems points per thread
   // (kElems, or 1, 2, 4 for small problems), Ce tiles of elems * kThreads
@@ -101,13 +98,7 @@ struct finom_plan_s {
   int elems = finom::kElems;
   int64_t Ce = 0;
   int32_t* tile_x0e = nullptr;
-  int32_t* fw[2] = {nullptr, nullptr};  // per tile, [o_is_x]: the W point before the O point
-                                        // that precedes the tile (frames of 2D first passes)
-  // 2D plans (Sec. 3): grids x1 (x) y1 and x2 (x) y2 with N points on the x
-  // axis and M on the y axis; ax merges x1 with x2, ay merges y1 with y2
-  int dim = 1;
-  finom_plan_s* ax = nullptr;
-  finom_plan_s* ay = nullptr;
+  int dim = 1;                   // axes of a grid plan (1: a 1D or batch plan)
   // batches of independent 1D instances (batch.cu): instance b owns x[offx[b] ..
   // offx[b+1]), y[offy[b] .. offy[b+1]) and the tiles itile[b] .. itile[b+1]-1
   // of the packed merged arrays (every instance starts on a tile boundary)
@@ -156,22 +147,13 @@ int tune_pick_batch(finom_precision prec);
 void free_plan(finom_plan_s* p);
 finom_status cost64(finom_plan_s* p, const double* px, const double* py, const double* u,
                     const double* v, double* err, double* w1, cudaStream_t s);
-finom_status cost64_2d(finom_plan_s* p, const double* pa, const double* pb, const double* u,
-                       const double* v, double* err, double* w1, cudaStream_t s);
-// 2D plans (api2d.cu)
-finom_status plan2d_build(finom_plan_s* p, const double* x1, const double* x2, int64_t N,
-                          const double* y1, const double* y2, int64_t M, cudaStream_t s);
-void plan2d_free(finom_plan_s* p);
-finom_status kv2d(finom_plan_s* p, bool transpose_k, bool logmode, const double* a, const double* b,
-                  double* out, cudaStream_t s);
-finom_status solve2d(finom_plan_s* p, const double* u, const double* v, double tol, int64_t maxit,
-                     double* f, double* g, int32_t warm, finom_result* res, cudaStream_t s);
-finom_status solve2d_begin(finom_plan_s* p, const double* u, const double* v, double tol,
-                           int64_t maxit, const double* f0, const double* g0, cudaStream_t s);
-finom_status solve2d_step(finom_plan_s* p, int64_t iters, cudaStream_t s);
-finom_status solve2d_end(finom_plan_s* p, double* f, double* g, finom_result* res, cudaStream_t s);
-finom_status cost2d(finom_plan_s* p, const double* u, const double* v, const double* f,
-                    const double* g, double* w1, double* err, cudaStream_t s);
+// float64 vector helpers (vec.cu)
+finom_status normalise_masses(const double* u, int64_t n, double* m64, double* scratch, int* bad,
+                              double* total_out, cudaStream_t s);
+void pot_from_f(const double* f, const double* m64, int64_t n, double scale, double* pot, cudaStream_t s);
+void fill_d(double* f, int64_t n, double v, cudaStream_t s);
+void add_scaled(double* out, const double* a, double sc, int64_t n, cudaStream_t s);
+void dot_pos(const double* m, const double* f, int64_t n, double* out, cudaStream_t s);
 // batches of 1D instances (batch.cu)
 finom_status plan_batch_build(finom_plan_s* p, const double* x, const int64_t* offx, const double* y,
                               const int64_t* offy, int64_t B, const double* eps, cudaStream_t s);

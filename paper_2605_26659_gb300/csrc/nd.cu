@@ -40,11 +40,6 @@ namespace finom {
 
 template <class R>
 finom_status half_launch(const HalfArgs<R>&, int, int, cudaStream_t);
-template <class R>
-finom_status normalise_masses(const double*, int64_t, void*, double*, double*, int*, double*,
-                              cudaStream_t);
-void fill_d(double*, int64_t, double, cudaStream_t);
-void dot_pos(const double*, const double*, int64_t, double*, cudaStream_t);
 
 namespace {
 
@@ -246,8 +241,6 @@ finom_status ensure_state_nd(finom_plan_s* p) {
   FINOM_CUDA(cudaMalloc(&st.qom, lv * G));
   FINOM_CUDA(cudaMalloc(&st.qwm, lv * G));
   FINOM_CUDA(cudaMalloc(&st.q2, lv * 2 * G));
-  FINOM_CUDA(cudaMalloc(&st.mu, sizeof(typename Tr<R>::Mass) * G));
-  FINOM_CUDA(cudaMalloc(&st.nu, sizeof(typename Tr<R>::Mass) * G));
   FINOM_CUDA(cudaMalloc(&st.mu64, sizeof(double) * G));
   FINOM_CUDA(cudaMalloc(&st.nu64, sizeof(double) * G));
   FINOM_CUDA(cudaMalloc(&st.tx, sizeof(double) * std::max<int64_t>(G, 512)));
@@ -400,10 +393,10 @@ finom_status nd_begin(finom_plan_s* p, const double* u, const double* v, double 
   const int64_t G = p->nd_G;
   // masses: nu's in L_0; mu's normalised in L_0, then turned into L_{d-1}
   double* red = st.scal + 256;   // partial sums of the normalisation
-  rc = normalise_masses<double>(u, G, st.tx, st.tx, red, st.bad, nullptr, s);
+  rc = normalise_masses(u, G, st.tx, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   nd_rot(p, 0, false, (const double*)st.tx, st.mu64, s);
-  rc = normalise_masses<double>(v, G, st.nu64, st.nu64, red, st.bad, nullptr, s);
+  rc = normalise_masses(v, G, st.nu64, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   const double none = (double)HT<R>::kNone;
   k_grid_lmass<<<nb(G), 256, 0, s>>>(st.mu64, G, (LvT<R>*)st.qom, none);
@@ -803,10 +796,10 @@ finom_status cost_nd(finom_plan_s* p, const double* u, const double* v, const do
   const int64_t G = p->nd_G;
   double* red = st.scal + 256;
   // mu's masses and log-weights into L_{d-1} (through ty), nu's in L_0
-  rc = normalise_masses<double>(u, G, st.ty, st.ty, red, st.bad, nullptr, s);
+  rc = normalise_masses(u, G, st.ty, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   nd_rot(p, 0, false, (const double*)st.ty, st.mu64, s);
-  rc = normalise_masses<double>(v, G, st.nu64, st.nu64, red, st.bad, nullptr, s);
+  rc = normalise_masses(v, G, st.nu64, red, st.bad, nullptr, s);
   if (rc != FINOM_OK) return rc;
   const double scale = 1.0 / (p->eps * kLn2);
   k_grid_set<<<nb(G), 256, 0, s>>>(st.ty, G, f, scale, 0.0, -INFINITY);

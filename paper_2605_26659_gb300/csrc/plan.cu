@@ -8,6 +8,13 @@
 // 2^{-gap_k}, gap_k = (z_k - z_{k-1}) / (eps ln 2): the ratio vectors r, r'
 // of the Theorems on the vector representation of K_L and K_U (eq. ratio)
 // are products of these factors over the merged points between two rows.
+//
+// The merge is a merge path: one binary search on the diagonal k0 of every
+// tile boundary gives the x points among the first k0 merged points; each
+// tile then stages its x and y runs in shared memory, every thread finds
+// its own diagonal inside the tile the same way and merges its points
+// serially, writing the type bits, the gaps and the dividing index of its x
+// points.  Every point is read once from global memory.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -31,69 +38,97 @@ __global__ void k_check_sorted(const double* a, int64_t n, int* bad) {
   if (!ok) atomicOr(bad, 1);
 }
 
-// number of entries of sorted a[0..n) that are <= v (strict = false) or < v (strict = true)
-__device__ __forceinline__ int64_t count_le(const double* a, int64_t n, double v, bool strict) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    bool go_right = strict ? (a[mid] < v) : (a[mid] <= v);
-    if (go_right) lo = mid + 1; else hi = mid;
+// x points among the first d merged points (y before x on ties): the
+// number of k with pos(x_k) < d, i.e. with x_k before y_{d-k-1}, found by
+// bisection on the diagonal i + j = d
+__device__ __forceinline__ int64_t merge_split(const double* x, int64_t N, const double* y, int64_t M,
+                                               int64_t d) {
+  int64_t lo = d > M ? d - M : 0, hi = d < N ? d : N;
+  while (lo < hi) {   // for lo <= k < hi: 0 <= d - k - 1 < M
+    const int64_t k = (lo + hi) >> 1;
+    if (x[k] < y[d - k - 1]) lo = k + 1; else hi = k;
   }
   return lo;
 }
 
-__global__ void k_ranks_x(const double* x, int64_t N, const double* y, int64_t M, int32_t* zeta,
-                          int64_t* posx) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int64_t z = count_le(y, M, x[i], false);
-  zeta[i] = (int32_t)z;
-  posx[i] = i + z;
-}
-
-__global__ void k_ranks_y(const double* x, int64_t N, const double* y, int64_t M, int32_t* zetaT,
-                          int64_t* posy) {
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  double v = y[j];
-  zetaT[j] = (int32_t)count_le(x, N, v, false);
-  posy[j] = j + count_le(x, N, v, true);
-}
-
-__global__ void k_scatter(const double* a, int64_t n, const int64_t* pos, double* z, uint8_t* type,
-                          uint8_t t) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  z[pos[i]] = a[i];
-  type[pos[i]] = t;
-}
-
-// gaps in bits and packed type bits; one thread per merged position, padded to
-// a multiple of 32 so every warp writes one whole word.
-__global__ void k_gaps_bits(const double* z, const uint8_t* type, int64_t L, double inv_eps_ln2,
-                            double* gap64, float* gap32, uint32_t* bits) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  bool in = k < L;
-  int t = in ? (int)type[k] : 0;
-  unsigned w = __ballot_sync(0xffffffffu, t != 0);
-  if ((threadIdx.x & 31) == 0 && (k >> 5) < ((L + 31) >> 5)) bits[k >> 5] = w;
-  if (!in) return;
-  double g = (k == 0) ? 0.0 : (z[k] - z[k - 1]) * inv_eps_ln2;
-  gap64[k] = g;
-  if (gap32) gap32[k] = (float)g;
-}
-
-// tile_x0[t] = number of x points whose merged position is < t * kTile
-__global__ void k_tiles(const int64_t* posx, int64_t N, int64_t C, int32_t* tile_x0) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// tile_x0[t] = x points among the first min(t * kTile, L) merged points
+__global__ void k_tile_split(const double* x, int64_t N, const double* y, int64_t M, int64_t C,
+                             int32_t* tile_x0) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t > C) return;
-  int64_t bound = t * (int64_t)kTile;
+  tile_x0[t] = (int32_t)merge_split(x, N, y, M, min(t * (int64_t)kTile, N + M));
+}
+
+// One CTA per tile of kTile merged points, kElems per thread: type bits,
+// gaps in bits (gap64) and zeta of the tile's x points.
+__global__ void __launch_bounds__(kThreads) k_merge(const double* x, int64_t N, const double* y, int64_t M,
+                                                    const int32_t* tile_x0, double inv_eps_ln2, int32_t* zeta,
+                                                    double* gap64, uint32_t* bits) {
+  __shared__ double sx[kTile], sy[kTile];
+  const int tid = threadIdx.x;
+  const int64_t L = N + M;
+  const int64_t k0 = (int64_t)blockIdx.x * kTile;
+  const int64_t kend = min(k0 + (int64_t)kTile, L);
+  const int64_t x0 = tile_x0[blockIdx.x], x1 = tile_x0[blockIdx.x + 1];
+  const int64_t y0 = k0 - x0, y1 = kend - x1;
+  const int nx = (int)(x1 - x0), ny = (int)(y1 - y0);
+  for (int i = tid; i < nx; i += kThreads) sx[i] = x[x0 + i];
+  for (int j = tid; j < ny; j += kThreads) sy[j] = y[y0 + j];
+  __syncthreads();
+  // this thread's diagonal inside the tile
+  const int dl = tid * kElems;
+  uint32_t b8 = 0;
+  if (k0 + dl < kend) {
+    int lo = dl > ny ? dl - ny : 0, hi = dl < nx ? dl : nx;
+    while (lo < hi) {
+      const int k = (lo + hi) >> 1;
+      if (sx[k] < sy[dl - k - 1]) lo = k + 1; else hi = k;
+    }
+    int i = lo, j = dl - lo;
+    // the merged point before this thread's first one: the later (larger)
+    // of the x and y points before the split
+    double prev = -INFINITY;
+    if (x0 + i > 0) prev = x[x0 + i - 1];
+    if (y0 + j > 0) prev = fmax(prev, y[y0 + j - 1]);
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      const int64_t k = k0 + dl + e;
+      if (k >= kend) break;
+      const bool take_x = i < nx && (j >= ny || sx[i] < sy[j]);
+      double v;
+      if (take_x) {
+        v = sx[i];
+        zeta[x0 + i] = (int32_t)(y0 + j);   // the y points before x_i
+        b8 |= 1u << e;
+        ++i;
+      } else {
+        v = sy[j];
+        ++j;
+      }
+      gap64[k] = k == 0 ? 0.0 : (v - prev) * inv_eps_ln2;
+      prev = v;
+    }
+  }
+  // kElems-bit chunks of 32 / kElems consecutive threads form one word
+  constexpr int kPer = 32 / kElems;
+  uint32_t w = b8 << ((tid % kPer) * kElems);
+#pragma unroll
+  for (int o = 1; o < kPer; o <<= 1) w |= __shfl_xor_sync(0xffffffffu, w, o);
+  if (tid % kPer == 0) bits[(k0 + dl) >> 5] = w;
+}
+
+// zetaT(j) = #{i : x_i <= y_j} (the dividing index of K^T, Definition applied
+// to K^T; reported by finom_dividing_index only)
+__global__ void k_zeta_t(const double* x, int64_t N, const double* y, int64_t M, int32_t* zetaT) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double v = y[j];
   int64_t lo = 0, hi = N;
   while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (posx[mid] < bound) lo = mid + 1; else hi = mid;
+    const int64_t mid = (lo + hi) >> 1;
+    if (x[mid] <= v) lo = mid + 1; else hi = mid;
   }
-  tile_x0[t] = (int32_t)lo;
+  zetaT[j] = (int32_t)lo;
 }
 
 // the same table for tiles of `tile` points from the dividing index: the
@@ -110,23 +145,6 @@ __global__ void k_tiles_zeta(const int32_t* zeta, int64_t N, int64_t C, int64_t 
   tile_x0[t] = (int32_t)lo;
 }
 
-// fw[o_is_x][t]: index of the last W point before the O point that precedes
-// tile t (0 when there is none); the O point before the first O point of the
-// sequence is that point itself
-__global__ void k_frame_w(const double* x, int64_t N, const double* y, int64_t M, const int32_t* zeta,
-                          const int32_t* tile_x0, int64_t C, int64_t L, int32_t* fw_y, int32_t* fw_x) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t > C) return;
-  const int64_t k0 = min(t * (int64_t)kTile, L);
-  const int64_t x0 = tile_x0[t], y0 = k0 - x0;
-  // O = x: W points before x_o are the y_j <= x_o
-  const int64_t ox = x0 > 0 ? x0 - 1 : 0;
-  fw_x[t] = (int32_t)max((int64_t)zeta[ox] - 1, (int64_t)0);
-  // O = y: W points before y_o are the x_i < y_o
-  const int64_t oy = y0 > 0 ? min(y0 - 1, M - 1) : 0;
-  fw_y[t] = (int32_t)max(count_le(x, N, y[oy], true) - 1, (int64_t)0);
-}
-
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -135,8 +153,8 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
   const int64_t N = p->N, M = p->M, L = N + M;
   p->L = L;
   p->C = (L + kTile - 1) / kTile;
-  const int64_t words = (L + 31) / 32;
-  // tile-aligned word count so vector loads past L stay inside the allocation
+  // tile-aligned sizes: every tile writes its whole words of type bits, and
+  // vector loads past L stay inside the allocations
   const int64_t Lpad = p->C * kTile;
 
   FINOM_CUDA(cudaMalloc(&p->x, sizeof(double) * N));
@@ -161,44 +179,15 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
   FINOM_CUDA(cudaMalloc(&p->zeta, sizeof(int32_t) * N));
   FINOM_CUDA(cudaMalloc(&p->zetaT, sizeof(int32_t) * M));
   FINOM_CUDA(cudaMalloc(&p->tbits, sizeof(uint32_t) * (Lpad / 32)));
-  FINOM_CUDA(cudaMemsetAsync(p->tbits, 0, sizeof(uint32_t) * (Lpad / 32), s));
   FINOM_CUDA(cudaMalloc(&p->gap64, sizeof(double) * Lpad));
   FINOM_CUDA(cudaMemsetAsync(p->gap64, 0, sizeof(double) * Lpad, s));
-  float* gap32 = nullptr;
-  if (p->prec == FINOM_F32_LOG) {
-    FINOM_CUDA(cudaMalloc(&gap32, sizeof(float) * Lpad));
-    FINOM_CUDA(cudaMemsetAsync(gap32, 0, sizeof(float) * Lpad, s));
-    p->gap = gap32;
-  } else {
-    p->gap = p->gap64;
-  }
   FINOM_CUDA(cudaMalloc(&p->tile_x0, sizeof(int32_t) * (p->C + 1)));
-
-  int64_t *posx = nullptr, *posy = nullptr;
-  double* z = nullptr;
-  uint8_t* type = nullptr;
-  FINOM_CUDA(cudaMalloc(&posx, sizeof(int64_t) * N));
-  FINOM_CUDA(cudaMalloc(&posy, sizeof(int64_t) * M));
-  FINOM_CUDA(cudaMalloc(&z, sizeof(double) * L));
-  FINOM_CUDA(cudaMalloc(&type, L));
-
-  k_ranks_x<<<nblk(N, 256), 256, 0, s>>>(p->x, N, p->y, M, p->zeta, posx);
-  k_ranks_y<<<nblk(M, 256), 256, 0, s>>>(p->x, N, p->y, M, p->zetaT, posy);
-  k_scatter<<<nblk(N, 256), 256, 0, s>>>(p->x, N, posx, z, type, 1);
-  k_scatter<<<nblk(M, 256), 256, 0, s>>>(p->y, M, posy, z, type, 0);
   const double inv = 1.0 / (p->eps * std::log(2.0));
-  k_gaps_bits<<<nblk(words * 32, 256), 256, 0, s>>>(z, type, L, inv, p->gap64, gap32, p->tbits);
-  k_tiles<<<nblk(p->C + 1, 256), 256, 0, s>>>(posx, N, p->C, p->tile_x0);
-  FINOM_CUDA(cudaMalloc(&p->fw[0], sizeof(int32_t) * (p->C + 1)));
-  FINOM_CUDA(cudaMalloc(&p->fw[1], sizeof(int32_t) * (p->C + 1)));
-  k_frame_w<<<nblk(p->C + 1, 256), 256, 0, s>>>(p->x, N, p->y, M, p->zeta, p->tile_x0, p->C, L,
-                                                  p->fw[0], p->fw[1]);
+  k_tile_split<<<nblk(p->C + 1, 256), 256, 0, s>>>(p->x, N, p->y, M, p->C, p->tile_x0);
+  k_merge<<<(unsigned)p->C, kThreads, 0, s>>>(p->x, N, p->y, M, p->tile_x0, inv, p->zeta, p->gap64, p->tbits);
+  k_zeta_t<<<nblk(M, 256), 256, 0, s>>>(p->x, N, p->y, M, p->zetaT);
   FINOM_CUDA(cudaGetLastError());
   FINOM_CUDA(cudaStreamSynchronize(s));
-  cudaFree(posx);
-  cudaFree(posy);
-  cudaFree(z);
-  cudaFree(type);
   p->elems = kElems;
   p->Ce = p->C;
   p->tile_x0e = p->tile_x0;
@@ -239,12 +228,9 @@ void free_plan(finom_plan_s* p) {
   cudaFree(p->zeta);
   cudaFree(p->zetaT);
   cudaFree(p->tbits);
-  if (p->gap && p->gap != p->gap64) cudaFree(p->gap);
   cudaFree(p->gap64);
   if (p->tile_x0e && p->tile_x0e != p->tile_x0) cudaFree(p->tile_x0e);
   cudaFree(p->tile_x0);
-  cudaFree(p->fw[0]);
-  cudaFree(p->fw[1]);
 }
 
 }  // namespace finom
