@@ -210,6 +210,37 @@ struct HT<float> {
   }
 };
 
+// 2^x in float64 for the scans: x = n + f with n = rint(x) and |f| <= 1/2,
+// 2^f = e^{f ln 2} summed as its Taylor series to degree 13 (for |f ln 2| <=
+// 0.347 the remainder is below 1e-17 relative), and n added to the binary
+// exponent.  Arguments below -1021 give 0 (the terms they weigh are below
+// 2^-1021 of the sums they join), above 1023 infinity.  About 16 float64
+// instructions: on GB300 every float64 warp instruction occupies its
+// sub-partition's float64 pipe for 64 cycles, so the scans' combines are
+// counted in these.
+__device__ __forceinline__ double exp2_series(double x) {
+  if (!(x > -1021.0)) return 0.0;
+  if (x > 1023.0) return INFINITY;
+  const double n = rint(x);
+  const double t = (x - n) * 0.69314718055994530942;
+  // 1/k! for k = 13 .. 2
+  double p = 1.6059043836821614599e-10;
+  p = fma(p, t, 2.0876756987868098979e-09);
+  p = fma(p, t, 2.5052108385441718775e-08);
+  p = fma(p, t, 2.7557319223985890653e-07);
+  p = fma(p, t, 2.7557319223985890653e-06);
+  p = fma(p, t, 2.4801587301587301587e-05);
+  p = fma(p, t, 1.9841269841269841270e-04);
+  p = fma(p, t, 1.3888888888888888889e-03);
+  p = fma(p, t, 8.3333333333333333333e-03);
+  p = fma(p, t, 4.1666666666666666667e-02);
+  p = fma(p, t, 1.6666666666666666667e-01);
+  p = fma(p, t, 0.5);
+  p = fma(p, t, 1.0);
+  p = fma(p, t, 1.0);
+  return __longlong_as_double(__double_as_longlong(p) + (long long)n * (1LL << 52));
+}
+
 template <>
 struct HT<double> {
   using Lv = double;
@@ -221,7 +252,7 @@ struct HT<double> {
   __device__ __forceinline__ static Beta pack(Lv p, Lv m) { return make_double2(p, m); }
   __device__ __forceinline__ static Lv none() { return kNone; }
   __device__ __forceinline__ static bool valid(Lv a) { return a > 0.5 * kNone; }
-  __device__ __forceinline__ static double ex2(double x) { return exp2(x); }
+  __device__ __forceinline__ static double ex2(double x) { return exp2_series(x); }
   __device__ __forceinline__ static double lg2(double x) { return log2(x); }
   __device__ __forceinline__ static double lg2_acc(double x) { return log2(x); }
   __device__ __forceinline__ static double diff(Lv a, Lv b) { return a - b; }
@@ -900,6 +931,29 @@ __device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
                     sizeof(R) * 2 * HT<R>::kSt * K, "staging");
   R* buf = reinterpret_cast<R*>(sm.pfM);   // pfM, pfs, sfM, sfs are adjacent
   const int C = a.C;
+  if (C <= 32) {
+    // a few tiles: warp 0 scans the forward aggregates and warp 1 the
+    // backward ones at the same time, one tile per lane (five shuffle
+    // levels instead of the chunked rake; float64 combines on GB300 cost
+    // their pipe time per warp instruction, so the depth is what counts)
+    using H = HT<R>;
+    constexpr int kS = H::kSt;
+    const int tid = threadIdx.x, lane = tid & 31, dir = tid >> 5;
+    if (tid < 64) {
+      const int t = dir == 0 ? lane : C - 1 - lane;   // tile of this lane (dir 1: right to left)
+      const bool in = lane < C;
+      St<R> inc = st_empty<R>();
+      if (in) H::get(a.agg_out + 2 * kS * (int64_t)t + dir * kS, inc.M, inc.s);
+      for (int o = 1; o < C; o <<= 1) {   // (C is uniform: whole levels are skipped)
+        const St<R> u = st_shfl_up(inc, o);
+        if (lane >= o) inc = st_comb(u, inc);
+      }
+      St<R> ex = st_shfl_up(inc, 1);
+      if (lane == 0) ex = st_empty<R>();
+      if (in) H::put(a.carry_out + 2 * kS * (int64_t)t + dir * kS, ex.M, ex.s);
+    }
+    return;
+  }
   const int nch = (C + K - 1) / K;
   St<R> runF = st_empty<R>(), runB = st_empty<R>();
 #pragma unroll 1
