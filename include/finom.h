@@ -197,10 +197,13 @@ finom_status finom_barycentric(finom_plan_t plan, const double* f, const double*
 
 /*
  * Tile size of 1D plans (not a form of the paper: a property of the GPU
- * kernel).  The fused half-step kernel processes tiles of 256 threads x E
- * points, E in {1, 2, 4, 8}.  finom_plan picks E from a tuning table indexed
- * by precision and the bucket b = ceil(log2(N + M)); results of different E
- * agree to rounding (float64) or within the float32 bounds.
+ * kernel).  The half-step kernel processes tiles of 256 threads x E points,
+ * E in {1, 2, 4, 8}, or, for E = -1, tiles of 64 threads x 1 point (many
+ * short tiles on many SMs: the choice of small problems, float64 above all,
+ * whose warp instructions hold GB300's float64 pipe for 64 cycles each).
+ * finom_plan picks E from a tuning table indexed by precision and the bucket
+ * b = ceil(log2(N + M)); results of different E agree to rounding (float64)
+ * or within the float32 bounds.
  *   finom_plan_set_elems  forces E on a 1D plan (2D and batch plans: ENOTSUP);
  *                         releases the plan's solve state (a solve in
  *                         progress ends).  Synchronises `stream`.
@@ -209,11 +212,12 @@ finom_status finom_barycentric(finom_plan_t plan, const double* f, const double*
  *   finom_autotune        the autotuner of one bucket: times `iters` Sinkhorn
  *                         iterations (after 16 warm-up ones) of a synthetic
  *                         problem with N = M = 2^(b-1) (sorted pseudo-random
- *                         points, eps = 1e-2) for E = 1, 2, 4, 8 with CUDA
- *                         events on `stream`, installs the fastest in the
- *                         table, returns it in *best and the four times (us
- *                         per iteration, HOST array of 4, may be NULL) in
- *                         us_per_iter.  4 <= b <= 26.  Synchronous.
+ *                         points, eps = 1e-2) for E = -1, 1, 2, 4, 8 with
+ *                         CUDA events on `stream`, installs the fastest in
+ *                         the table, returns it in *best and the five times
+ *                         (us per iteration, in that order, HOST array of
+ *                         5, may be NULL) in us_per_iter.  4 <= b <= 26.
+ *                         Synchronous.
  */
 finom_status finom_plan_set_elems(finom_plan_t plan, int32_t elems, void* stream);
 finom_status finom_plan_elems(finom_plan_t plan, int32_t* elems, int64_t* tiles);
@@ -225,7 +229,8 @@ finom_status finom_autotune(finom_precision prec, int32_t log2_bucket, int32_t i
 /*
  * finom_plan_batch_elems -- finom_plan_batch with the kernel's points per
  * thread chosen: each instance is packed into tiles of 256 * elems points
- * (elems in {1, 2, 4, 8}; 0 takes the process-wide batch entry of the tuning
+ * (elems in {1, 2, 4, 8}, or -1: tiles of 64 points on 64 threads; 0 takes
+ * the process-wide batch entry of the tuning
  * table, 8 unless finom_tune_set_batch changed it).  Smaller tiles waste less
  * padding on small instances; results agree to rounding across elems.
  * finom_tune_set_batch / finom_tune_get_batch set and read that entry

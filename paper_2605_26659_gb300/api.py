@@ -405,14 +405,15 @@ def finom_tune_get_batch(precision):
 
 
 def finom_autotune(precision, log2_bucket, iters=64, stream=None):
-    """Time E = 1, 2, 4, 8 on a synthetic problem of 2^log2_bucket merged
-    points, install the fastest; returns (best, {E: us per iteration})."""
+    """Time the tile kinds E = -1 (64-point tiles), 1, 2, 4, 8 on a synthetic
+    problem of 2^log2_bucket merged points, install the fastest; returns
+    (best, {E: us per iteration})."""
     load()
     best = _I32()
-    t = (ctypes.c_double * 4)()
+    t = (ctypes.c_double * 5)()
     _check(_lib.finom_autotune(_PREC[precision], int(log2_bucket), int(iters), ctypes.byref(best),
                                ctypes.cast(t, ctypes.c_void_p), _stream(stream)))
-    return best.value, dict(zip((1, 2, 4, 8), list(t)))
+    return best.value, dict(zip((-1, 1, 2, 4, 8), list(t)))
 
 
 def finom_plan_destroy(plan: Plan):

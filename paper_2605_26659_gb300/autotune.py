@@ -46,7 +46,7 @@ def batch(x, offx, y, offy, eps, precision="f32_log", u=None, v=None, iters=8, w
     if v is None:
         v = torch.ones(int(offy[-1]), dtype=torch.float64, device=dev)
     times = {}
-    for e in (1, 2, 4, 8):
+    for e in (-1, 1, 2, 4, 8):
         p = api.finom_plan_batch(x, offx, y, offy, eps, precision, elems=e)
         api.finom_solve_batch_begin(p, u, v, 0.0, 1 << 30)
         api.finom_solve_batch_step(p, warmup)

@@ -623,8 +623,8 @@ finom_status finom_plan_batch_elems(const double* x, const int64_t* offx, const 
   }
   *out = nullptr;
   if (elems == 0) elems = tune_pick_batch(prec);
-  if (elems != 1 && elems != 2 && elems != 4 && elems != kElems) {
-    set_error("finom_plan_batch: points per thread must be 1, 2, 4 or 8");
+  if (!tile_kind_ok(elems)) {
+    set_error("finom_plan_batch: tile kind must be 1, 2, 4 or 8 points per thread, or -1 (64-point tiles)");
     return FINOM_EINVAL;
   }
   if (!x || !y || !offx || !offy || !eps || B < 1 || B > (int64_t)1 << 24 ||
@@ -652,7 +652,7 @@ finom_status finom_plan_batch_elems(const double* x, const int64_t* offx, const 
   }
   finom_plan_s* p = new (std::nothrow) finom_plan_s();
   if (!p) return FINOM_ENOMEM;
-  p->btile = (int64_t)elems * kThreads;
+  p->btile = tile_points(elems);
   p->elems = elems;
   p->eps = eps[0];
   p->prec = prec;

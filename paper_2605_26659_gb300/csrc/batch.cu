@@ -433,7 +433,7 @@ HalfArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q) {
 
 template <class R>
 finom_status launch_half(finom_plan_s* p, bool o_is_x, int q, int mode, cudaStream_t s) {
-  return half_launch<R>(batch_args<R>(p, o_is_x, q), mode, (int)(p->btile / kThreads), s);
+  return half_launch<R>(batch_args<R>(p, o_is_x, q), mode, p->elems, s);
 }
 
 template <class R>

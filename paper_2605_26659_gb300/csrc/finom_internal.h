@@ -24,6 +24,19 @@ constexpr int kThreads = FINOM_THREADS;
 constexpr int kElems = FINOM_ELEMS;
 constexpr int kTile = kThreads * kElems;   // merged points per tile (2048 by default)
 
+// Tiles of the half-step kernel: `elems` points per thread of kThreads
+// threads (1, 2, 4 or kElems), or kElemsSmall: 64 threads with one point
+// each.  Small problems want many small tiles on many SMs with short scans
+// over few run totals; on GB300 a float64 warp instruction holds its
+// sub-partition's float64 pipe for 64 cycles, so small float64 plans most.
+constexpr int kElemsSmall = -1;
+constexpr bool tile_kind_ok(int elems) {
+  return elems == kElemsSmall || elems == 1 || elems == 2 || elems == 4 || elems == kElems;
+}
+constexpr int tile_threads(int elems) { return elems == kElemsSmall ? 64 : kThreads; }
+constexpr int tile_elems(int elems) { return elems == kElemsSmall ? 1 : elems; }
+constexpr int64_t tile_points(int elems) { return (int64_t)tile_elems(elems) * tile_threads(elems); }
+
 void set_error(const std::string& msg);
 finom_status cuda_fail(cudaError_t e, const char* what);
 

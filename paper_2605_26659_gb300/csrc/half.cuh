@@ -29,7 +29,7 @@
 // and the marginal error of Algorithm 1's loop head (Sec. 4) is
 //     sum_k |S_k - mu_k| = sum_k mu_k |2^{delta_k} - 1|.
 //
-// One CTA owns one tile of the merged order (E * kThreads points).  Its weight
+// One CTA owns one tile of the merged order (E points per thread).  Its weight
 // (W) points and output (O) points are handled separately, each as contiguous
 // runs of about equal length per thread (no per-point predication):
 //   1. every thread records, for each O point of its merged points, the
@@ -397,13 +397,22 @@ struct HalfArgs {
   const int32_t* acount;
 };
 
-constexpr int kHSlots = kThreads + kThreads / 32;
+// The template parameter E of the kernel is the tile kind of tile_threads:
+// points per thread, or kElemsSmall for 64-thread tiles of one point each.
+template <class R, int E>
+constexpr int half_threads() { return tile_threads(E); }
+template <int E>
+constexpr int half_e() { return tile_elems(E); }
+
 __device__ __forceinline__ int hslot(int t) { return t + (t >> 5); }
 
 template <class R, int E>
 struct HalfSmem {
   using Lv = typename HT<R>::Lv;
-  static constexpr int T = E * kThreads;
+  static constexpr int NT = half_threads<R, E>();
+  static constexpr int T = half_e<E>() * NT;
+  static constexpr int kSlots = NT + NT / 32;
+  static_assert((NT & (NT - 1)) == 0 && NT >= 64 && NT <= 256, "own[] holds thread indices as bytes");
   Lv pfM[T];      // W phase: running prefix states of the owning thread (levels ...
   R pfs[T];       //   ... and mantissas)
   Lv sfM[T];      // running suffix states
@@ -411,13 +420,13 @@ struct HalfSmem {
   // per thread: run totals, then entry states ([0] forward, [1] backward);
   // level hi / lo parts and mantissas as separate 4-byte arrays so that the
   // raking lanes (8 consecutive slots each, padded) hit distinct banks
-  R slh[2][kHSlots];
-  R sll[2][kHSlots];
-  R sls[2][kHSlots];
+  R slh[2][kSlots];
+  R sll[2][kSlots];
+  R sls[2][kSlots];
   int16_t zl[T];        // per O point of the tile: W points of the tile before it
   uint8_t own[T];       // per W point of the tile: the thread whose run holds it
-  double red[kThreads / 32];
-  int iscan[kThreads / 32];
+  double red[NT / 32];
+  int iscan[NT / 32];
   int last;
   typename HT<R>::Lv totM;   // launch tail: the running carry of a chunk of tiles
   R tots;
@@ -437,13 +446,12 @@ __device__ __forceinline__ St<R> hslot_get(const HalfSmem<R, E>& sm, int dir, in
   return {HT<R>::mk(sm.slh[dir][i], sizeof(R) == 4 ? sm.sll[dir][i] : R(0)), sm.sls[dir][i]};
 }
 
-constexpr int kHPer = kThreads / 32;   // slots raked per lane
-
-// Warps 0 (forward) and 1 (backward): turn the kThreads run totals in the
+// Warps 0 (forward) and 1 (backward): turn the run totals of the threads in the
 // slots into entry states: forward, the carry cf and the totals of threads
 // 0 .. t-1; backward, the carry cb and the totals of threads t+1 .. end.
 template <class R, int E>
 __device__ __forceinline__ void hrake_scan(HalfSmem<R, E>& sm, const St<R>& cf, const St<R>& cb) {
+  constexpr int kHPer = half_threads<R, E>() / 32;   // slots raked per lane
   const int lane = threadIdx.x & 31;
   const int dir = threadIdx.x >> 5;   // 0 or 1
   St<R> f = st_empty<R>();
@@ -482,10 +490,11 @@ __device__ __forceinline__ void hrake_scan(HalfSmem<R, E>& sm, const St<R>& cf, 
   }
 }
 
-// Warps 0 and 1: log-sum of the kThreads partial states of slot direction 0
+// Warps 0 and 1: log-sum of the threads' partial states of slot direction 0
 // (warp 0) and 1 (warp 1); lane 0 stores it at out + dir * kSt.
 template <class R, int E>
 __device__ __forceinline__ void hrake_reduce(HalfSmem<R, E>& sm, R* out) {
+  constexpr int kHPer = half_threads<R, E>() / 32;   // slots raked per lane
   const int lane = threadIdx.x & 31;
   const int dir = threadIdx.x >> 5;
   St<R> f = st_empty<R>();
@@ -502,6 +511,7 @@ __device__ __forceinline__ void hrake_reduce(HalfSmem<R, E>& sm, R* out) {
 // states and (totM, tots) the log-sum of seed and every slot.
 template <class R, int E, int dir>
 __device__ __forceinline__ void hrake_one(HalfSmem<R, E>& sm, const St<R>& seed) {
+  constexpr int kHPer = half_threads<R, E>() / 32;   // slots raked per lane
   const int lane = threadIdx.x & 31;
   St<R> f = st_empty<R>();
 #pragma unroll
@@ -549,12 +559,14 @@ __device__ __forceinline__ R pow2m1(R x) {
 // the loop is already done (the launch does nothing).  Per-thread runs have a
 // fixed trip count E; indices past a thread's run are clamped to a valid
 // point of the tile and its contributions masked, so the loops do not branch.
-template <class R, int kFlags, int E>
-__device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int unit, bool first) {
+template <class R, int kFlags, int EK>
+__device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, EK>& sm, int unit, bool first) {
+  constexpr int E = half_e<EK>();   // points per thread
   using H = HT<R>;
   using Lv = typename H::Lv;
   using Beta = typename H::Beta;
-  constexpr int kT = E * kThreads;
+  constexpr int NT = half_threads<R, EK>();
+  constexpr int kT = E * NT;
   constexpr bool kAgg = (kFlags & H_AGG) != 0;
   constexpr bool kLines = (kFlags & H_LINES) != 0;
   constexpr bool kProd = (kFlags & (H_LOG | H_LIN | H_QOUT | H_FB)) != 0;
@@ -614,7 +626,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
       const uint32_t bits = (a.tbits[seg >> 5] >> (seg & 31)) & ((1u << E) - 1u);
       omask = (a.o_is_x ? bits : ~bits) & vmask;
     }
-    int r = block_exclusive_sum<kThreads>(__popc(omask), sm.iscan);
+    int r = block_exclusive_sum<NT>(__popc(omask), sm.iscan);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((omask >> e) & 1u) sm.zl[r] = (int16_t)(tid * E + e - r);
@@ -628,8 +640,8 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   }
 
   // 2. W phase: running log-sums over this thread's W run
-  const int wlo = (int)(((int64_t)tid * n_w) / kThreads);
-  const int qw = (int)(((int64_t)(tid + 1) * n_w) / kThreads) - wlo;
+  const int wlo = (int)(((int64_t)tid * n_w) / NT);
+  const int qw = (int)(((int64_t)(tid + 1) * n_w) / NT) - wlo;
   St<R> tf = st_empty<R>(), tb = st_empty<R>();
   auto wbeta = [&](int i) -> Beta {
     if constexpr ((kFlags & H_RAW) != 0) {
@@ -659,7 +671,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   } else {
   // longest run of the tile (block-uniform trip count); the loads of a run
   // are all in flight before its chain starts
-  const int qwm = (n_w + kThreads - 1) / kThreads;
+  const int qwm = (n_w + NT - 1) / NT;
   const int wl = max(n_w - 1, 0);
   Beta bw[E];
 #pragma unroll
@@ -690,8 +702,8 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   }
   const int wlast = max(n_w - 1, 0);
   // O run of this thread
-  const int olo = (int)(((int64_t)tid * n_o) / kThreads);
-  const int qo = (int)(((int64_t)(tid + 1) * n_o) / kThreads) - olo;
+  const int olo = (int)(((int64_t)tid * n_o) / NT);
+  const int qo = (int)(((int64_t)(tid + 1) * n_o) / NT) - olo;
   St<R> cf = st_empty<R>(), cb = st_empty<R>();
   if (a.carry_in) {
     const R* c = a.carry_in + 2 * H::kSt * slot;
@@ -708,7 +720,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
   // last point with the results masked)
   R err = R(0);
   St<R> nf = st_empty<R>(), nb = st_empty<R>();
-  const int qom = (n_o + kThreads - 1) / kThreads;
+  const int qom = (n_o + NT - 1) / NT;
   const int ol = max(n_o - 1, 0);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -726,8 +738,10 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
     // forward: the W points before z (entry of the owner of W point z-1
     // and its local prefix); backward: the W points from z on
     const int i1 = max(z - 1, 0), i2 = min(z, wlast);
-    const St<R> Fo = st_comb(hslot_get(sm, 0, sm.own[i1]), St<R>{sm.pfM[i1], sm.pfs[i1]});
-    const St<R> Bo = st_comb(hslot_get(sm, 1, sm.own[i2]), St<R>{sm.sfM[i2], sm.sfs[i2]});
+    // (a tile without W points leaves own[] stale or unset; Fo / Bo are not
+    // used then, and the mask keeps the slot index inside the slot arrays)
+    const St<R> Fo = st_comb(hslot_get(sm, 0, sm.own[i1] & (NT - 1)), St<R>{sm.pfM[i1], sm.pfs[i1]});
+    const St<R> Bo = st_comb(hslot_get(sm, 1, sm.own[i2] & (NT - 1)), St<R>{sm.sfM[i2], sm.sfs[i2]});
     const St<R> F = z > 0 ? Fo : cf;
     const St<R> B = z < n_w ? Bo : cb;
     {
@@ -818,7 +832,7 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, E>& 
     if (tid == 0) {
       double tot = 0.0;
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) tot += sm.red[w];
+      for (int w = 0; w < NT / 32; ++w) tot += sm.red[w];
       a.part[slot] = tot;
     }
   }
@@ -842,17 +856,18 @@ __device__ __forceinline__ void half_stage(const HalfArgs<R>& a, R* buf, int c0,
   constexpr int kS2 = 2 * HT<R>::kSt;
   const R* src = a.agg_out + kS2 * (int64_t)c0;
   const int nv = kS2 * nq;
+  constexpr int NT = half_threads<R, E>();
 #pragma unroll 1
-  for (int r0 = threadIdx.x; r0 < nv; r0 += 8 * kThreads) {
+  for (int r0 = threadIdx.x; r0 < nv; r0 += 8 * NT) {
     R v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int i = r0 + k * kThreads;
+      const int i = r0 + k * NT;
       v[k] = i < nv ? __ldcg(src + i) : R(0);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int i = r0 + k * kThreads;
+      const int i = r0 + k * NT;
       if (i < nv) buf[i] = v[k];
     }
   }
@@ -863,7 +878,7 @@ __device__ __forceinline__ void half_carry_chunk(const HalfArgs<R>& a, HalfSmem<
                                                  int nq, St<R>& run) {
   using H = HT<R>;
   constexpr int kS = H::kSt;
-  constexpr int kQ = E;
+  constexpr int kQ = half_e<E>();
   const int tid = threadIdx.x;
   const int j0 = tid * kQ;
   St<R> f = st_empty<R>();
@@ -895,6 +910,53 @@ __device__ __forceinline__ void half_carry_chunk(const HalfArgs<R>& a, HalfSmem<
   run = {sm.totM, sm.tots};
 }
 
+// Both directions of one chunk that holds every tile (no running state
+// enters it): each thread forms the forward and backward log-sums of its kQ
+// tiles, warps 0 and 1 scan the two directions at the same time (as a
+// tile's W phase does), and each thread writes its tiles' carries.
+template <class R, int E>
+__device__ __forceinline__ void half_carry_chunk2(const HalfArgs<R>& a, HalfSmem<R, E>& sm, const R* buf, int nq) {
+  using H = HT<R>;
+  constexpr int kS = H::kSt;
+  constexpr int kQ = half_e<E>();
+  const int tid = threadIdx.x;
+  const int j0 = tid * kQ;
+  St<R> f = st_empty<R>(), b = st_empty<R>();
+#pragma unroll 1
+  for (int k = 0; k < kQ; ++k) {
+    const int j = j0 + k;
+    if (j < nq) {
+      St<R> u, w;
+      H::get_s(buf + 2 * kS * j, u.M, u.s);
+      H::get_s(buf + 2 * kS * j + kS, w.M, w.s);
+      f = st_comb(f, u);
+      b = st_comb(b, w);
+    }
+  }
+  hslot_put(sm, 0, tid, f);
+  hslot_put(sm, 1, tid, b);
+  __syncthreads();
+  if (tid < 64) hrake_scan(sm, st_empty<R>(), st_empty<R>());
+  __syncthreads();
+  St<R> sf = hslot_get(sm, 0, tid), sb = hslot_get(sm, 1, tid);
+#pragma unroll 1
+  for (int kk = 0; kk < kQ; ++kk) {
+    const int jf = j0 + kk, jb = j0 + kQ - 1 - kk;
+    if (jf < nq) {
+      H::put(a.carry_out + 2 * kS * (int64_t)jf, sf.M, sf.s);
+      St<R> u;
+      H::get_s(buf + 2 * kS * jf, u.M, u.s);
+      sf = st_comb(sf, u);
+    }
+    if (jb < nq) {
+      H::put(a.carry_out + 2 * kS * (int64_t)jb + kS, sb.M, sb.s);
+      St<R> w;
+      H::get_s(buf + 2 * kS * jb + kS, w.M, w.s);
+      sb = st_comb(sb, w);
+    }
+  }
+}
+
 // Last CTA, line mode: each thread scans the tiles of whole lines (a line
 // spans a few tiles); a line starts and ends empty.
 template <class R>
@@ -903,7 +965,7 @@ __device__ void half_carries_lines(const HalfArgs<R>& a) {
   constexpr int kS = H::kSt;
   const int C = a.C;
 #pragma unroll 1
-  for (int l = threadIdx.x; l < a.lines; l += kThreads) {
+  for (int l = threadIdx.x; l < a.lines; l += blockDim.x) {
     const int64_t u0 = (int64_t)l * C;
     St<R> st = st_empty<R>();
 #pragma unroll 1
@@ -926,7 +988,7 @@ __device__ void half_carries_lines(const HalfArgs<R>& a) {
 
 template <class R, int E>
 __device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
-  constexpr int K = E * kThreads;   // tiles per chunk
+  constexpr int K = half_e<E>() * half_threads<R, E>();   // tiles per chunk
   static_assert(sizeof(sm.pfM) + sizeof(sm.pfs) + sizeof(sm.sfM) + sizeof(sm.sfs) >=
                     sizeof(R) * 2 * HT<R>::kSt * K, "staging");
   R* buf = reinterpret_cast<R*>(sm.pfM);   // pfM, pfs, sfM, sfs are adjacent
@@ -955,6 +1017,13 @@ __device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
     return;
   }
   const int nch = (C + K - 1) / K;
+  if (nch == 1) {
+    __syncthreads();
+    half_stage<R, E>(a, buf, 0, C);
+    __syncthreads();
+    half_carry_chunk2<R, E>(a, sm, buf, C);
+    return;
+  }
   St<R> runF = st_empty<R>(), runB = st_empty<R>();
 #pragma unroll 1
   for (int ch = 0; ch < nch; ++ch) {
@@ -963,17 +1032,14 @@ __device__ void half_carries(const HalfArgs<R>& a, HalfSmem<R, E>& sm) {
     half_stage<R, E>(a, buf, c0, nq);
     __syncthreads();
     half_carry_chunk<R, E, 0>(a, sm, buf, c0, nq, runF);
-    if (nch == 1) half_carry_chunk<R, E, 1>(a, sm, buf, c0, nq, runB);
   }
-  if (nch > 1) {
 #pragma unroll 1
-    for (int ch = nch - 1; ch >= 0; --ch) {
-      const int c0 = ch * K, nq = min(K, C - c0);
-      __syncthreads();
-      half_stage<R, E>(a, buf, c0, nq);
-      __syncthreads();
-      half_carry_chunk<R, E, 1>(a, sm, buf, c0, nq, runB);
-    }
+  for (int ch = nch - 1; ch >= 0; --ch) {
+    const int c0 = ch * K, nq = min(K, C - c0);
+    __syncthreads();
+    half_stage<R, E>(a, buf, c0, nq);
+    __syncthreads();
+    half_carry_chunk<R, E, 1>(a, sm, buf, c0, nq, runB);
   }
 }
 
@@ -985,7 +1051,7 @@ __device__ void half_finish(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int units)
   double ep = 0.0;
   if (kFlags & H_ERR) {
 #pragma unroll 4
-    for (int i = tid; i < units; i += kThreads) ep += __ldcg(a.part + i);
+    for (int i = tid; i < units; i += (int)blockDim.x) ep += __ldcg(a.part + i);
   }
   if (kFlags & (H_NEXT | H_AGG)) {
     if (kFlags & H_LINES) half_carries_lines<R>(a);
@@ -998,7 +1064,7 @@ __device__ void half_finish(const HalfArgs<R>& a, HalfSmem<R, E>& sm, int units)
     if ((tid & 31) == 0) sm.red[tid >> 5] = ep;
     __syncthreads();
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) errsum += sm.red[w];
+    for (int w = 0; w < half_threads<R, E>() / 32; ++w) errsum += sm.red[w];
   }
   if (tid == 0) {
     int32_t* c = a.ctrl;
@@ -1040,13 +1106,13 @@ __device__ __forceinline__ bool half_last_cta(int32_t* ticket, int G, HalfSmem<R
 #endif
 template <class R, int E>
 constexpr int half_min_blocks() {
-  return sizeof(R) != 4 ? 1 : (E >= 8 ? FINOM_HALF_MINB8 : (E == 4 ? 3 : 4));
+  return sizeof(R) != 4 ? 1 : (E >= 8 ? FINOM_HALF_MINB8 : (E == 4 ? 3 : (E == kElemsSmall ? 8 : 4)));
 }
 
 // Persistent CTAs: CTA b handles the tiles b, b + G, b + 2G, ... (G = grid
 // size); the last CTA to finish (ticket ctrl[0]) runs half_finish.
 template <class R, int kFlags, int E>
-__global__ void __launch_bounds__(kThreads, half_min_blocks<R, E>()) k_half(HalfArgs<R> a) {
+__global__ void __launch_bounds__(half_threads<R, E>(), half_min_blocks<R, E>()) k_half(HalfArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HalfSmem<R, E>& sm = *reinterpret_cast<HalfSmem<R, E>*>(smem_raw);
   if constexpr ((kFlags & H_BATCH) != 0) {

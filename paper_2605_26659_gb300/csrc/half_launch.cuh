@@ -21,7 +21,9 @@ unsigned half_grid(int64_t units, size_t smem) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_half<R, M, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half<R, M, E>, kThreads, smem) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half<R, M, E>, half_threads<R, E>(), smem) !=
+        cudaSuccess)
+      n = 1;
     per_sm = n < 1 ? 1 : n;
   }
   return (unsigned)std::min<int64_t>(units, (int64_t)per_sm * sms);
@@ -34,7 +36,7 @@ cudaError_t half_launch_me(const HalfArgs<R>& a, cudaStream_t s) {
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(half_threads<R, E>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
@@ -80,7 +82,8 @@ cudaError_t half_launch_e(const HalfArgs<R>& a, int mode, cudaStream_t s, bool* 
   }
 }
 
-// Launch one mode with elems points per thread (1, 2, 4 or 8).
+// Launch one mode with tiles of kind elems (1, 2, 4 or 8 points per thread of
+// 256 threads, or kElemsSmall: 64 threads of one point).
 template <class R>
 finom_status half_launch(const HalfArgs<R>& a, int mode, int elems, cudaStream_t s) {
   bool known = false;
@@ -90,6 +93,7 @@ finom_status half_launch(const HalfArgs<R>& a, int mode, int elems, cudaStream_t
     case 2: e = half_launch_e<R, 2>(a, mode, s, &known); break;
     case 4: e = half_launch_e<R, 4>(a, mode, s, &known); break;
     case 8: e = half_launch_e<R, 8>(a, mode, s, &known); break;
+    case kElemsSmall: e = half_launch_e<R, kElemsSmall>(a, mode, s, &known); break;
     default: break;
   }
   if (!known) {

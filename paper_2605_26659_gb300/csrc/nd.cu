@@ -715,8 +715,11 @@ finom_status plan_nd_build(finom_plan_s* p, int d, const int64_t* n, const doubl
     finom_status rc = build_plan(ax, xs[k], ys[k], s);
     // the smallest tile that holds a whole line (lines give the parallelism;
     // a line in one tile needs no carries and no aggregate launch)
-    int e = 1;
-    while (e < kElems && (int64_t)e * kThreads < 2 * n[k]) e *= 2;
+    int e = kElemsSmall;
+    if (tile_points(e) < 2 * n[k]) {
+      e = 1;
+      while (e < kElems && tile_points(e) < 2 * n[k]) e *= 2;
+    }
     if (rc == FINOM_OK) rc = build_tiles_e(ax, e, s);
     if (rc != FINOM_OK) return rc;
     // the axis minimum over both meshes (the sorted copies' first entries)

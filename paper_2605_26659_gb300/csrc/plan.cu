@@ -195,8 +195,9 @@ finom_status build_plan(finom_plan_s* p, const double* x, const double* y, cudaS
 }
 
 finom_status build_tiles_e(finom_plan_s* p, int elems, cudaStream_t s) {
-  if (elems != 1 && elems != 2 && elems != 4 && elems != kElems) {
-    set_error("points per thread must be 1, 2, 4 or " + std::to_string(kElems));
+  if (!tile_kind_ok(elems)) {
+    set_error("tile kind must be 1, 2, 4 or " + std::to_string(kElems) + " points per thread, or " +
+              std::to_string(kElemsSmall) + " (64-point tiles)");
     return FINOM_EINVAL;
   }
   if (elems == p->elems) return FINOM_OK;
@@ -205,7 +206,7 @@ finom_status build_tiles_e(finom_plan_s* p, int elems, cudaStream_t s) {
   p->Ce = p->C;
   p->elems = kElems;
   if (elems == kElems) return FINOM_OK;
-  const int64_t tile = (int64_t)elems * kThreads;
+  const int64_t tile = tile_points(elems);
   const int64_t Ce = (p->L + tile - 1) / tile;
   int32_t* t0 = nullptr;
   FINOM_CUDA(cudaMalloc(&t0, sizeof(int32_t) * (Ce + 1)));

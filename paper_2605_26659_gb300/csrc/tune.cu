@@ -1,11 +1,12 @@
 // Tile-size tuning of 1D plans: points per thread of the fused half-step
 // kernel by size bucket and precision, and the autotuner that measures it.
 //
-// The kernel's tile is kThreads threads x E points.  Large problems want the
-// full tile (E = kElems: fewer tiles, fewer carries, longer per-thread runs);
-// small ones want more, smaller tiles, so that a problem of a few thousand
-// points spreads over more SMs (float64 arithmetic on one SM is slow) and
-// each tile's serial chains are shorter.  The table maps the bucket
+// The kernel's tile is kThreads threads x E points, or for E = kElemsSmall
+// 64 threads x 1 point.  Large problems want the full tile (E = kElems:
+// fewer tiles, fewer carries, longer per-thread runs); small ones want more,
+// smaller tiles, so that a problem of a few thousand points spreads over
+// more SMs (float64 arithmetic on one SM is slow) and each tile's serial
+// chains are shorter.  The table maps the bucket
 // ceil(log2(N + M)) to E; finom_plan reads it.  finom_autotune times a few
 // Sinkhorn iterations of a synthetic problem of the bucket's size for every
 // E and installs the fastest; finom_tune_set / finom_tune_get let a caller
@@ -26,18 +27,24 @@ constexpr int kBuckets = 40;
 std::mutex g_tune_mu;
 
 // Defaults from a tuning run on GB300 (finom_autotune, 64 iterations per
-// candidate, buckets 2^10 .. 2^22): float64 up to 2^15 merged points takes
-// E = 1 (127-165 us per iteration against 279-337 us with E = 8), 2^16 E = 2,
-// 2^17 E = 4, larger E = 8; float32 up to 2^13 takes E = 1 (12-14 us against
-// 20-23 us), 2^14-2^15 E = 2, 2^16-2^17 E = 4, 2^18 E = 8, 2^19 E = 4, from
-// 2^20 on E = 8.
+// candidate, buckets 2^10 .. 2^22; E = -1 is the 64-point tile).  float64:
+// 2^10-2^12 take E = -1 (52-74 us per iteration against 93-97 with E = 1 and
+// 117-209 with E = 8), 2^13 E = 1, 2^14 E = 2, 2^15 E = 4, 2^16 E = 2, 2^17-2^18
+// E = 4, from 2^19 on E = 8.  float32: 2^10-2^11 E = -1 (9.7-10.3 us against
+// 11.0 with E = 1), 2^12-2^13 E = 1, 2^14 E = 2, 2^15 E = 4, 2^16 E = 1, 2^17
+// E = 2, 2^18-2^20 E = 4, from 2^21 on E = 8.  Smaller buckets take E = -1,
+// larger ones E = 8.
 struct Table {
   int e[2][kBuckets];
   int batch[2] = {kElems, kElems};   // batch plans (finom_tune_set_batch)
   Table() {
+    //                           2^10 .. 2^22
+    const int f64[13] = {kElemsSmall, kElemsSmall, kElemsSmall, 1, 2, 4, 2, 4, 4, 8, 8, 8, 8};
+    const int f32[13] = {kElemsSmall, kElemsSmall, 1, 1, 2, 4, 1, 2, 4, 4, 4, 8, 8};
     for (int b = 0; b < kBuckets; ++b) {
-      e[FINOM_F64][b] = b <= 15 ? 1 : (b == 16 ? 2 : (b == 17 ? 4 : kElems));
-      e[FINOM_F32_LOG][b] = b <= 13 ? 1 : (b <= 15 ? 2 : (b <= 17 || b == 19 ? 4 : kElems));
+      const int k = b < 10 ? 0 : (b > 22 ? 12 : b - 10);
+      e[FINOM_F64][b] = b < 10 ? kElemsSmall : (b > 22 ? kElems : f64[k]);
+      e[FINOM_F32_LOG][b] = b < 10 ? kElemsSmall : (b > 22 ? kElems : f32[k]);
     }
   }
 };
@@ -49,7 +56,7 @@ int bucket_of(int64_t L) {
   return b;
 }
 
-bool valid_elems(int e) { return e == 1 || e == 2 || e == 4 || e == kElems; }
+bool valid_elems(int e) { return tile_kind_ok(e); }
 
 }  // namespace
 
@@ -69,7 +76,7 @@ extern "C" {
 
 finom_status finom_tune_set_batch(finom_precision prec, int32_t elems) {
   if ((prec != FINOM_F64 && prec != FINOM_F32_LOG) || !finom::valid_elems(elems)) {
-    finom::set_error("finom_tune_set_batch: need a known precision and elems in {1, 2, 4, 8}");
+    finom::set_error("finom_tune_set_batch: need a known precision and elems in {-1, 1, 2, 4, 8}");
     return FINOM_EINVAL;
   }
   std::lock_guard<std::mutex> lk(finom::g_tune_mu);
@@ -90,7 +97,7 @@ finom_status finom_tune_get_batch(finom_precision prec, int32_t* elems) {
 finom_status finom_tune_set(finom_precision prec, int32_t log2_bucket, int32_t elems) {
   if ((prec != FINOM_F64 && prec != FINOM_F32_LOG) || log2_bucket < 0 || log2_bucket >= finom::kBuckets ||
       !finom::valid_elems(elems)) {
-    finom::set_error("finom_tune_set: need a known precision, 0 <= log2_bucket < 40, elems in {1, 2, 4, 8}");
+    finom::set_error("finom_tune_set: need a known precision, 0 <= log2_bucket < 40, elems in {-1, 1, 2, 4, 8}");
     return FINOM_EINVAL;
   }
   std::lock_guard<std::mutex> lk(finom::g_tune_mu);
@@ -133,15 +140,15 @@ finom_status finom_autotune(finom_precision prec, int32_t log2_bucket, int32_t i
   finom_plan_t p = nullptr;
   finom_status rc = FINOM_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const int cand[4] = {1, 2, 4, finom::kElems};
-  double t[4] = {0, 0, 0, 0};
+  const int cand[5] = {finom::kElemsSmall, 1, 2, 4, finom::kElems};
+  double t[5] = {0, 0, 0, 0, 0};
   if (cudaMemcpyAsync(d, h.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     rc = finom::cuda_fail(cudaGetLastError(), "finom_autotune setup");
   }
   if (rc == FINOM_OK) rc = finom_plan(d, n, d + n, n, 1e-2, prec, stream, &p);
   const int warm = std::min(16, iters);
-  for (int k = 0; k < 4 && rc == FINOM_OK; ++k) {
+  for (int k = 0; k < 5 && rc == FINOM_OK; ++k) {
     rc = finom_plan_set_elems(p, cand[k], stream);
     if (rc == FINOM_OK) rc = finom_solve_begin(p, d + 2 * n, d + 3 * n, 0.0, 1 + warm + iters, nullptr, nullptr,
                                                stream);
@@ -162,11 +169,11 @@ finom_status finom_autotune(finom_precision prec, int32_t log2_bucket, int32_t i
   cudaFree(d);
   if (rc != FINOM_OK) return rc;
   int bi = 0;
-  for (int k = 1; k < 4; ++k)
+  for (int k = 1; k < 5; ++k)
     if (t[k] < t[bi]) bi = k;
   *best = cand[bi];
   if (us_per_iter)
-    for (int k = 0; k < 4; ++k) us_per_iter[k] = t[k];
+    for (int k = 0; k < 5; ++k) us_per_iter[k] = t[k];
   return finom_tune_set(prec, log2_bucket, cand[bi]);
 }
 

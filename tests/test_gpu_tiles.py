@@ -1,6 +1,7 @@
-"""The fused half-step kernel with every tile size (points per thread E in
-{1, 2, 4, 8}) on 1D plans: products and solves against the CPU oracle, the
-tile counts, agreement across E, and the autotuner.
+"""The half-step kernel with every tile kind (points per thread E in
+{1, 2, 4, 8} on 256 threads, and E = -1: 64-point tiles on 64 threads) on 1D
+plans: products and solves against the CPU oracle, the tile counts,
+agreement across kinds, and the autotuner.
 
 Small problems run with small tiles by default (the tuning table), so the
 other GPU tests cover E < 8 too; here every E runs on the same inputs, with
@@ -16,7 +17,8 @@ from tests.gpu_util import H, T, meshes, relerr
 
 pytestmark = pytest.mark.gpu
 
-ELEMS = [1, 2, 4, 8]
+ELEMS = [-1, 1, 2, 4, 8]
+POINTS = {-1: 64, 1: 256, 2: 512, 4: 1024, 8: 2048}   # merged points per tile
 TOL = {"f64": 1e-12, "f32_log": 1e-5}
 
 
@@ -30,7 +32,7 @@ def test_products_every_tile_size(lib, prec, E, N, M, kind):
     p = lib.finom_plan(T(x), T(y), eps, prec)
     lib.finom_plan_set_elems(p, E)
     e, tiles = lib.finom_plan_elems(p)
-    assert e == E and tiles == math.ceil((N + M) / (256 * E))
+    assert e == E and tiles == math.ceil((N + M) / POINTS[E])
     g = np.random.default_rng(N + M)
     v = g.uniform(0, 1, M)
     v[g.random(M) < 0.05] = 0.0
@@ -115,11 +117,11 @@ def test_autotune_installs_the_fastest(lib):
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
 def test_launch_tail_paths_agree(lib, prec):
-    """The last CTA of a launch scans the tile maps with one warp per direction
-    (up to 128 tiles), four warps per direction (up to 1025 float32 / 683
-    float64 tiles) or the whole block: N + M = 200,000 points give 98 tiles
-    with E = 8, 196 with E = 4, 391 with E = 2 and 782 with E = 1, so every
-    path runs on the same problem; a 30-iteration solve must agree."""
+    """The last CTA of a launch scans the tile aggregates into carries in
+    chunks of E x (threads) tiles: N + M = 200,000 points give 98 tiles with
+    E = 8 (one chunk), 196 with E = 4, 391 with E = 2, 782 with E = 1 and
+    3125 64-point tiles (49 chunks), so one and several chunks run on the same
+    problem; a 30-iteration solve must agree across them."""
     x, y = meshes("uniform_random", 110000, 90000, 8)
     g = np.random.default_rng(3)
     u, v = g.uniform(0.1, 1, 110000), g.uniform(0.1, 1, 90000)
@@ -127,12 +129,12 @@ def test_launch_tail_paths_agree(lib, prec):
     for E in ELEMS:
         p = lib.finom_plan(T(x), T(y), 0.002, prec)
         lib.finom_plan_set_elems(p, E)
-        assert lib.finom_plan_elems(p)[1] == math.ceil(200000 / (256 * E))
+        assert lib.finom_plan_elems(p)[1] == math.ceil(200000 / POINTS[E])
         f, gg, res = lib.finom_solve(p, T(u), T(v), 0.0, 30)
         outs[E] = (H(f), H(gg), res)
     ref = outs[8]
     lock = 1e-12 if prec == "f64" else 3e-5
-    for E in (1, 2, 4):
+    for E in (-1, 1, 2, 4):
         f, gg, res = outs[E]
         assert np.max(np.abs(f - ref[0])) / 0.002 <= lock and np.max(np.abs(gg - ref[1])) / 0.002 <= lock
         assert res["marginal_err"] == pytest.approx(ref[2]["marginal_err"], rel=1e-9 if prec == "f64" else 1e-3)
