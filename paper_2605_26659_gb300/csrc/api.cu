@@ -157,6 +157,7 @@ HalfArgs<R> half_args(finom_plan_s* p, bool o_is_x, int q) {
     a.o_is_x = 0;
     a.bO = (const Beta*)st.py[q];
     a.lmO = (const Lv*)st.qwm;
+    a.mO = st.nu64;
     a.bO_out = (Beta*)st.py[1 - q];
     a.bW = (const Beta*)st.px[q];
   } else {         // phi <- mu / (K psi): outputs on x, weights on y

@@ -422,6 +422,7 @@ HalfArgs<R> batch_args(finom_plan_s* p, bool o_is_x, int q) {
     a.bO_out = (Beta*)st.py[1 - q];
     a.bW = (const Beta*)st.px[q];
     a.lmO = (const Lv*)st.qwm;
+    a.mO = st.nu64;
   } else {         // phi <- u / (K psi)
     a.bO = (const Beta*)st.px[q];
     a.bO_out = (Beta*)st.px[1 - q];

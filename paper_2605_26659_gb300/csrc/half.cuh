@@ -353,6 +353,7 @@ struct HalfArgs {
   int o_is_x;              // 1: outputs at x (K psi), 0: outputs at y (K^T phi)
   const Beta* bO;          // O levels (frames)
   const typename HT<R>::Lv* lmO;   // O log2 masses (none for a zero mass); H_POT / H_ERR
+  const double* mO;                // H_ERR, float64 kernels: the O masses (may be null)
   Beta* bO_out;            // new O levels (H_POT)
   const Beta* bW;          // W levels
   double* out;             // H_LOG / H_LIN: per O point
@@ -546,13 +547,33 @@ __device__ __forceinline__ void hrake_one(HalfSmem<R, E>& sm, const St<R>& seed)
   }
 }
 
-// S - 1 for S = 2^x without the cancellation near x = 0 (branch-free)
+// S - 1 for S = 2^x without the cancellation near x = 0: the series of
+// e^t - 1, t = x ln 2, for |t| < 0.03 (float32: degree 4, branch-free;
+// float64: degree 9, which leaves a relative error below 1e-17, and a
+// branch, since near the fixed point every point takes the series and the
+// float64 exp2 is skipped), else 2^x - 1
 template <class R>
 __device__ __forceinline__ R pow2m1(R x) {
   const R t = x * R(0.69314718055994530942);
-  const R p = t * (R(1) + t * (R(0.5) + t * (R(1.0 / 6) + t * R(1.0 / 24))));
-  const R q = HT<R>::ex2(x) - R(1);
-  return (fabs(t) < R(0.03)) ? p : q;
+  if constexpr (sizeof(R) == sizeof(double)) {
+    if (fabs(t) < 0.03) {
+      double p = 2.7557319223985890653e-06;   // 1/9!
+      p = fma(p, t, 2.4801587301587301587e-05);
+      p = fma(p, t, 1.9841269841269841270e-04);
+      p = fma(p, t, 1.3888888888888888889e-03);
+      p = fma(p, t, 8.3333333333333333333e-03);
+      p = fma(p, t, 4.1666666666666666667e-02);
+      p = fma(p, t, 1.6666666666666666667e-01);
+      p = fma(p, t, 0.5);
+      p = fma(p, t, 1.0);
+      return p * t;
+    }
+    return HT<R>::ex2(x) - 1.0;
+  } else {
+    const R p = t * (R(1) + t * (R(0.5) + t * (R(1.0 / 6) + t * R(1.0 / 24))));
+    const R q = HT<R>::ex2(x) - R(1);
+    return (fabs(t) < R(0.03)) ? p : q;
+  }
 }
 
 // One tile of a launch: steps 1-3 of the header comment.  Returns false when
@@ -801,7 +822,14 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, EK>&
         const R mb = g1 ? m1 : m2, mo = g1 ? m2 : m1;
         const R delta = big + H::lg2_acc(fma(mo, ed, mb));
         if constexpr ((kFlags & H_ERR) != 0) {
-          const R term = has_mass ? H::ex2(H::hi(lm)) * fabs(pow2m1(delta)) : H::ex2(delta);
+          // the mass mu_k: 2^{log2 mu} (float32), or the float64 mass itself
+          // where the plan passes it (a float64 exp2 saved per point)
+          R mu;
+          if constexpr (sizeof(R) == sizeof(double))
+            mu = a.mO ? a.mO[kLines ? gi : o_start + j] : H::ex2(H::hi(lm));
+          else
+            mu = H::ex2(H::hi(lm));
+          const R term = has_mass ? mu * fabs(pow2m1(delta)) : H::ex2(delta);
           err += v ? term : R(0);
         }
         if constexpr ((kFlags & H_POT) != 0) {

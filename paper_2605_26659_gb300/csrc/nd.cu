@@ -289,6 +289,7 @@ finom_status nd_pass(finom_plan_s* p, int k, int o_is_x, const LvT<R>* gW, int m
   a.gO = gO;
   a.gO_out = gO_out;
   a.lmO = lmO;
+  a.mO = (lmO && !o_is_x) ? p->st.nu64 : nullptr;   // nu's masses (layout L_0) for the error term
   a.q_out = q_out;
   a.out = out;
   a.grid = p->nd_G;
