@@ -214,6 +214,27 @@ def test_batch_every_tile_size(lib, prec):
                                                            abs=1e-12 if prec == "f64" else 2e-6)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("E", [-1, 8])
+def test_batch_large_gaps(lib, prec, E):
+    """Instances whose merged gaps are tens of bits (disjoint supports and a
+    few far-apart nodes at eps = 0.004, next to ordinary ones): every
+    instance in lock-step with the oracle, as alone."""
+    shapes = [(300, 250, "disjoint", 0.004), (40, 3, "disjoint", 0.004), (500, 400, "uniform_random", 0.004),
+              (7, 9, "uniform_random", 0.004), (1200, 900, "disjoint", 0.01)]
+    xs, ys, us, vs, eps, offx, offy = _batch(shapes, 190)
+    p = lib.finom_plan_batch(T(np.concatenate(xs)), offx, T(np.concatenate(ys)), offy, eps, prec, elems=E)
+    f, g, res = lib.finom_solve_batch(p, T(np.concatenate(us)), T(np.concatenate(vs)), 0.0, 10)
+    f, g = H(f), H(g)
+    for b, (N, M, kind, e) in enumerate(shapes):
+        fo, go, it, err = serial_c.sinkhorn(xs[b], ys[b], us[b], vs[b], e, 0.0, 10)
+        u, v = us[b], vs[b]
+        fb, gb = _split(f, offx, b), _split(g, offy, b)
+        assert res[b]["iters"] == it == 10
+        assert np.max(np.abs(fb[u > 0] - fo[u > 0])) / e <= LOCK_TOL[prec], b
+        assert np.max(np.abs(gb[v > 0] - go[v > 0])) / e <= LOCK_TOL[prec], b
+
+
 def test_batch_autotune_sets_the_batch_entry(lib):
     from paper_2605_26659_gb300 import autotune
     xs, ys, us, vs, eps, offx, offy = _batch(SHAPES[:5], 170, zeros=False)
