@@ -16,6 +16,13 @@ from tests.gpu_util import H, T, meshes
 pytestmark = pytest.mark.gpu
 
 LOCK_TOL = {"f64": 1e-10, "f32_log": 2e-5}   # |f_gpu - f_oracle| / eps on points with mass
+# float32 iterates against the oracle (or another tiling) at the same iteration:
+# |err - err_ref| <= F32_ERR_REL err_ref + F32_ERR_ABS for the float64 marginal errors
+# (F32_ERR_ONE in place of F32_ERR_ABS where a side has a few points, or the
+# supports are disjoint: each weight carries the float32 rounding of its sum,
+# ~1e-6 relative, and with few terms, or with the rank-one kernel of disjoint
+# supports where every point shares one sum, nothing averages it out)
+F32_ERR_REL, F32_ERR_ABS, F32_ERR_ONE = 2e-4, 2e-7, 1e-6
 
 # (N, M, kind, eps): tiny, single points, ragged tiles, multi-tile, ties, disjoint supports
 SHAPES = [(3, 5, "uniform_random", 0.05), (300, 257, "uniform_random", 0.01), (2047, 1, "uniform_random", 0.05),
@@ -72,8 +79,11 @@ def test_batch_lockstep_with_oracle(lib, prec, maxit):
         assert np.max(np.abs(fb[u > 0] - fo[u > 0])) / e <= LOCK_TOL[prec], b
         assert np.max(np.abs(gb[v > 0] - go[v > 0])) / e <= LOCK_TOL[prec], b
         assert np.all(np.isneginf(fb[u == 0])) and np.all(np.isneginf(gb[v == 0]))
-        assert res[b]["marginal_err"] == pytest.approx(err, rel=1e-6 if prec == "f64" else 1e-3,
-                                                       abs=1e-9 if prec == "f64" else 2e-6)
+        if prec == "f64":
+            assert res[b]["marginal_err"] == pytest.approx(err, rel=1e-6, abs=1e-9)
+        else:
+            f32_abs = F32_ERR_ONE if min(N, M) <= 8 or kind == "disjoint" else F32_ERR_ABS
+            assert abs(res[b]["marginal_err"] - err) <= F32_ERR_REL * err + f32_abs, b
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32_log", 1e-6)])
@@ -208,10 +218,12 @@ def test_batch_every_tile_size(lib, prec):
             fb = _split(f, offx, b)
             assert res[b]["iters"] == 7
             assert np.max(np.abs(fb[u > 0] - fo[u > 0])) / e <= LOCK_TOL[prec], (b, E)
-            # (float32: errors near the float32 floor differ by a few 1e-7 across tilings)
-            assert res[b]["marginal_err"] == pytest.approx(outs[8][2][b]["marginal_err"],
-                                                           rel=1e-9 if prec == "f64" else 1e-3,
-                                                           abs=1e-12 if prec == "f64" else 2e-6)
+            ref = outs[8][2][b]["marginal_err"]
+            if prec == "f64":
+                assert res[b]["marginal_err"] == pytest.approx(ref, rel=1e-9, abs=1e-12)
+            else:
+                f32_abs = F32_ERR_ONE if min(N, M) <= 8 or kind == "disjoint" else F32_ERR_ABS
+                assert abs(res[b]["marginal_err"] - ref) <= F32_ERR_REL * ref + f32_abs, (b, E)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])

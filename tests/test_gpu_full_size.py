@@ -57,9 +57,9 @@ def test_config1_full(lib, prec):
         assert res["marginal_err"] == pytest.approx(gold["marginal_err"], rel=1e-6)
     else:
         assert res["w1"] == pytest.approx(gold["w1"], rel=1e-4)
-        # the float32 iterate after 2000 iterations: its float64 error within
-        # 1 % of the oracle's at the same iteration
-        assert res["marginal_err"] == pytest.approx(gold["marginal_err"], rel=1e-2)
+        # the float32 iterate after 2000 iterations: its float64 error next to
+        # the oracle's at the same iteration (2e-4 relative + 2e-7)
+        assert abs(res["marginal_err"] - gold["marginal_err"]) <= 2e-4 * gold["marginal_err"] + 2e-7
 
 
 def test_config2_full(lib):

@@ -137,4 +137,7 @@ def test_launch_tail_paths_agree(lib, prec):
     for E in (-1, 1, 2, 4):
         f, gg, res = outs[E]
         assert np.max(np.abs(f - ref[0])) / 0.002 <= lock and np.max(np.abs(gg - ref[1])) / 0.002 <= lock
-        assert res["marginal_err"] == pytest.approx(ref[2]["marginal_err"], rel=1e-9 if prec == "f64" else 1e-3)
+        if prec == "f64":
+            assert res["marginal_err"] == pytest.approx(ref[2]["marginal_err"], rel=1e-9)
+        else:
+            assert abs(res["marginal_err"] - ref[2]["marginal_err"]) <= 2e-4 * ref[2]["marginal_err"] + 2e-7
