@@ -8,6 +8,11 @@ divide and marginal-error check, then the K psi half step): 2^21
 point-iterations.  L2 is flushed (256 MB write) before every timed step, and
 each step is timed with CUDA events on the launching stream.
 
+Unless `--no-sub`, the default line also carries bounded sub-results: `serve`
+(the first 100 arrivals of the serving workload), `batch` (the batch workload)
+and `small_fp64` (the 1000-point float64 workload: time per iteration and its
+2000-iteration solve beside the stored oracle solve).
+
 `--workload batch` times batches of independent 1D instances (4096 instances,
 N = M log-uniform in [256, 65536], clustered meshes, eps log-uniform in
 [1e-3, 1e-2]); one step = one iteration of every instance (four launches).
@@ -57,6 +62,7 @@ KERNEL_SOURCES = ["paper_2605_26659_gb300/csrc/half.cuh", "paper_2605_26659_gb30
 # per output point, i.e. 44 N bytes = 22 B per merged point
 ALG_BYTES_PER_POINT = 22.0
 GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "full_config2.json")
+GOLDEN_C1 = os.path.join(ROOT, "tests", "golden", "full_config1.json")
 
 
 def parse():
@@ -436,6 +442,45 @@ def run_finom_2d(args, ws, rank, local):
         }
         print(json.dumps(line), flush=True)
     api.finom_plan_destroy(plan)
+
+
+def run_small(dev, stream):
+    """The 1000-point float64 workload (N = M = 1000, eps = 1e-2, tol 1e-9,
+    2000 iterations): time per iteration of the stepwise loop (CUDA events
+    over 512 iterations after 64), and the blocking solve beside the stored
+    float64 oracle solve of the same problem."""
+    import torch
+    from paper_2605_26659_gb300 import api, inputs
+    pr = inputs.config1()
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    p = api.finom_plan(T(pr.x), T(pr.y), pr.eps, "f64", stream=stream)
+    elems = api.finom_plan_elems(p)[0]
+    api.finom_solve_begin(p, T(pr.u), T(pr.v), 0.0, 1 << 40, stream=stream)
+    api.finom_solve_step(p, 64, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    api.finom_solve_step(p, 512, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us_iter = e0.elapsed_time(e1) * 1e3 / 512
+    u, v = T(pr.u), T(pr.v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f, g, res = api.finom_solve(p, u, v, pr.tol, pr.maxit, stream=stream)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    api.finom_plan_destroy(p)
+    out = {"value": us_iter, "unit": "us/iteration", "dtype": "f64", "tile_kind": elems,
+           "solve": {"seconds": secs, "iters": res["iters"], "w1": res["w1"], "marginal_err": res["marginal_err"]},
+           "config": {"workload": pr.name + f", tol {pr.tol:g}, maxit {pr.maxit}"}}
+    try:
+        gold = json.load(open(GOLDEN_C1))
+        out["solve"]["oracle"] = {"w1": gold["w1"], "iters": gold["iters"], "marginal_err": gold["marginal_err"],
+                                  "w1_relerr": abs(res["w1"] - gold["w1"]) / abs(gold["w1"]),
+                                  "source": "tests/golden/full_config1.json (serial C float64 FINOM oracle)"}
+    except (OSError, KeyError, ValueError):
+        pass
+    return out
 
 
 def _concat_batch(probs):
@@ -824,8 +869,9 @@ def run_finom(args, ws, rank, local):
     # short: served solves/s with p50 / p99 on the first arrivals of the
     # serving process, and the batched form, each beside the plain
     # one-at-a-time FP64 form
-    serve = batch = None
+    serve = batch = small = None
     if not args.no_sub:
+        small = run_small(dev, stream)
         sub = argparse.Namespace(**vars(args))
         sub.requests, sub.plain_count, sub.slots, sub.budget_gb, sub.policy = 100, 4, 64, 64.0, "smallest"
         sub.rates, sub.eps_stages, sub.warmup = "", 0, 3
@@ -858,6 +904,8 @@ def run_finom(args, ws, rank, local):
         if batch is not None:
             line["batch"] = {k: batch[k] for k in ("value", "unit", "ms_per_step", "roofline", "clocks", "e2e",
                                                    "config")}
+        if small is not None:
+            line["small_fp64"] = small
         print(json.dumps(line), flush=True)
     api.finom_plan_destroy(plan)
 
