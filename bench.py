@@ -81,6 +81,8 @@ def parse():
                     help="serve: admission order of queued requests")
     ap.add_argument("--rates", type=str, default="",
                     help="serve: extra arrival rates (req/s, comma-separated) for a latency-vs-load sweep")
+    ap.add_argument("--batch-points", type=int, default=1 << 16,
+                    help="serve: 1D requests with N + M up to this are batched (0: every request alone)")
     ap.add_argument("--eps-stages", type=int, default=0,
                     help="serve: eps-scaling stages of the second run (0: no second run)")
     ap.add_argument("--count", type=int, default=4096, help="batch: instances (default 4096)")
@@ -621,6 +623,7 @@ def _serve_once(api, args, reqs, probs, stages):
     request order, peak active solves)."""
     srv = api.Server(int(args.budget_gb * 2**30), max_active=args.slots, precision="f32_log")
     srv.set_policy(args.policy)
+    srv.set_batching(args.batch_points)
     if stages:
         srv.set_eps_scaling(stages, 0.5, 1e-4)
     t0 = time.perf_counter()
@@ -744,6 +747,7 @@ def run_finom_serve(args, ws, rank, local, emit=True):
                                    f"axes), eps in {{1e-3, 5e-3, 1e-2}}, tol 1e-6, maxit 10000, FP32 "
                                    f"log-domain with float64 verification; one step = one request",
                        "slots": args.slots, "budget_gb": args.budget_gb, "peak_active": peak_active,
+                       "batch_points": args.batch_points,
                        "policy": args.policy,
                        "l2": "inputs and potentials of the active solves exceed L2",
                        "parallelism": f"replicas x{ws}"},

@@ -303,6 +303,19 @@ finom_status finom_solve_batch_end(finom_plan_t plan, double* f, double* g, fino
  *     float32 potentials, on a float64 plan of the same meshes, in later
  *     rounds; then f, g are copied to the host and the slot and its memory
  *     are freed.
+ *   - batching (finom_server_set_batching; on by default for FINOM_F32_LOG
+ *     servers): a 1D request with N + M at most the batching limit is
+ *     admitted together with the queued requests compatible with it (the
+ *     same tol and maxit, eps within a factor 2), as far as the memory
+ *     budget allows (footprint: 240 B per merged point, each request rounded
+ *     up to whole 2048-point tiles, plus 1 MiB per batch).  The batch takes
+ *     one slot and counts as one active solve; it is solved as by
+ *     finom_plan_batch + finom_solve_batch on a host thread of the server
+ *     (its plan building and its blocking solve do not hold up the rounds),
+ *     and its requests finish together when the last of them retires.  A
+ *     batched request's result does not depend on what it was batched with.
+ *     The mesh and mass checks of a batched request are made on the host; a
+ *     bad one finishes with FINOM_EINVAL without joining a batch.
  * Solves on different slots overlap on the GPU.  All calls on one server
  * must come from one host thread at a time; the server uses the device that
  * was current at finom_server_create.
@@ -348,6 +361,14 @@ finom_status finom_server_set_policy(finom_server_t srv, int32_t policy);
 finom_status finom_server_set_eps_scaling(finom_server_t srv, int32_t stages, double factor, double tol_stage);
 
 /*
+ * finom_server_set_batching -- 1D requests admitted from now on with N + M <=
+ * max_points are batched (see above); 0 turns batching off.  Default: 65536
+ * for FINOM_F32_LOG servers, 0 for FINOM_F64 ones.  Requests are not batched
+ * while eps scaling is on.  0 <= max_points <= 2^22, else FINOM_EINVAL.
+ */
+finom_status finom_server_set_batching(finom_server_t srv, int64_t max_points);
+
+/*
  * finom_server_submit_1d -- queue a 1D solve (arguments as finom_plan and
  * finom_solve; x, y, u, v are HOST arrays of N, M, N, M doubles, copied before
  * the call returns).  *id receives the request id.  Sorting and mass checks
@@ -388,13 +409,16 @@ finom_status finom_server_result(finom_server_t srv, int64_t id, finom_server_do
 /*
  * finom_server_cancel -- stop a request: a queued one is dropped, an active
  * one is stopped after its launched work completes (its stream is
- * synchronised) and its memory and slot are freed.  Either then finishes with
- * status FINOM_ECANCELED (collect it with finom_server_result).  A finished
- * request is left as it is.  FINOM_EINVAL for an unknown id.
+ * synchronised) and its memory and slot are freed; a batched one finishes
+ * when its batch ends (a batch whose requests are all cancelled stops after
+ * its current round of launches).  Each then finishes with status
+ * FINOM_ECANCELED (collect it with finom_server_result).  A finished request
+ * is left as it is.  FINOM_EINVAL for an unknown id.
  */
 finom_status finom_server_cancel(finom_server_t srv, int64_t id);
 
-/* Release the server: waits for its active solves and drops every request. */
+/* Release the server: stops its batches, waits for its active solves and
+ * drops every request. */
 finom_status finom_server_destroy(finom_server_t srv);
 
 /* Release the plan and all device memory it owns.  NULL is accepted. */

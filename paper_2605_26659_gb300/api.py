@@ -101,6 +101,7 @@ _SIGS = {
     "finom_server_cancel": ([_P, _I64], ctypes.c_int),
     "finom_server_set_eps_scaling": ([_P, _I32, _D, _D], ctypes.c_int),
     "finom_server_set_policy": ([_P, _I32], ctypes.c_int),
+    "finom_server_set_batching": ([_P, _I64], ctypes.c_int),
     "finom_server_destroy": ([_P], ctypes.c_int),
 }
 
@@ -616,6 +617,10 @@ class Server:
     def set_policy(self, policy):
         """'fifo' (arrival order) or 'smallest' (smallest queued request first)."""
         _check(_lib.finom_server_set_policy(self.handle, {"fifo": 0, "smallest": 1}[policy]))
+
+    def set_batching(self, max_points):
+        """Batch 1D requests with N + M <= max_points (0: off)."""
+        _check(_lib.finom_server_set_batching(self.handle, int(max_points)))
 
     def set_eps_scaling(self, stages, factor=0.5, tol_stage=1e-4):
         _check(_lib.finom_server_set_eps_scaling(self.handle, int(stages), float(factor), float(tol_stage)))

@@ -495,6 +495,8 @@ finom_status build_body_batch(finom_plan_s* p) {
 
 // Launch graph bodies (two iterations each) until every instance retired;
 // the first body starts at parity 1 (iteration 0 was launched before).
+bool stopped(const finom_plan_s* p) { return p->stop && p->stop->load(std::memory_order_relaxed) != 0; }
+
 template <class R>
 finom_status run_loop(finom_plan_s* p, int64_t maxit, cudaStream_t s) {
   SolveState& st = p->st;
@@ -503,7 +505,7 @@ finom_status run_loop(finom_plan_s* p, int64_t maxit, cudaStream_t s) {
     int32_t h[8];
     FINOM_CUDA(cudaMemcpyAsync(h, st.ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
     FINOM_CUDA(cudaStreamSynchronize(s));
-    if (h[1] || launched > maxit + 2) break;
+    if (h[1] || launched > maxit + 2 || stopped(p)) break;
     for (int64_t k = 0; k < bodies; ++k) FINOM_CUDA(cudaGraphLaunch(st.body, s));
     launched += 2 * bodies;
     bodies = std::min<int64_t>(bodies * 2, 64);
@@ -665,7 +667,7 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
     if (rc != FINOM_OK) return rc;
     rc = evaluate<R>(p, tol, maxit, f, g, res, s, err64.data(), &changed);
     if (rc != FINOM_OK) return rc;
-    if (sizeof(R) == sizeof(double) || attempt >= 6) break;
+    if (sizeof(R) == sizeof(double) || attempt >= 6 || stopped(p)) break;
     // float64 verification: an instance whose float32 check passed but whose
     // float64 error is above tol resumes from its stop state (the skipped phi
     // half step of its stop iteration) with a tighter loop tolerance.  Their
@@ -723,7 +725,7 @@ finom_status solve_batch_impl(finom_plan_s* p, const double* u, const double* v,
   }
   st.tol = tol;
   st.active = false;
-  if (sizeof(R) == sizeof(double)) return FINOM_OK;
+  if (sizeof(R) == sizeof(double) || stopped(p)) return FINOM_OK;
   // instances whose float32 state cannot reach tol in float64 (a float32
   // floor above tol: coarse gaps in bits) are finished in float64, warm
   // started from their float32 potentials

@@ -372,12 +372,14 @@ __global__ void __launch_bounds__(kThreads) k_cost(CostArgs a) {
 
 finom_status run_cost(const CostArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(CostSmem);
-  static bool attr = false;
-  if (!attr) {
-    FINOM_CUDA(cudaFuncSetAttribute(k_cost<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FINOM_CUDA(cudaFuncSetAttribute(k_cost<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  // once per process (a function-local static: thread-safe initialisation)
+  static const cudaError_t attr = [smem]() {
+    cudaError_t e = cudaFuncSetAttribute(k_cost<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cost<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+  }();
+  FINOM_CUDA(attr);
   k_cost<true><<<(unsigned)a.C, kThreads, smem, s>>>(a);
   k_cost<false><<<(unsigned)a.C, kThreads, smem, s>>>(a);
   FINOM_CUDA(cudaGetLastError());

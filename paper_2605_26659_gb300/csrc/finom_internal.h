@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -127,6 +128,10 @@ struct finom_plan_s {
   std::vector<int32_t> hitilec;  // per instance: first 2048-point tile of the float64 evaluation
   int32_t* tile_x0c = nullptr;   // the evaluation's tile tables (as tile_x0, 2048-point tiles)
   double* ieps = nullptr;        // per instance
+  // batch solves stop early (between rounds of launches, before the float64
+  // resumes) once *stop is non-zero: the serving loop's cancellation of a
+  // batch whose requests were all cancelled (not owned; null: never)
+  const std::atomic<int>* stop = nullptr;
   // d-dimensional tensor-product plans (nd.cu; finom_plan_nd): grids of
   // nd_n[0] x ... x nd_n[d-1] points, axis 0 fastest; one 1D plan per axis
   // merging mu's nodes (x side) with nu's (y side); per axis the node

@@ -12,11 +12,13 @@
 
 namespace finom {
 
+// Persistent grid of an instantiation: resident CTAs per SM times SMs, found
+// once (a function-local static, so concurrent first launches from several
+// host threads initialise it once).
 template <class R, int M, int E>
 unsigned half_grid(int64_t units, size_t smem) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
+  static const int64_t slots = [smem]() -> int64_t {
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_half<R, M, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -24,9 +26,9 @@ unsigned half_grid(int64_t units, size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_half<R, M, E>, half_threads<R, E>(), smem) !=
         cudaSuccess)
       n = 1;
-    per_sm = n < 1 ? 1 : n;
-  }
-  return (unsigned)std::min<int64_t>(units, (int64_t)per_sm * sms);
+    return (int64_t)(n < 1 ? 1 : n) * (sms < 1 ? 1 : sms);
+  }();
+  return (unsigned)std::min<int64_t>(units, slots);
 }
 
 template <class R, int M, int E>

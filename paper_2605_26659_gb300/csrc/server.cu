@@ -12,6 +12,16 @@
 // the whole solve, and the kernels of all active solves run concurrently on
 // the GPU from their streams; each solve's arithmetic is that of finom_solve,
 // whatever else is running.
+//
+// Small 1D requests (N + M up to the server's batching limit) are admitted
+// together instead: the queued requests compatible with the next one (same
+// tol and maxit, eps within a factor 2) form one batch (finom_plan_batch /
+// finom_solve_batch: one launch per half step for all of them, each retiring
+// at its own stop), which takes one slot and runs on a host thread of its
+// own, so that its plan building, its blocking solve and its plan release
+// never hold up the scheduling rounds.  An instance's arithmetic in a batch
+// does not depend on the other instances, so a batched request's result is
+// the same whatever it was batched with.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,13 +30,16 @@
 #include <chrono>
 #include <cmath>
 #include <deque>
+#include <atomic>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "finom_internal.h"
 
 struct finom_server_s {
+  struct Group;
   struct Req {
     int64_t id = 0;
     int kind = 1;                     // 1: 1D, 2: 2D
@@ -49,6 +62,27 @@ struct finom_server_s {
     int32_t status = FINOM_OK;
     finom_result res{};
     std::vector<double> f, g;
+    // batching: host checks of a 1D request (done at submit), the batch it
+    // runs in, and a cancellation that takes effect when that batch ends
+    bool valid = true;
+    Group* group = nullptr;
+    bool cancelled = false;
+  };
+  // A batch of small 1D requests, solved by a host thread on the batch's
+  // slot.  The thread writes the members' results, then sets ready (the
+  // members are no longer touched by it), releases the plan and the device
+  // memory, then sets done.
+  struct Group {
+    std::vector<Req*> members;
+    int slot = -1;
+    int64_t footprint = 0;
+    double tol = 0.0;
+    int64_t maxit = 0;
+    std::atomic<int> stop{0};
+    std::atomic<int> ready{0};
+    std::atomic<int> done{0};
+    bool collected = false;     // members moved to finished
+    std::thread worker;
   };
   int64_t budget = 0, used = 0;
   int max_active = 8;
@@ -57,6 +91,9 @@ struct finom_server_s {
   int sc_stages = 0;
   double sc_factor = 0.5, sc_tol = 1e-4;
   int policy = FINOM_SERVE_FIFO;        // admission order
+  // 1D requests with N + M <= batch_points are batched (0: never); the
+  // default for float32 servers, float64 servers solve every request alone
+  int64_t batch_points = 0;
   finom_precision prec = FINOM_F32_LOG;
   int device = 0;
   int64_t next_id = 1;
@@ -67,6 +104,8 @@ struct finom_server_s {
   // before any request changes hands.
   std::deque<Req*> pending;
   std::vector<Req*> active;
+  std::vector<Group*> groups;   // active batches
+  int64_t grouped = 0;          // requests in active batches, not yet finished
   std::vector<Req*> finished;
   std::vector<cudaStream_t> streams;
   std::vector<int> free_slots;
@@ -131,6 +170,212 @@ void fail(finom_server_s* s, Req* r, finom_status rc) {
 
 std::vector<Req*>::iterator find_finished(finom_server_s* s, int64_t id) {
   return std::find_if(s->finished.begin(), s->finished.end(), [id](const Req* r) { return r->id == id; });
+}
+
+// batching
+constexpr int64_t kBatchPoints = (int64_t)1 << 16;   // default limit of float32 servers (N + M)
+constexpr size_t kGroupMax = 1024;                   // requests per batch
+constexpr int64_t kGroupPoints = (int64_t)1 << 24;   // padded merged points per batch
+constexpr int64_t kPad = 2048;                       // a batch packs each request into whole tiles of
+                                                     // at most this many merged points
+
+int64_t padded(const Req* r) { return (r->N + r->M + kPad - 1) / kPad * kPad; }
+
+// the footprint a batch adds for one more member, and that of a batch of one
+int64_t member_bytes(const Req* r) { return padded(r) * 240; }
+int64_t group_bytes(const Req* r) { return member_bytes(r) + (1 << 20); }
+
+// the checks finom_plan and finom_solve make on the device, on the host: a
+// batch plan refuses the whole batch for one bad request, so bad requests
+// are finished before they join one
+bool check_1d(const Req* r) {
+  auto mesh = [](const std::vector<double>& a) {
+    for (size_t i = 0; i < a.size(); ++i)
+      if (!std::isfinite(a[i]) || (i > 0 && a[i] < a[i - 1])) return false;
+    return true;
+  };
+  auto mass = [](const std::vector<double>& a) {
+    double t = 0.0;
+    for (double v : a) {
+      if (!std::isfinite(v) || v < 0.0) return false;
+      t += v;
+    }
+    return t > 0.0 && std::isfinite(t);
+  };
+  return std::isfinite(r->eps) && mesh(r->in[0]) && mesh(r->in[1]) && mass(r->in[2]) && mass(r->in[3]);
+}
+
+bool batchable(const finom_server_s* s, const Req* r) {
+  return s->batch_points > 0 && s->sc_stages == 0 && r->kind == 1 && r->N + r->M <= s->batch_points;
+}
+
+// requests that share a batch: the same stop rule, and eps within a factor 2
+// (similar iteration counts, so that members retire at similar times)
+bool compatible(const Req* a, const Req* b) {
+  return a->tol == b->tol && a->maxit == b->maxit && std::max(a->eps, b->eps) <= 2.0 * std::min(a->eps, b->eps);
+}
+
+// The host thread of a batch: packed inputs to the device, the batch plan,
+// the blocking batch solve (float64 verification and finish included), the
+// members' potentials and results; then ready, then the plan and the device
+// memory are released, then done.
+void run_group(finom_server_s::Group* g, int device, cudaStream_t st, finom_precision prec) {
+  const size_t B = g->members.size();
+  finom_status rc = FINOM_OK;
+  std::vector<finom_result> res;
+  finom_plan_t plan = nullptr;
+  double* d = nullptr;
+  cudaSetDevice(device);
+  try {
+    std::vector<int64_t> offx(B + 1, 0), offy(B + 1, 0);
+    std::vector<double> eps(B);
+    for (size_t b = 0; b < B; ++b) {
+      offx[b + 1] = offx[b] + g->members[b]->N;
+      offy[b + 1] = offy[b] + g->members[b]->M;
+      eps[b] = g->members[b]->eps;
+    }
+    const int64_t X = offx[B], Y = offy[B];
+    // x | y | u | v of every member, packed; f | g follow on the device
+    std::vector<double> h(2 * (X + Y));
+    for (size_t b = 0; b < B; ++b) {
+      const Req* r = g->members[b];
+      std::copy(r->in[0].begin(), r->in[0].end(), h.begin() + offx[b]);
+      std::copy(r->in[1].begin(), r->in[1].end(), h.begin() + X + offy[b]);
+      std::copy(r->in[2].begin(), r->in[2].end(), h.begin() + (X + Y) + offx[b]);
+      std::copy(r->in[3].begin(), r->in[3].end(), h.begin() + (2 * X + Y) + offy[b]);
+    }
+    res.resize(B);
+    cudaError_t e = cudaMallocAsync(&d, sizeof(double) * 3 * (X + Y), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = finom::cuda_fail(e, "finom_server_step: batch inputs");
+    if (rc == FINOM_OK)
+      rc = finom_plan_batch(d, offx.data(), d + X, offy.data(), (int64_t)B, eps.data(), prec, st, &plan);
+    double* fg = d ? d + 2 * (X + Y) : nullptr;
+    if (rc == FINOM_OK) {
+      plan->stop = &g->stop;
+      rc = finom_solve_batch(plan, d + (X + Y), d + (2 * X + Y), g->tol, g->maxit, fg, fg + X, res.data(), st);
+    }
+    if (rc == FINOM_OK) {
+      for (Req* r : g->members) {
+        r->f.resize(r->N);
+        r->g.resize(r->M);
+      }
+      h.resize(X + Y);
+      e = cudaMemcpyAsync(h.data(), fg, sizeof(double) * (X + Y), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = finom::cuda_fail(e, "finom_server_step: batch results");
+      for (size_t b = 0; b < B && rc == FINOM_OK; ++b) {
+        Req* r = g->members[b];
+        std::copy(h.begin() + offx[b], h.begin() + offx[b + 1], r->f.begin());
+        std::copy(h.begin() + X + offy[b], h.begin() + X + offy[b + 1], r->g.begin());
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    finom::set_error("finom_server_step: out of host memory for a batch");
+    rc = FINOM_ENOMEM;
+  }
+  const double t = now_s();
+  for (size_t b = 0; b < B; ++b) {
+    Req* r = g->members[b];
+    r->status = rc;
+    if (rc == FINOM_OK) {
+      r->res = res[b];
+    } else {
+      r->res = finom_result{};
+      r->res.status = rc;
+      std::vector<double>().swap(r->f);
+      std::vector<double>().swap(r->g);
+    }
+    r->t_done = t;
+  }
+  g->ready.store(1, std::memory_order_release);   // the members are the server's again
+  if (plan) finom_plan_destroy(plan);
+  if (d) {
+    cudaFreeAsync(d, st);
+    cudaStreamSynchronize(st);
+  }
+  g->done.store(1, std::memory_order_release);
+}
+
+// Admission of a batch headed by *pick: the head and the queued requests
+// compatible with it (in admission order) while the memory budget allows.
+// FINOM_ENOMEM, with nothing changed, when the host bookkeeping or the
+// thread cannot be had.
+finom_status admit_group(finom_server_s* s, std::deque<Req*>::iterator pick) {
+  using Group = finom_server_s::Group;
+  Req* head = *pick;
+  Group* g = new (std::nothrow) Group();
+  if (!g) return FINOM_ENOMEM;
+  std::deque<Req*> rest;
+  try {
+    g->members.push_back(head);
+    g->footprint = group_bytes(head);
+    int64_t pts = padded(head);
+    std::vector<Req*> cand;
+    for (Req* q : s->pending)
+      if (q != head && q->valid && batchable(s, q) && compatible(head, q)) cand.push_back(q);
+    if (s->policy == FINOM_SERVE_SMALLEST_FIRST)
+      std::stable_sort(cand.begin(), cand.end(), [](const Req* a, const Req* b) { return a->footprint < b->footprint; });
+    for (Req* q : cand) {
+      if (g->members.size() >= kGroupMax) break;
+      if (s->used + g->footprint + member_bytes(q) > s->budget || pts + padded(q) > kGroupPoints) continue;
+      g->members.push_back(q);
+      g->footprint += member_bytes(q);
+      pts += padded(q);
+    }
+    for (Req* q : g->members) q->group = g;
+    for (Req* q : s->pending)
+      if (q->group != g) rest.push_back(q);
+    g->slot = s->free_slots.back();
+    g->tol = head->tol;
+    g->maxit = head->maxit;
+    g->worker = std::thread(run_group, g, s->device, s->streams[g->slot], s->prec);
+  } catch (...) {   // std::bad_alloc, or std::system_error from the thread
+    for (Req* q : g->members) q->group = nullptr;
+    delete g;
+    return FINOM_ENOMEM;
+  }
+  // nothing below throws (the round reserved room in groups)
+  s->free_slots.pop_back();
+  s->pending.swap(rest);
+  s->used += g->footprint;
+  s->grouped += (int64_t)g->members.size();
+  const double t = now_s();
+  for (Req* q : g->members) {
+    q->t_admit = t;
+    q->slot = g->slot;
+  }
+  s->groups.push_back(g);
+  return FINOM_OK;
+}
+
+// a batch whose thread has written its results: the members to finished;
+// once the thread is done, the slot and the memory are free again
+bool retire_group(finom_server_s* s, finom_server_s::Group* g) {
+  if (!g->collected && g->ready.load(std::memory_order_acquire)) {
+    for (Req* q : g->members) {
+      if (q->cancelled) q->status = q->res.status = FINOM_ECANCELED;
+      q->group = nullptr;
+      q->slot = -1;
+      for (auto& v : q->in) std::vector<double>().swap(v);
+      s->finished.push_back(q);   // (capacity reserved by submit)
+    }
+    s->grouped -= (int64_t)g->members.size();
+    g->collected = true;
+  }
+  if (!g->collected || !g->done.load(std::memory_order_acquire)) return false;
+  g->worker.join();
+  s->free_slots.push_back(g->slot);
+  s->used -= g->footprint;
+  return true;
+}
+
+// a queued request that fails the host checks of batching
+void finish_invalid(finom_server_s* s, Req* r) {
+  r->status = r->res.status = FINOM_EINVAL;
+  r->t_admit = r->t_done = now_s();
+  for (auto& v : r->in) std::vector<double>().swap(v);
+  s->finished.push_back(r);   // (capacity reserved by submit)
 }
 
 // a plan of the request's meshes (device copies in r->dev) at eps e
@@ -244,7 +489,7 @@ finom_status finish(finom_server_s* s, Req* r, bool* more) {
 finom_status submit(finom_server_s* s, Req* r, int64_t* id) {
   try {
     // room for every request in flight to finish without a reallocation
-    s->finished.reserve(s->finished.size() + s->pending.size() + s->active.size() + 1);
+    s->finished.reserve(s->finished.size() + s->pending.size() + s->active.size() + (size_t)s->grouped + 1);
     s->pending.push_back(r);
   } catch (const std::bad_alloc&) {
     delete r;
@@ -253,6 +498,7 @@ finom_status submit(finom_server_s* s, Req* r, int64_t* id) {
   }
   r->id = s->next_id++;
   r->footprint = footprint(r->kind, r->N, r->M);
+  if (r->kind == 1) r->valid = check_1d(r);
   r->t_submit = now_s();
   if (id) *id = r->id;
   return FINOM_OK;
@@ -274,6 +520,7 @@ finom_status finom_server_create(int64_t mem_budget_bytes, int32_t max_active, f
   s->budget = mem_budget_bytes;
   s->max_active = max_active;
   s->prec = prec;
+  s->batch_points = prec == FINOM_F32_LOG ? kBatchPoints : 0;
   cudaGetDevice(&s->device);
   try {
     s->streams.resize(max_active);
@@ -302,6 +549,15 @@ finom_status finom_server_set_policy(finom_server_t s, int32_t policy) {
     return FINOM_EINVAL;
   }
   s->policy = policy;
+  return FINOM_OK;
+}
+
+finom_status finom_server_set_batching(finom_server_t s, int64_t max_points) {
+  if (!s || max_points < 0 || max_points > ((int64_t)1 << 22)) {
+    finom::set_error("finom_server_set_batching: need a server and 0 <= max_points <= 2^22");
+    return FINOM_EINVAL;
+  }
+  s->batch_points = max_points;
   return FINOM_OK;
 }
 
@@ -383,13 +639,16 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   }
   // the only host allocations of a round, before any state changes: every
   // request can move to the active list or its successor, and release up to
-  // three plans (two of a request, one of an eps-scaling stage)
+  // three plans (two of a request, one of an eps-scaling stage); a batch's
+  // own bookkeeping is allocated at its admission, which falls back to a
+  // solve alone when that fails
   std::vector<Req*> still;
   try {
-    const size_t n = s->active.size() + s->free_slots.size();
+    const size_t n = (size_t)s->max_active;   // every active solve or batch holds a slot
     s->active.reserve(n);
     still.reserve(n);
     s->graveyard.reserve(s->graveyard.size() + 3 * n);
+    s->groups.reserve(n);
   } catch (const std::bad_alloc&) {
     finom::set_error("finom_server_step: out of host memory");
     return FINOM_ENOMEM;
@@ -397,6 +656,18 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != s->device) cudaSetDevice(s->device);
+  // batches whose threads have finished (their slots serve this round's
+  // admissions)
+  for (size_t k = 0; k < s->groups.size();) {
+    finom_server_s::Group* g = s->groups[k];
+    if (!retire_group(s, g)) {
+      ++k;
+      continue;
+    }
+    s->groups[k] = s->groups.back();
+    s->groups.pop_back();
+    delete g;
+  }
   // admissions, first come first served: an empty server always admits
   while (!s->pending.empty() && !s->free_slots.empty()) {
     // the next request: the queue head, or the smallest queued one
@@ -405,8 +676,18 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
       for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
         if ((*it)->footprint < (*pick)->footprint) pick = it;
     Req* r = *pick;
-    if (s->used + r->footprint > s->budget && !s->graveyard.empty()) flush_graveyard(s);
-    if (!s->active.empty() && s->used + r->footprint > s->budget) break;
+    const bool batch = batchable(s, r);
+    if (batch && !r->valid) {   // refused before it can join a batch
+      s->pending.erase(pick);
+      finish_invalid(s, r);
+      continue;
+    }
+    const int64_t need = batch ? group_bytes(r) : r->footprint;
+    if (s->used + need > s->budget && !s->graveyard.empty()) flush_graveyard(s);
+    if (!(s->active.empty() && s->groups.empty()) && s->used + need > s->budget) break;
+    // a batch of it and the compatible queued requests; without host memory
+    // or a thread for one, the request is served alone
+    if (batch && admit_group(s, pick) == FINOM_OK) continue;
     s->pending.erase(pick);
     finom_status rc = admit(s, r);
     if (rc != FINOM_OK) fail(s, r, rc);
@@ -447,7 +728,7 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   if (s->graveyard.size() >= kGraveyard || (s->active.empty() && !s->graveyard.empty())) flush_graveyard(s);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   if (n_pending) *n_pending = (int32_t)s->pending.size();
-  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_active) *n_active = (int32_t)(s->active.size() + s->groups.size());
   if (n_finished) *n_finished = (int32_t)s->finished.size();
   return FINOM_OK;
 }
@@ -498,6 +779,16 @@ finom_status finom_server_cancel(finom_server_t s, int64_t id) {
     s->finished.push_back(r);
     return FINOM_OK;
   }
+  for (finom_server_s::Group* g : s->groups) {   // a batched request: when its batch ends
+    if (g->collected) continue;
+    for (Req* q : g->members) {
+      if (q->id != id) continue;
+      q->cancelled = true;
+      if (std::all_of(g->members.begin(), g->members.end(), [](const Req* m) { return m->cancelled; }))
+        g->stop.store(1, std::memory_order_relaxed);
+      return FINOM_OK;
+    }
+  }
   for (auto it = s->active.begin(); it != s->active.end(); ++it) {
     if ((*it)->id != id) continue;
     Req* r = *it;
@@ -516,6 +807,13 @@ finom_status finom_server_cancel(finom_server_t s, int64_t id) {
 
 finom_status finom_server_destroy(finom_server_t s) {
   if (!s) return FINOM_OK;
+  for (finom_server_s::Group* g : s->groups) {
+    g->stop.store(1, std::memory_order_relaxed);
+    g->worker.join();
+    if (!g->collected)
+      for (Req* q : g->members) delete q;
+    delete g;
+  }
   for (Req* r : s->active) {
     cudaStreamSynchronize(s->streams[r->slot]);
     release(s, r);

@@ -75,7 +75,8 @@ def test_served_alone_equals_in_the_mix_and_matches_oracle(lib, prec):
         alone.append(srv.run([rid])[rid])
         srv.close()
     # the mix: every request queued at once, three slots, a 12 MB budget that
-    # makes the N = M = 12000 request wait for memory
+    # makes some requests wait for memory (float32: the small 1D requests are
+    # batched, float64: each is solved alone)
     srv = lib.Server(12 << 20, max_active=3, precision=prec)
     ids = [_submit(srv, r) for r in reqs]
     peak_active = 0
@@ -238,3 +239,107 @@ def test_smallest_first_admission(lib):
     rc = lib._lib.finom_server_set_policy(srv.handle, 7)
     assert rc == lib.FINOM_EINVAL
     srv.close()
+
+
+def _small_1d(n, seed, eps, kind="uniform_random"):
+    x, y = meshes(kind, n, n + 17, seed)
+    u, v = _masses(n, n + 17, seed + 1)
+    return ("1d", (x, y, u, v), eps, 1e-6, 20000)
+
+
+@pytest.mark.parametrize("prec", ["f32_log", "f64"])
+def test_batched_requests_run_together_and_match_the_oracle(lib, prec):
+    """Compatible small 1D requests queued on a one-slot server are admitted
+    as one batch (one active solve, admitted at once); each result is the one
+    the request gets alone, and the oracle's."""
+    reqs = [_small_1d(n, 50 + n, eps) for n, eps in [(900, 0.02), (3000, 0.01), (64, 0.015), (1500, 0.02)]]
+    srv = lib.Server(1 << 32, max_active=1, precision=prec)
+    srv.set_batching(1 << 16)
+    ids = [_submit(srv, r) for r in reqs]
+    out, peak = {}, 0
+    while len(out) < len(ids):
+        pend, act, fin = srv.step()
+        peak = max(peak, act)
+        for rid in ids:
+            if rid not in out:
+                got = srv.result(rid)
+                if got is not None:
+                    out[rid] = got
+    srv.close()
+    assert peak == 1
+    d = [out[rid][0] for rid in ids]
+    # one admission for all four: none waited for another to finish
+    assert max(x["queue_s"] for x in d) < min(x["latency_s"] for x in d)
+    for r, rid in zip(reqs, ids):
+        dm, fm, gm = out[rid]
+        assert dm["status"] == 0 and dm["converged"] == 1
+        srv1 = lib.Server(1 << 32, max_active=1, precision=prec)
+        srv1.set_batching(1 << 16)
+        k = _submit(srv1, r)
+        da, fa, ga = srv1.run([k])[k]
+        srv1.close()
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm) and da["iters"] == dm["iters"]
+        w1o, ito = _oracle(r)
+        assert dm["w1"] == pytest.approx(w1o, rel=1e-4 if prec == "f32_log" else 1e-9)
+        if prec == "f64":
+            assert dm["iters"] == ito
+        e_or = _oracle_err(r, fm, gm)
+        assert e_or <= r[3] * (1 + 1e-6) + 1e-15
+        assert dm["marginal_err"] == pytest.approx(e_or, rel=1e-6, abs=1e-13)
+
+
+def test_batching_limit_and_compatibility(lib):
+    """Requests above the limit, with another tol, or with eps more than a
+    factor 2 apart are not batched together; batching off serves every
+    request alone; both give the oracle's fixed point."""
+    reqs = [_small_1d(800, 7, 0.01), _small_1d(700, 9, 0.05), _small_1d(5000, 11, 0.01),
+            ("1d",) + _small_1d(600, 13, 0.01)[1:3] + (1e-7, 20000)]
+    res = {}
+    for limit in (4096, 0):
+        srv = lib.Server(1 << 32, max_active=1, precision="f32_log")
+        srv.set_batching(limit)
+        ids = [_submit(srv, r) for r in reqs]
+        res[limit] = srv.run(ids)
+        res[limit] = [res[limit][i] for i in ids]
+        srv.close()
+    # with one slot and nothing compatible, each request waits for the one before
+    d = [x[0] for x in res[4096]]
+    for a, b in zip(d, d[1:]):
+        assert b["queue_s"] >= a["latency_s"] - 0.05
+    for r, a, b in zip(reqs, res[4096], res[0]):
+        assert a[0]["converged"] == b[0]["converged"] == 1
+        w1o, _ = _oracle(r)
+        assert a[0]["w1"] == pytest.approx(w1o, rel=1e-4) and b[0]["w1"] == pytest.approx(w1o, rel=1e-4)
+        assert _oracle_err(r, a[1], a[2]) <= r[3] * (1 + 1e-6) + 1e-15
+    srv = lib.Server(1, max_active=1)
+    assert lib._lib.finom_server_set_batching(srv.handle, -1) == lib.FINOM_EINVAL
+    assert lib._lib.finom_server_set_batching(srv.handle, (1 << 22) + 1) == lib.FINOM_EINVAL
+    srv.close()
+
+
+def test_cancel_batched_requests(lib):
+    """Cancelling every request of a running batch stops it early; cancelling
+    one of two leaves the other to converge."""
+    x, y = meshes("graded", 20000, 20000, 3)
+    u, v = _masses(20000, 20000, 4)
+    srv = lib.Server(1 << 32, max_active=1, precision="f32_log")
+    long_ = [srv.submit_1d(x, y, u, v, 0.001, 1e-9, 100000) for _ in range(3)]   # one batch
+    srv.step()
+    for rid in long_:
+        srv.cancel(rid)
+    x2, y2 = meshes("uniform_random", 900, 700, 5)
+    u2, v2 = _masses(900, 700, 6)
+    a = srv.submit_1d(x2, y2, u2, v2, 0.02, 1e-6, 5000)
+    b = srv.submit_1d(x2, y2, u2, v2, 0.02, 1e-6, 5000)
+    out = srv.run(long_ + [a, b])
+    assert all(out[r][0]["status"] == lib.FINOM_ECANCELED for r in long_)
+    assert all(out[r][0]["iters"] < 100000 for r in long_)
+    assert out[a][0]["status"] == 0 and out[a][0]["converged"] == 1
+    c = srv.submit_1d(x2, y2, u2, v2, 0.02, 1e-6, 5000)
+    d = srv.submit_1d(x2, y2, u2, v2, 0.02, 1e-6, 5000)
+    srv.step()
+    srv.cancel(c)
+    out = srv.run([c, d])
+    srv.close()
+    assert out[c][0]["status"] == lib.FINOM_ECANCELED
+    assert out[d][0]["status"] == 0 and out[d][0]["converged"] == 1
