@@ -111,9 +111,18 @@ struct finom_server_s {
   std::vector<int> free_slots;
   // plans of retired requests, destroyed together: freeing device memory
   // waits for the whole device, so it is done once per batch of plans (or
-  // when their memory is needed) rather than at every retirement
+  // when their memory is needed) rather than at every retirement, and on a
+  // host thread (a reaper), so that the scheduling rounds never wait for it;
+  // their bytes count as used until the reaper is done
   std::vector<finom_plan_t> graveyard;
   int64_t dead_bytes = 0;
+  struct Reaper {
+    std::vector<finom_plan_t> plans;
+    int64_t bytes = 0;
+    std::atomic<int> done{0};
+    std::thread worker;
+  };
+  std::vector<Reaper*> reapers;
 };
 
 namespace {
@@ -138,11 +147,52 @@ int64_t npoints(const Req* r, int side) {   // points of the first (side 0) or s
 
 constexpr size_t kGraveyard = 32;
 
-void flush_graveyard(finom_server_s* s) {
+// Destroy the plans of the graveyard: on a reaper thread, or here when
+// `wait` is set or no thread can be had.
+void flush_graveyard(finom_server_s* s, bool wait = false) {
+  if (!wait && !s->graveyard.empty()) {
+    auto* k = new (std::nothrow) finom_server_s::Reaper();
+    if (k) {
+      try {
+        s->reapers.reserve(s->reapers.size() + 1);
+        k->plans.assign(s->graveyard.begin(), s->graveyard.end());
+        k->bytes = s->dead_bytes;
+        const int dev = s->device;
+        k->worker = std::thread([k, dev] {
+          cudaSetDevice(dev);
+          for (finom_plan_t p : k->plans) finom_plan_destroy(p);
+          k->done.store(1, std::memory_order_release);
+        });
+        s->reapers.push_back(k);   // (reserved above)
+        s->graveyard.clear();      // (keeps its capacity for the round)
+        s->dead_bytes = 0;
+        return;
+      } catch (...) {   // no memory or thread: destroy them here
+        delete k;
+      }
+    }
+  }
   for (finom_plan_t p : s->graveyard) finom_plan_destroy(p);
   s->graveyard.clear();
   s->used -= s->dead_bytes;
   s->dead_bytes = 0;
+}
+
+// reapers that are done: their plans' bytes are free again (all of them
+// when `wait` is set)
+void collect_reapers(finom_server_s* s, bool wait) {
+  for (size_t k = 0; k < s->reapers.size();) {
+    finom_server_s::Reaper* r = s->reapers[k];
+    if (!wait && !r->done.load(std::memory_order_acquire)) {
+      ++k;
+      continue;
+    }
+    r->worker.join();
+    s->used -= r->bytes;
+    s->reapers[k] = s->reapers.back();
+    s->reapers.pop_back();
+    delete r;
+  }
 }
 
 void release(finom_server_s* s, Req* r) {
@@ -656,8 +706,9 @@ finom_status finom_server_step(finom_server_t s, int32_t* n_pending, int32_t* n_
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != s->device) cudaSetDevice(s->device);
-  // batches whose threads have finished (their slots serve this round's
-  // admissions)
+  // batches whose threads have finished and reapers that are done (their
+  // slots and bytes serve this round's admissions)
+  collect_reapers(s, false);
   for (size_t k = 0; k < s->groups.size();) {
     finom_server_s::Group* g = s->groups[k];
     if (!retire_group(s, g)) {
@@ -821,7 +872,8 @@ finom_status finom_server_destroy(finom_server_t s) {
   }
   for (Req* r : s->pending) delete r;
   for (Req* r : s->finished) delete r;
-  flush_graveyard(s);
+  flush_graveyard(s, true);
+  collect_reapers(s, true);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   delete s;
   return FINOM_OK;
