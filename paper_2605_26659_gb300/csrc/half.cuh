@@ -51,6 +51,7 @@
 #include <cstdint>
 
 #include "dev_common.cuh"
+#include "exp2_table.h"
 #include "finom_internal.h"
 
 namespace finom {
@@ -210,35 +211,49 @@ struct HT<float> {
   }
 };
 
-// 2^x in float64 for the scans: x = n + f with n = rint(x) and |f| <= 1/2,
-// 2^f = e^{f ln 2} summed as its Taylor series to degree 13 (for |f ln 2| <=
-// 0.347 the remainder is below 1e-17 relative), and n added to the binary
-// exponent.  Arguments below -1021 give 0 (the terms they weigh are below
-// 2^-1021 of the sums they join), above 1023 infinity.  About 16 float64
-// instructions: on GB300 every float64 warp instruction occupies its
-// sub-partition's float64 pipe for 64 cycles, so the scans' combines are
-// counted in these.
-__device__ __forceinline__ double exp2_series(double x) {
-  if (!(x > -1021.0)) return 0.0;
-  if (x > 1023.0) return INFINITY;
-  const double n = rint(x);
-  const double t = (x - n) * 0.69314718055994530942;
-  // 1/k! for k = 13 .. 2
-  double p = 1.6059043836821614599e-10;
-  p = fma(p, t, 2.0876756987868098979e-09);
-  p = fma(p, t, 2.5052108385441718775e-08);
-  p = fma(p, t, 2.7557319223985890653e-07);
-  p = fma(p, t, 2.7557319223985890653e-06);
-  p = fma(p, t, 2.4801587301587301587e-05);
-  p = fma(p, t, 1.9841269841269841270e-04);
-  p = fma(p, t, 1.3888888888888888889e-03);
+// 2^x in float64 for the scans, table-driven (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15(2), 1989, in base 2): x = n + k/64 + r with n =
+// floor(x), k in 0..63 and 0 <= r < 1/64 read off the fixed-point bits of x
+// by integer operations; 2^(k/64) from a 64-entry table (exp2_table.h) and
+// 2^r = e^t, t = r ln 2 < 0.0109, as its Taylor series to degree 6 (remainder
+// below 4e-18 relative); n is added to the binary exponent.  Within about 3
+// ulp.  Nine float64 instructions: on GB300 every float64 warp instruction
+// occupies its sub-partition's float64 pipe for 64 cycles, so the scans'
+// combines are counted in these (a plain range reduction and a degree-13
+// series take about eighteen).  Arguments below -1021 (and NaN) give 0,
+// above 1023 infinity.
+__device__ __forceinline__ double exp2_tab(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7ff);
+  const bool neg = (u >> 63) != 0;
+  if (ex >= 1023 + 11) {   // |x| >= 2048, infinities, NaN
+    const bool nan = ex == 0x7ff && (u << 12) != 0;
+    return (neg || nan) ? 0.0 : INFINITY;
+  }
+  if (ex < 1023 - 53) return 1.0;   // |x| < 2^-53
+  // |x| 2^52 as an integer (bits below 2^-52 dropped: an error below 2^-52 in x)
+  const unsigned long long m = (u & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = ex - 1023;   // -53 .. 10
+  const unsigned long long X = sh >= 0 ? (m << sh) : (m >> (-sh));
+  const long long Xs = neg ? -(long long)X : (long long)X;
+  const long long n = Xs >> 52;   // floor(x)
+  if (n < -1021) return 0.0;
+  if (n > 1023) return INFINITY;
+  const unsigned long long F = (unsigned long long)Xs & 0xfffffffffffffull;   // (x - n) 2^52
+  const int k = (int)(F >> 46);
+  const double r = (double)(long long)(F & 0x3fffffffffffull);   // r 2^52, exact
+  const double t = r * (0.69314718055994530942 * 0x1p-52);
+  // 1/j! for j = 6 .. 2
+  double p = 1.3888888888888888889e-03;
   p = fma(p, t, 8.3333333333333333333e-03);
   p = fma(p, t, 4.1666666666666666667e-02);
   p = fma(p, t, 1.6666666666666666667e-01);
   p = fma(p, t, 0.5);
   p = fma(p, t, 1.0);
   p = fma(p, t, 1.0);
-  return __longlong_as_double(__double_as_longlong(p) + (long long)n * (1LL << 52));
+  const double v = __ldg(&kExp2Tab[k]) * p;   // in [1, 2)
+  return __longlong_as_double(__double_as_longlong(v) + (n << 52));
 }
 
 template <>
@@ -252,7 +267,7 @@ struct HT<double> {
   __device__ __forceinline__ static Beta pack(Lv p, Lv m) { return make_double2(p, m); }
   __device__ __forceinline__ static Lv none() { return kNone; }
   __device__ __forceinline__ static bool valid(Lv a) { return a > 0.5 * kNone; }
-  __device__ __forceinline__ static double ex2(double x) { return exp2_series(x); }
+  __device__ __forceinline__ static double ex2(double x) { return exp2_tab(x); }
   __device__ __forceinline__ static double lg2(double x) { return log2(x); }
   __device__ __forceinline__ static double lg2_acc(double x) { return log2(x); }
   __device__ __forceinline__ static double diff(Lv a, Lv b) { return a - b; }
