@@ -345,6 +345,83 @@ __device__ __forceinline__ void st_term(St<R>& a, typename HT<R>::Lv lv) {
   a.M = gt ? lv : a.M;
 }
 
+// Float64 states keep M a whole number of bits, so that the factor between
+// two states is an exact power of two, built from the bits of the
+// difference of their levels: a combine is one float64 fused multiply-add
+// and an add instead of a 2^x (GB300 runs float64 at a 64th of the float32
+// rate, and the scans chain their combines).  A term 2^lv enters as
+// 2^(lv - floor lv) 2^floor(lv).  The value s 2^M of a state is the same as
+// with a fractional M; s then lies in [1, 2 n) for n terms.
+
+// 2^-|d| for a whole number d (0 when |d| > 1022, and for d = +-none)
+__device__ __forceinline__ double pow2_neg(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int ex = (int)((u >> 52) & 0x7ff);
+  if (ex < 1023) return 1.0;            // d = 0
+  if (ex >= 1023 + 10) return 0.0;      // |d| >= 1024
+  const int k = (int)(((u & 0xfffffffffffffull) | (1ull << 52)) >> (52 - (ex - 1023)));   // |d|
+  return k > 1022 ? 0.0 : __longlong_as_double((long long)(1023 - k) << 52);
+}
+
+// d > 0 from the bits of d (no float64 instruction)
+__device__ __forceinline__ bool pos_bits(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0;   // sign clear and not +0 (NaN does not occur)
+}
+
+// 2^x = v 2^n with n = floor(x) and v = 2^(x - n) in [1, 2), by the steps of
+// exp2_tab on the fraction; v = 0 (and n = 0) for a level below -2^900 (none)
+__device__ __forceinline__ double exp2_split(double x, double& n) {
+  const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
+  if ((ux >> 63) && ((ux >> 52) & 0x7ff) >= 1023 + 900) {
+    n = 0.0;
+    return 0.0;
+  }
+  n = floor(x);
+  const double f = x - n;   // in [0, 1], exact unless it rounds up to 1 (x just below a whole number)
+  const unsigned long long u = (unsigned long long)__double_as_longlong(f);
+  const int ex = (int)((u >> 52) & 0x7ff);
+  if (ex < 1023 - 53) return 1.0;   // f < 2^-53
+  if (ex >= 1023) {                 // f = 1
+    n += 1.0;
+    return 1.0;
+  }
+  const unsigned long long F = ((u & 0xfffffffffffffull) | (1ull << 52)) >> (1023 - ex);   // f 2^52
+  const int k = (int)(F >> 46);
+  const double r = (double)(long long)(F & 0x3fffffffffffull);
+  const double t = r * (0.69314718055994530942 * 0x1p-52);
+  double p = 1.3888888888888888889e-03;
+  p = fma(p, t, 8.3333333333333333333e-03);
+  p = fma(p, t, 4.1666666666666666667e-02);
+  p = fma(p, t, 1.6666666666666666667e-01);
+  p = fma(p, t, 0.5);
+  p = fma(p, t, 1.0);
+  p = fma(p, t, 1.0);
+  return __ldg(&kExp2Tab[k]) * p;
+}
+
+template <>
+__device__ __forceinline__ St<double> st_comb(const St<double>& a, const St<double>& b) {
+  const double d = b.M - a.M;   // a whole number, or +-none
+  const bool gt = pos_bits(d);
+  const double e = pow2_neg(d);
+  St<double> r;
+  r.s = gt ? fma(a.s, e, b.s) : fma(b.s, e, a.s);
+  r.M = gt ? b.M : a.M;
+  return r;
+}
+
+template <>
+__device__ __forceinline__ void st_term(St<double>& a, double lv) {
+  double n;
+  const double v = exp2_split(lv, n);
+  const double d = n - a.M;
+  const bool gt = __double_as_longlong(v) != 0 && pos_bits(d);
+  const double e = pow2_neg(d);
+  a.s = gt ? fma(a.s, e, v) : fma(v, e, a.s);
+  a.M = gt ? n : a.M;
+}
+
 template <class R>
 __device__ __forceinline__ St<R> st_shfl_up(const St<R>& a, int o) {
   return {HT<R>::shfl_up(a.M, o), __shfl_up_sync(0xffffffffu, a.s, o)};

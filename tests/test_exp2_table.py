@@ -101,3 +101,57 @@ def test_table_driven_exp2_steps_against_exp2():
     assert _exp2_tab(-1022.0, t) == 0.0 and _exp2_tab(-1e300, t) == 0.0 and _exp2_tab(-math.inf, t) == 0.0
     assert _exp2_tab(1024.5, t) == math.inf and _exp2_tab(math.inf, t) == math.inf
     assert _exp2_tab(math.nan, t) == 0.0
+
+
+def _exp2_split(x, t):
+    """2^x = v 2^n, n = floor(x), v = 2^(x - n): the kernel's steps for the
+    terms of the float64 scans (levels of any size; none gives v = 0)."""
+    ux = _bits(x)
+    if (ux >> 63) and ((ux >> 52) & 0x7FF) >= 1023 + 900:
+        return 0.0, 0.0
+    n = math.floor(x)
+    f = x - n
+    u = _bits(f)
+    ex = (u >> 52) & 0x7FF
+    if ex < 1023 - 53:
+        return 1.0, float(n)
+    if ex >= 1023:
+        return 1.0, float(n + 1)
+    F = ((u & ((1 << 52) - 1)) | (1 << 52)) >> (1023 - ex)
+    k = F >> 46
+    r = float(F & ((1 << 46) - 1))
+    tt = r * (0.69314718055994530942 * 2.0 ** -52)
+    from fractions import Fraction
+    p = 1.3888888888888888889e-03
+    for coef in (8.3333333333333333333e-03, 4.1666666666666666667e-02, 1.6666666666666666667e-01, 0.5, 1.0, 1.0):
+        p = float(Fraction(p) * Fraction(tt) + Fraction(coef))
+    return t[k] * p, float(n)
+
+
+def _pow2_neg(d):
+    u = _bits(d)
+    ex = (u >> 52) & 0x7FF
+    if ex < 1023:
+        return 1.0
+    if ex >= 1023 + 10:
+        return 0.0
+    k = (((u & ((1 << 52) - 1)) | (1 << 52)) >> (52 - (ex - 1023)))
+    return 0.0 if k > 1022 else _double((1023 - k) << 52)
+
+
+def test_split_terms_and_whole_number_scales():
+    t = _table()
+    g = np.random.default_rng(21)
+    xs = list(g.uniform(-3e4, 3e4, 3000)) + list(g.uniform(-3, 3, 3000)) + [0.0, -1e-20, 5e-17, 2047.999, -0.5,
+                                                                                   -3.0 - 1e-17, 7.0 - 2.0 ** -50]
+    for x in xs:
+        v, n = _exp2_split(float(x), t)
+        assert n in (math.floor(x), math.floor(x) + 1) and 1.0 <= v < 2.0
+        # 2^x = 2^(x - n) 2^n, x - n in [0, 1) rounded at most once
+        want = math.exp2(x - n)
+        assert abs(v - want) <= 3 * _ulp(want), x
+    assert _exp2_split(-1e300, t) == (0.0, 0.0)
+    for d in range(-1100, 1100):
+        want = 0.0 if abs(d) > 1022 else 2.0 ** -abs(d)
+        assert _pow2_neg(float(d)) == want
+    assert _pow2_neg(1e300) == 0.0 and _pow2_neg(-1e300) == 0.0 and _pow2_neg(0.0) == 1.0
