@@ -474,6 +474,12 @@ finom_status finom_ktu_log(finom_plan_t plan, const double* a, const double* b, 
  *   f: N doubles, g: M doubles (device, outputs; f, g in cost units).  If
  *      warm != 0 they are also inputs (warm-start potentials).
  *   res: host struct, filled on return.
+ * FINOM_F32_LOG plans (1D): the float32 loop's own check stops no lower than
+ * 2e-7 (its rounding floor); the marginal error is then verified in float64,
+ * and a solve whose float64 error is above tol continues, first in float32
+ * with a tightened check while that stays above the floor, then in float64
+ * on a float64 plan of the same meshes, warm-started from the float32
+ * potentials (res->iters counts every iteration).
  * Synchronous (returns when the solve is done).  Non-convergence is not an
  * error: res->converged = 0, res->iters = maxit.
  */
@@ -523,11 +529,15 @@ finom_status finom_solve_eps_scaling(finom_plan_t plan, const double* u, const d
  *   finom_solve_step   launches `iterations` more Sinkhorn iterations (two
  *                      kernels each) on `stream`; asynchronous.  Iterations
  *                      after the loop has stopped return at once.
- *   finom_solve_poll   *done = 1 once the loop stopped (check <= tol or maxit);
+ *   finom_solve_poll   *done = 1 once the loop stopped (check <= tol or maxit;
+ *                      1D float32 plans: check <= max(tol, 2e-7));
  *                      *iters = completed iterations.  Synchronises `stream`.
  *   finom_solve_end    writes f, g (device, cost units) and res (host) for the
  *                      state at the loop exit, or after the last completed
- *                      iteration if the loop is still running.  Synchronous.
+ *                      iteration if the loop is still running; res->converged
+ *                      is the float64 error <= tol for float32 plans (a caller
+ *                      may continue in float64, warm-started, as the serving
+ *                      loop does).  Synchronous.
  * Any kernel product or finom_cost on the same plan in between ends the solve.
  */
 finom_status finom_solve_begin(finom_plan_t plan, const double* u, const double* v, double tol,

@@ -230,7 +230,8 @@ finom_status solve_begin(finom_plan_s* p, const double* u, const double* v, doub
   }
   FINOM_CUDA(cudaMemsetAsync(st.ctrl, 0, sizeof(int32_t) * 8, s));
   FINOM_CUDA(cudaMemsetAsync(st.scal, 0, sizeof(double) * 8, s));
-  st.tol = tol;
+  st.tol = sizeof(R) == sizeof(float) ? std::max(tol, kF32LoopFloor) : tol;
+  st.tol_user = tol;
   st.maxit = maxit;
   st.launched = 0;
   st.active = true;
@@ -334,7 +335,7 @@ finom_status solve_end(finom_plan_s* p, double* f, double* g, finom_result* res,
     res->marginal_err_loop = loop_err;
     res->dual = hd[0] + hd[1];
     res->iters = iters;
-    res->converged = (err64 <= st.tol || (converged && sizeof(R) == sizeof(double))) ? 1 : 0;
+    res->converged = (err64 <= st.tol_user || (converged && sizeof(R) == sizeof(double))) ? 1 : 0;
     res->status = FINOM_OK;
   }
   st.active = false;
@@ -394,8 +395,10 @@ finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, d
       if (rc != FINOM_OK) return rc;
       if (err64 <= tol) break;
       // resume: clear the stop, continue with the phi half step of iteration l
-      const double f = std::max(0.1, std::min(0.97, 0.97 * tol / err64));
-      st.tol = std::max(loop_err * f, 0.0);
+      // (not below the float32 floor: then the float64 finish below)
+      const double fr = std::max(0.1, std::min(0.97, 0.97 * tol / err64));
+      if (loop_err * fr < kF32LoopFloor) break;
+      st.tol = loop_err * fr;
       int32_t zero[2] = {0, 0};
       FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 1, &zero[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
       FINOM_CUDA(cudaMemcpyAsync(st.ctrl + 4, &zero[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -403,10 +406,27 @@ finom_status solve_blocking(finom_plan_s* p, const double* u, const double* v, d
       if (rc != FINOM_OK) return rc;
       st.launched = l + 1;
     }
-    st.tol = tol;
+    st.tol = sizeof(R) == sizeof(float) ? std::max(tol, kF32LoopFloor) : tol;
   }
-  rc = solve_end<R>(p, f, g, res, s);
+  finom_result r32{};
+  rc = solve_end<R>(p, f, g, &r32, s);
   if (rc != FINOM_OK) return rc;
+  // a float32 solve whose float64 error is still above tol (a float32 floor
+  // above it) is finished in float64, warm-started from its potentials, on a
+  // float64 plan of the same meshes; iters counts both parts
+  if (sizeof(R) == sizeof(float) && !r32.converged && r32.iters < maxit) {
+    finom_plan_t p64 = nullptr;
+    rc = finom_plan(p->x, p->N, p->y, p->M, p->eps, FINOM_F64, s, &p64);
+    if (rc != FINOM_OK) return rc;
+    finom_result r64{};
+    rc = finom_solve(p64, u, v, tol, maxit - r32.iters, f, g, 1, &r64, s);
+    finom_plan_destroy(p64);
+    if (rc != FINOM_OK) return rc;
+    r64.iters += r32.iters;
+    r64.marginal_err_loop = r32.marginal_err_loop;
+    r32 = r64;
+  }
+  if (res) *res = r32;
   return FINOM_OK;
 }
 

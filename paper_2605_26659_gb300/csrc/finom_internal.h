@@ -50,6 +50,11 @@ finom_status cuda_fail(cudaError_t e, const char* what);
 // Device state of the Sinkhorn loop of one plan (allocated on first use).
 // iterations per graph launch of the stepwise solves (an even number)
 constexpr int kChunkIters = 16;
+// The float32 loop's own marginal-error check stops no lower than this: the
+// float32 estimate of the error sum has a rounding floor of about this size
+// (an error of a few float32 roundings in each log-sum); a solve to a tighter
+// tol continues in float64 from the float32 potentials.
+constexpr double kF32LoopFloor = 2e-7;
 
 struct SolveState {
   bool ready = false;
@@ -85,7 +90,8 @@ struct SolveState {
   // the solve in progress
   bool active = false;
   bool warm = false;
-  double tol = 0.0;
+  double tol = 0.0;                   // the loop's own check (device)
+  double tol_user = 0.0;              // the solve's tol (float64 verification)
   int64_t maxit = 0;
   int64_t launched = 0;               // iterations launched so far (host count)
 };
