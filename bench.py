@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--impl", choices=["finom", "reference"], default="finom")
     ap.add_argument("--n", "--mesh-points", dest="n", type=int, default=1 << 20, help="points per mesh (default 2^20)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", choices=["1d", "2d", "batch", "serve"], default="1d")
+    ap.add_argument("--workload", choices=["1d", "2d", "batch", "serve", "small"], default="1d")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests of the arrival process")
     ap.add_argument("--slots", type=int, default=64, help="serve: concurrent solves (streams)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory for active solves")
@@ -483,6 +483,29 @@ def run_small(dev, stream):
     except (OSError, KeyError, ValueError):
         pass
     return out
+
+
+def run_finom_small(args, ws, rank, local):
+    """The 1000-point float64 workload alone, as its own line: point-iters/s
+    of the stepwise loop (its us per iteration from run_small)."""
+    import torch
+    from paper_2605_26659_gb300 import api
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    api.load()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        run_small(dev, stream)
+    small = run_small(dev, stream)
+    if rank == 0:
+        us = small["value"]
+        line = {"metric": METRIC, "value": ws * 2000 / (us * 1e-6), "unit": UNIT, "n_gpus": ws, "steps": 512,
+                "warmup": max(args.warmup, 1), "ms_per_step": us * 1e-3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": small["config"]["workload"], "parallelism": f"replicas x{ws}",
+                           "l2": "resident (88 KB of inputs; latency-bound)", "tile_kind": small["tile_kind"]},
+                "gpu_launches": 2 * 512, "roofline": None, "small_fp64": small}
+        print(json.dumps(line), flush=True)
 
 
 def _concat_batch(probs):
@@ -925,6 +948,8 @@ def main():
         run_finom_batch(args, ws, rank, local)
     elif args.workload == "serve":
         run_finom_serve(args, ws, rank, local)
+    elif args.workload == "small":
+        run_finom_small(args, ws, rank, local)
     else:
         run_finom(args, ws, rank, local)
     if ws > 1:
