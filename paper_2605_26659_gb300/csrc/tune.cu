@@ -28,19 +28,19 @@ std::mutex g_tune_mu;
 
 // Defaults from a tuning run on GB300 (finom_autotune, 64 iterations per
 // candidate, buckets 2^10 .. 2^22; E = -1 is the 64-point tile).  float64:
-// 2^10-2^12 take E = -1 (52-74 us per iteration against 93-97 with E = 1 and
-// 117-209 with E = 8), 2^13 E = 1, 2^14 E = 2, 2^15 E = 4, 2^16 E = 2, 2^17-2^18
-// E = 4, from 2^19 on E = 8.  float32: 2^10-2^11 E = -1 (9.7-10.3 us against
-// 11.0 with E = 1), 2^12-2^13 E = 1, 2^14 E = 2, 2^15 E = 4, 2^16 E = 1, 2^17
-// E = 2, 2^18-2^20 E = 4, from 2^21 on E = 8.  Smaller buckets take E = -1,
-// larger ones E = 8.
+// 2^10-2^13 take E = -1 (24.9-39.8 us per iteration against 40.9-41.9 with
+// E = 1 and 61.6-112.6 with E = 8), 2^14-2^15 E = 1, 2^16 E = 2, 2^17 E = 4,
+// from 2^18 on E = 8.  float32: 2^10-2^12 E = -1 (9.7-10.5 us against
+// 11.0-11.3 with E = 1), 2^13 E = 1, 2^14 E = 2, 2^15 E = 4, 2^16 E = 2,
+// 2^17-2^20 E = 4, from 2^21 on E = 8.  Smaller buckets take E = -1, larger
+// ones E = 8.
 struct Table {
   int e[2][kBuckets];
   int batch[2] = {kElems, kElems};   // batch plans (finom_tune_set_batch)
   Table() {
     //                           2^10 .. 2^22
-    const int f64[13] = {kElemsSmall, kElemsSmall, kElemsSmall, 1, 2, 4, 2, 4, 4, 8, 8, 8, 8};
-    const int f32[13] = {kElemsSmall, kElemsSmall, 1, 1, 2, 4, 1, 2, 4, 4, 4, 8, 8};
+    const int f64[13] = {kElemsSmall, kElemsSmall, kElemsSmall, kElemsSmall, 1, 1, 2, 4, 8, 8, 8, 8, 8};
+    const int f32[13] = {kElemsSmall, kElemsSmall, kElemsSmall, 1, 2, 4, 2, 4, 4, 4, 4, 8, 8};
     for (int b = 0; b < kBuckets; ++b) {
       const int k = b < 10 ? 0 : (b > 22 ? 12 : b - 10);
       e[FINOM_F64][b] = b < 10 ? kElemsSmall : (b > 22 ? kElems : f64[k]);
