@@ -9,9 +9,10 @@ point-iterations.  L2 is flushed (256 MB write) before every timed step, and
 each step is timed with CUDA events on the launching stream.
 
 Unless `--no-sub`, the default line also carries bounded sub-results: `serve`
-(the first 100 arrivals of the serving workload), `batch` (the batch workload)
-and `small_fp64` (the 1000-point float64 workload: time per iteration and its
-2000-iteration solve beside the stored oracle solve).
+(the first 100 arrivals of the serving workload), `batch` (the batch workload),
+`small_fp64` (the 1000-point float64 workload: time per iteration and its
+2000-iteration solve beside the stored oracle solve) and `grid_2d` (the 2D
+workload on 1024 x 1024 grids: 10 timed steps and one end-to-end solve).
 
 `--workload batch` times batches of independent 1D instances (4096 instances,
 N = M log-uniform in [256, 65536], clustered meshes, eps log-uniform in
@@ -371,7 +372,7 @@ def timed_steps(api, plan, args, stream, dev, ws):
     return float(sum(times)), clocks
 
 
-def run_finom_2d(args, ws, rank, local):
+def run_finom_2d(args, ws, rank, local, emit=True):
     import torch
 
     from paper_2605_26659_gb300 import api, inputs
@@ -442,8 +443,12 @@ def run_finom_2d(args, ws, rank, local):
                          "algorithmic_bytes_per_step": bytes_per_step},
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        api.finom_plan_destroy(plan)
+        return line
     api.finom_plan_destroy(plan)
+    return None
 
 
 def run_small(dev, stream):
@@ -896,9 +901,12 @@ def run_finom(args, ws, rank, local):
     # short: served solves/s with p50 / p99 on the first arrivals of the
     # serving process, and the batched form, each beside the plain
     # one-at-a-time FP64 form
-    serve = batch = small = None
+    serve = batch = small = grid = None
     if not args.no_sub:
         small = run_small(dev, stream)
+        sub = argparse.Namespace(**vars(args))
+        sub.side, sub.steps, sub.warmup, sub.e2e_steps, sub.no_cpu_baseline = 1024, 10, 3, 1, True
+        grid = run_finom_2d(sub, ws, rank, local, emit=False)
         sub = argparse.Namespace(**vars(args))
         sub.requests, sub.plain_count, sub.slots, sub.budget_gb, sub.policy = 100, 4, 64, 64.0, "smallest"
         sub.rates, sub.eps_stages, sub.warmup = "", 0, 3
@@ -933,6 +941,9 @@ def run_finom(args, ws, rank, local):
                                                    "config")}
         if small is not None:
             line["small_fp64"] = small
+        if grid is not None:
+            line["grid_2d"] = {k: grid[k] for k in ("value", "unit", "ms_per_step", "roofline", "clocks", "e2e",
+                                                    "config")}
         print(json.dumps(line), flush=True)
     api.finom_plan_destroy(plan)
 
