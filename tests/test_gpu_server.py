@@ -343,3 +343,28 @@ def test_cancel_batched_requests(lib):
     srv.close()
     assert out[c][0]["status"] == lib.FINOM_ECANCELED
     assert out[d][0]["status"] == 0 and out[d][0]["converged"] == 1
+
+
+def test_close_with_running_batches_and_reapers(lib):
+    """Closing a server while batches run on their threads, solves run on their
+    streams and retired plans wait for their reaper stops the batches, joins
+    every thread and frees everything (the process goes on to use the GPU)."""
+    srv = lib.Server(1 << 32, max_active=4, precision="f32_log")
+    x, y = meshes("graded", 20000, 20000, 3)
+    u, v = _masses(20000, 20000, 4)
+    for _ in range(6):   # one long batch
+        srv.submit_1d(x, y, u, v, 0.001, 1e-9, 100000)
+    x2, y2 = meshes("uniform_random", 90000, 80000, 5)   # above the batching limit: alone
+    u2, v2 = _masses(90000, 80000, 6)
+    srv.submit_1d(x2, y2, u2, v2, 0.001, 1e-9, 100000)
+    small = [_small_1d(n, 70 + n, 0.02) for n in (300, 500, 700)]
+    ids = [_submit(srv, r) for r in small]
+    for _ in range(3):
+        srv.step()
+    srv.close()
+    # the GPU is usable afterwards, and a new server serves the small requests
+    srv = lib.Server(1 << 32, max_active=2, precision="f32_log")
+    ids = [_submit(srv, r) for r in small]
+    out = srv.run(ids)
+    srv.close()
+    assert all(out[i][0]["status"] == 0 and out[i][0]["converged"] == 1 for i in ids)
