@@ -468,6 +468,8 @@ struct HalfArgs {
   // H_LINES: lines of the launch; line l's node i sits at grid index
   // (l % inner) + (l / inner) * inner * nk + i * inner
   int lines;
+  int pair;                        // lines of exactly two tiles: each tile forms its carry
+                                   // from the other tile's W points (no aggregate launch)
   int64_t inner, nk;
   const typename HT<R>::Lv* gW;    // W log-weights on the grid (bits)
   const typename HT<R>::Lv* gO;    // O log-weights on the grid (frames; H_POT / H_ERR)
@@ -822,6 +824,37 @@ __device__ __forceinline__ bool half_unit(const HalfArgs<R>& a, HalfSmem<R, EK>&
     const R* c = a.carry_in + 2 * H::kSt * slot;
     H::get(c, cf.M, cf.s);
     H::get(c + H::kSt, cb.M, cb.s);
+  }
+  if constexpr (kLines) {
+    if (a.pair) {
+      // A line of two tiles: the carry entering this tile is the log-sum of
+      // the other tile's W levels (beta- of tile 1 for tile 0's backward
+      // sums, beta+ of tile 0 for tile 1's forward sums), formed here from
+      // its W points, a run per thread and one warp's scan of the run totals.
+      const int t2 = tile ^ 1;
+      const int64_t k0b = (int64_t)t2 * kT, kendb = min(k0b + (int64_t)kT, a.L);
+      const int x0b = a.tile_x0[t2], x1b = a.tile_x0[t2 + 1];
+      const int y0b = (int)(k0b - x0b), y1b = (int)(kendb - x1b);
+      const int wsb = a.o_is_x ? y0b : x0b;
+      const int nwb = a.o_is_x ? (y1b - y0b) : (x1b - x0b);
+      const int lo2 = (int)(((int64_t)tid * nwb) / NT);
+      const int q2 = (int)(((int64_t)(tid + 1) * nwb) / NT) - lo2;   // at most E
+      St<R> pt = st_empty<R>();
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (e < q2) {
+          const Beta b = wbeta(wsb + lo2 + e - (int)w_start);
+          st_term(pt, tile == 0 ? H::bm(b) : H::bp(b));
+        }
+      }
+      hslot_put(sm, 0, tid, pt);
+      __syncthreads();
+      if (tid < 32) hrake_one<R, EK, 0>(sm, st_empty<R>());
+      __syncthreads();
+      const St<R> tot{sm.totM, sm.tots};
+      if (tile == 0) cb = tot;
+      else cf = tot;
+    }
   }
   hslot_put(sm, 0, tid, tf);
   hslot_put(sm, 1, tid, tb);

@@ -270,7 +270,8 @@ double* w64(finom_plan_s* p) {
 
 // One axis pass along axis k.  W: log-weights on the grid (gW; positions of
 // the W side's nodes); O: grid frames gO (or frames 0 for QOUT / FB passes).
-// Lines spanning several tiles get their carries from an aggregate launch.
+// Lines of two tiles form their carries inside the pass (each tile from the
+// other's W points); lines of more tiles get them from an aggregate launch.
 template <class R>
 finom_status nd_pass(finom_plan_s* p, int k, int o_is_x, const LvT<R>* gW, int mode, const LvT<R>* gO,
                      LvT<R>* gO_out, const LvT<R>* lmO, LvT<R>* q_out, double* out, const double* zlogW,
@@ -305,7 +306,8 @@ finom_status nd_pass(finom_plan_s* p, int k, int o_is_x, const LvT<R>* gW, int m
   a.tol = tol;
   a.maxit = maxit;
   a.carry_in = nullptr;
-  if (a.C > 1) {
+  a.pair = a.C == 2 ? 1 : 0;   // two tiles per line: carries formed inside the pass
+  if (a.C > 2) {
     finom_status rc = half_launch<R>(a, zlogW ? kLineAggZ : kLineAgg, ax->elems, s);
     if (rc != FINOM_OK) return rc;
     a.carry_in = carries;

@@ -63,11 +63,12 @@ def test_products_small_dense(lib, prec, n, eps):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32_log"])
-def test_products_multi_tile_lines(lib, prec):
-    """Axis 0 has 1500 + 1500 merged nodes per line (several tiles at any
-    tile size), so lines carry state from tile to tile; checked against the
-    axis-by-axis oracle."""
-    n = (1500, 3, 2)
+@pytest.mark.parametrize("n", [(1500, 3, 2), (2600, 2, 2)])
+def test_products_multi_tile_lines(lib, prec, n):
+    """Axis 0 has 1500 + 1500 merged nodes per line (two tiles of 2048: each
+    tile forms its carry from the other's weights inside the pass) or
+    2600 + 2600 (three tiles: carries from an aggregate launch), so lines carry
+    state from tile to tile; checked against the axis-by-axis oracle."""
     xs, ys = _axes(n, 5), _axes(n, 6)
     eps = 0.004
     G = int(np.prod(n))
@@ -99,6 +100,28 @@ def test_lockstep_with_oracle(lib, prec, maxit):
     assert np.max(np.abs(H(f)[mu] - A[mu])) / eps <= LOCK[prec]
     assert np.max(np.abs(H(g)[mv] - B[mv])) / eps <= LOCK[prec]
     assert np.all(np.isneginf(H(f)[~mu])) and np.all(np.isneginf(H(g)[~mv]))
+    if prec == "f64":
+        assert res["marginal_err"] == pytest.approx(err, rel=1e-8)
+    else:
+        assert abs(res["marginal_err"] - err) <= 2e-4 * err + 2e-7
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32_log"])
+@pytest.mark.parametrize("n", [(1100, 3), (2300, 2)])
+def test_lockstep_two_and_three_tile_lines(lib, prec, n):
+    """A 2D grid whose axis-0 lines span two tiles (1100 + 1100 merged nodes)
+    or three (2300 + 2300): every pass of four iterations against the oracle."""
+    xs, ys = _axes(n, 31), _axes(n, 32)
+    G = int(np.prod(n))
+    u, v = _masses(G, 33, zeros=True)
+    eps = 0.01
+    p = _plan(lib, xs, ys, eps, prec)
+    f, g, res = lib.finom_solve(p, T(u), T(v), 0.0, 4)
+    A, B, it, err = serial_c.sinkhorn_nd(xs, ys, u, v, eps, 0.0, 4)
+    assert res["iters"] == it == 4
+    mu, mv = u > 0, v > 0
+    assert np.max(np.abs(H(f)[mu] - A[mu])) / eps <= LOCK[prec]
+    assert np.max(np.abs(H(g)[mv] - B[mv])) / eps <= LOCK[prec]
     if prec == "f64":
         assert res["marginal_err"] == pytest.approx(err, rel=1e-8)
     else:
