@@ -155,3 +155,17 @@ def test_split_terms_and_whole_number_scales():
         want = 0.0 if abs(d) > 1022 else 2.0 ** -abs(d)
         assert _pow2_neg(float(d)) == want
     assert _pow2_neg(1e300) == 0.0 and _pow2_neg(-1e300) == 0.0 and _pow2_neg(0.0) == 1.0
+
+
+def test_table_header_is_what_its_generator_writes():
+    import contextlib
+    import importlib.util
+    import io
+    gen = os.path.join(os.path.dirname(HDR), "gen_exp2_table.py")
+    spec = importlib.util.spec_from_file_location("gen_exp2_table", gen)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        mod.main()
+    assert buf.getvalue() == open(HDR).read()
