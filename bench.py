@@ -784,6 +784,8 @@ def run_finom_serve(args, ws, rank, local, emit=True):
                           "queue_p99": float(np.percentile(que, 99))},
             "converged": int(nconv), "point_iters_per_s": pts / wall,
             "gpu_launches": launches,
+            "gpu_launches_note": "half-step launches if every request ran alone (2 per 1D iteration, 4 per 2D); "
+                                 "batched 1D requests share theirs, so this is an upper bound",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "every k_half launch of the served solves, over the wall time",
